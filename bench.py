@@ -1,0 +1,375 @@
+"""Benchmark: even-odd Wilson dslash throughput on a 32^3x64 lattice.
+
+One step = one parity-restricted hopping application (Dslash of the paper's
+section "Wilson inverter: Main features") over the V/2 = 1,048,576 sites of
+one parity, FP32 with 12-real links (the headline), alternating the output
+parity each step.  Effective Gflops use the nominal 1320 flops per site
+(reconstruction work not counted, as in the paper's "effective gigaflops",
+section "Performance").  The FP16 (per-site scale) variant is timed too.
+
+Contract: one JSON line on rank 0 with metric/value/unit, roofline (HBM),
+cpu_baseline (the FP64 oracle on the host cores), e2e (through the C ABI with
+host buffers), clocks and gpu_launches.  ``--impl reference`` times the FP64
+CPU oracle on the same workload instead (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "dslash GB/s & Gflops vs HBM peak; time-to-1e-10 solve vs plain FP64 CG"
+FLOPS_PER_SITE = 1320
+# compulsory bytes per output site of one parity application: 8 links, the
+# input spinor once, the output spinor once
+BYTES_PER_SITE = {"f32": 8 * 48 + 96 + 96, "f16": 8 * 24 + 52 + 52, "f64": 8 * 144 + 192 + 192}
+DIMS = (32, 32, 32, 64)
+KAPPA = 0.1365
+DATA = ("synthetic: seeded SU(3) links U = reunit(exp(i 0.3 H)), H Gaussian traceless "
+        "Hermitian; complex-Gaussian spinor (no dataset or checkpoint)")
+
+
+def dslash_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0810_5365_gb300", "csrc")
+    for f in ("wd_common.cuh", "wd_dslash.cuh", "wd_internal.h", "wd_dslash_f32.cu",
+              "wd_dslash_f16.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def profiled_traffic(prec: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    e = d.get(prec)
+    if not e or e.get("source_hash") != dslash_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=self.file,
+                stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.file.flush()
+        with open(self.file.name) as f:
+            rows = [r.strip().split(",") for r in f if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_fields(dims):
+    from synth import fields
+    U = fields.su3_links(dims)
+    psi = fields.gaussian_spinor(dims)
+    return U, psi
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_step_sample(U, psi, dims, target_s=0.05):
+    """Pick a site sample so one oracle step takes about target_s seconds."""
+    import oracle
+    from synth import fields
+    sites = fields.half_sites(dims, 0)
+    n = 4096
+    t0 = time.perf_counter()
+    oracle.hop_sites(psi, U, dims, sites[:n])
+    dt = time.perf_counter() - t0
+    n = int(min(len(sites), max(1024, n * target_s / max(dt, 1e-6))))
+    return sites[:n]
+
+
+def cpu_baseline(U, psi, dims, budget_s=12.0):
+    """The FP64 oracle's parity dslash on the same fields, on all host cores,
+    repeated over whole-lattice applications until about budget_s of work."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    Vh = int(np.prod(dims)) // 2
+    n, t = 0, 0.0
+    while t < budget_s and n < 50:
+        t0 = time.perf_counter()
+        oracle.hop(psi, U, dims, dagger=False, out_parity=0)
+        t += time.perf_counter() - t0
+        n += 1
+    return {"value": FLOPS_PER_SITE * Vh * n / t / 1e9, "unit": "Gflops",
+            "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{n} full even-parity applications of the FP64 oracle hopping term "
+                      f"on the 32^3x64 fields ({t:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    dims = DIMS
+    U, psi = make_fields(dims)
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    sites = oracle_step_sample(U, psi, dims)
+    for _ in range(args.warmup):
+        oracle.hop_sites(psi, U, dims, sites)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.hop_sites(psi, U, dims, sites)
+    dt = time.perf_counter() - t0
+    value = FLOPS_PER_SITE * len(sites) * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gflops",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": DATA,
+        "config": {"workload": "even-odd dslash 32^3x64, kappa=0.1365 (FP64 CPU oracle)",
+                   "dims": list(dims), "sites_per_step": int(len(sites))},
+        "cpu_baseline": {"value": value, "unit": "Gflops", "cores": oracle.get_threads(),
+                         "kind": "oracle",
+                         "sample": f"{len(sites)} even sites of 32^3x64 per step"},
+        "e2e": {"value": value, "unit": "Gflops", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU path
+# ---------------------------------------------------------------------------
+
+def time_dslash(W, torch, prec_id, gauge, bufs, dims, steps, warmup, stream):
+    """K back-to-back parity dslash launches (ping-pong), CUDA events on the
+    launching stream.  Returns elapsed seconds."""
+    a, b = bufs
+
+    def step(k):
+        if k & 1:
+            W.wd_dslash(a, b, gauge, KAPPA, W.WD_ODD, dims, prec_id)
+        else:
+            W.wd_dslash(b, a, gauge, KAPPA, W.WD_EVEN, dims, prec_id)
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        step(k)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_0810_5365_gb300 as W
+    W.wd.lib()
+    stream = torch.cuda.current_stream()
+    W.wd_set_stream(stream)
+
+    dims = DIMS
+    Vh = int(np.prod(dims)) // 2
+    U, psi = make_fields(dims)
+    Ud = torch.from_numpy(U.view(np.float64).reshape(-1)).cuda()
+    from synth import fields
+    src = fields.to_half(psi, dims, 1)
+    srcd = torch.from_numpy(src.view(np.float64).reshape(-1)).cuda()
+
+    results = {}
+    peaks, peak_kind = measured_peaks()
+    gauges = {}
+    with ClockSampler(local) as clk:
+        for name, pid in (("f32", W.WD_F32), ("f16", W.WD_F16)):
+            g = W.alloc_gauge(dims, pid, 12)
+            W.wd_pack_gauge(g, Ud, dims, pid, 12)
+            a = W.alloc_spinor(dims, W.WD_ODD, pid)
+            b = W.alloc_spinor(dims, W.WD_EVEN, pid)
+            W.wd_pack_spinor(a, srcd, dims, W.WD_ODD, pid)
+            W.wd_pack_spinor(b, srcd, dims, W.WD_EVEN, pid)
+            gauges[name] = (g, a, b, pid)
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            dt = time_dslash(W, torch, pid, g, (a, b), dims, args.steps, args.warmup, stream)
+            if world > 1:
+                t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                dt = t.item()
+                torch.distributed.barrier()
+            results[name] = dt
+            if args.quick:
+                break
+        # end to end through the C ABI with pinned host buffers
+        g, a, b, pid = gauges["f32"]
+        nb = W.wd_spinor_bytes(dims, W.WD_ODD, W.WD_F32)
+        h_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        h_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        h_in.copy_(a)
+        k_e2e = max(1, min(args.steps, 50))
+
+        def e2e_step():
+            a.copy_(h_in, non_blocking=True)
+            W.wd_dslash(b, a, g, KAPPA, W.WD_EVEN, dims, W.WD_F32)
+            h_out.copy_(b, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k_e2e):
+            e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        dt_e2e = e0.elapsed_time(e1) / 1e3
+    clocks = clk.summary()
+
+    dt = results["f32"]
+    gflops = FLOPS_PER_SITE * Vh * args.steps * world / dt / 1e9
+    launch_s = dt / args.steps
+    achieved = BYTES_PER_SITE["f32"] * Vh / launch_s / 1e9
+    traffic = profiled_traffic("f32")
+    line = {
+        "metric": METRIC, "value": gflops, "unit": "Gflops", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": DATA,
+        "config": {"workload": "even-odd dslash 32^3x64, FP32, 12-real links, kappa=0.1365, "
+                               "single RHS, parity alternating per step",
+                   "dims": list(dims), "kappa": KAPPA, "sites_per_step": Vh,
+                   "flops_per_site": FLOPS_PER_SITE,
+                   "l2": "inputs larger than L2 (links 403 MB + spinors 2 x 101 MB vs 129 MB L2)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "dslash_gbs": achieved,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                     "bytes_per_site": BYTES_PER_SITE["f32"]},
+        "gpu_launches": args.steps,
+    }
+    if "f16" in results:
+        d16 = results["f16"]
+        ach16 = BYTES_PER_SITE["f16"] * Vh / (d16 / args.steps) / 1e9
+        line["variants"] = {"f16": {
+            "value": FLOPS_PER_SITE * Vh * args.steps * world / d16 / 1e9, "unit": "Gflops",
+            "ms_per_step": 1e3 * d16 / args.steps, "dslash_gbs": ach16,
+            "frac": ach16 / peaks["hbm_gbs"], "bytes_per_site": BYTES_PER_SITE["f16"],
+            "traffic": profiled_traffic("f16")}}
+        line["gpu_launches"] += args.steps
+    line["e2e"] = {"value": FLOPS_PER_SITE * Vh * k_e2e * world / dt_e2e / 1e9, "unit": "Gflops",
+                   "steps": k_e2e, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+    line["gpu_launches"] += k_e2e
+    line["clocks"] = clocks
+    if rank == 0 and not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(U, psi, dims)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--quick", action="store_true", help="FP32 only")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,237 @@
+/*
+ * wd.h -- C ABI of libwd, a GB300 (sm_103a) library for the Wilson-Dirac
+ * operator and the Krylov solve that calls it.
+ *
+ * Paper: K. Barros, R. Babich, R. Brower, M. A. Clark, C. Rebbi, "Blasting
+ * through lattice calculations using CUDA", Lattice 2008 (arXiv:0810.5365).
+ * The paper implements a CUDA kernel "Dslash" (the Wilson-Dirac hopping term
+ * restricted to the even or odd sub-lattice, with its adjoint) and an
+ * even-odd preconditioned conjugate-gradient solver built from it, a
+ * double-precision dot product and BLAS-like vector kernels (section
+ * "Wilson inverter: Main features"); its Fig. 1 benchmarks the preconditioned
+ * operator 1 - kappa^2 D_eo D_oe.  The operator itself is not printed there;
+ * this library uses the standard Wilson fermion (r = 1, hopping-parameter
+ * normalisation):
+ *
+ *   D psi(x) = psi(x) - kappa * H psi(x),
+ *   H psi(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                     + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu) ],
+ *
+ * chiral gamma basis (gamma_5 = diag(1,1,-1,-1)), periodic boundaries in x, y,
+ * z and antiperiodic ones in t.  H^+ exchanges the two projectors.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions shared by every call
+ * ---------------------------------------------------------------------------
+ * dims[4]   lattice extents L0 (x), L1 (y), L2 (z), L3 (t).  Every extent must
+ *           be even and >= 2 (else WD_ERR_DIMS); V = L0 L1 L2 L3, Vh = V/2.
+ * parity    of site x is (x0+x1+x2+x3) & 1; WD_EVEN = 0, WD_ODD = 1.
+ *           WD_FULL (-1) means both parities (even half first, then odd).
+ * canonical FP64 layouts (row-major complex double, re then im):
+ *           full spinor   [V][4 spin][3 colour]
+ *           half spinor   [Vh][4][3]: the sites of one parity in increasing
+ *                         lexicographic order (site i sits at i >> 1)
+ *           gauge         [4 mu][V][3 row][3 col]; U_mu(x) links x -> x+mu
+ *           lexicographic site i = x0 + L0*(x1 + L1*(x2 + L2*x3)).
+ * packed    formats are opaque device buffers produced by wd_pack_* and sized
+ *           by wd_spinor_bytes / wd_gauge_bytes (site-blocked structure of
+ *           arrays: blocks of 32 checkerboard sites, each block holding one
+ *           128-bit vector per site per component group).  Precisions:
+ *           WD_F64 (double), WD_F32 (float), WD_F16 (half with one float
+ *           scale per site for spinors; plain half for SU(3) links).  Links
+ *           are stored with 18 reals (recon = 18) or as their first two rows,
+ *           12 reals (recon = 12), the third row being rebuilt in registers
+ *           as conj(row0 x row1) (paper, section "Performance": only two
+ *           columns of each gauge matrix are read; rows are used here, which
+ *           is equivalent for SU(3)).  WD_F16 links support recon = 12 only.
+ * pointers  unless stated otherwise, buffer arguments are DEVICE pointers,
+ *           16-byte aligned (else WD_ERR_ALIGN), owned by the caller; the
+ *           library never frees them.  Calls are asynchronous on the stream
+ *           set by wd_set_stream (default: the legacy default stream), except
+ *           wd_solve / wd_solve_ex, which return after the solve.
+ * errors    every int-returning call returns a WD_* status; no C++ exception
+ *           crosses this interface.  WD_ERR_CUDA means a CUDA runtime call
+ *           failed (wd_last_cuda_error gives its code).  The library is not
+ *           thread-safe: use it from one host thread at a time.
+ */
+#ifndef WD_H
+#define WD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2 };
+enum { WD_EVEN = 0, WD_ODD = 1, WD_FULL = -1 };
+
+enum {
+    WD_OK = 0,
+    WD_ERR_NULL = 1,       /* a required pointer is NULL */
+    WD_ERR_DIMS = 2,       /* an extent is odd, < 2, or the volume overflows */
+    WD_ERR_PREC = 3,       /* unknown precision / unsupported (prec, recon) */
+    WD_ERR_ALIGN = 4,      /* a device buffer is not 16-byte aligned */
+    WD_ERR_ALIAS = 5,      /* output aliases an input that is read at neighbours */
+    WD_ERR_NOCONV = 6,     /* solver hit maxiter; x holds the best iterate */
+    WD_ERR_NONFINITE = 7,  /* NaN/Inf met in a residual norm */
+    WD_ERR_TIMEOUT = 8,    /* a bounded device-side wait gave up */
+    WD_ERR_CUDA = 9,       /* a CUDA runtime call failed */
+    WD_ERR_ARG = 10,       /* another argument is out of range */
+    WD_ERR_BREAKDOWN = 11  /* Krylov breakdown (p^+ A p <= 0) */
+};
+
+/* ------------------------------------------------------------------ */
+/* state                                                               */
+/* ------------------------------------------------------------------ */
+
+/* Stream for all following calls (a cudaStream_t; NULL = legacy default). */
+int wd_set_stream(void *cuda_stream);
+void *wd_get_stream(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *wd_error_string(int status);
+
+/* cudaError_t of the last failed CUDA call (0 if none). */
+int wd_last_cuda_error(void);
+
+/* Free the library's cached workspace (solver fields, reduction scratch,
+ * captured graphs).  Caller buffers are untouched.  Safe to call twice. */
+void wd_finalize(void);
+
+/* ------------------------------------------------------------------ */
+/* layout: sizes, pack, unpack (paper, section "Data layout")          */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of a packed spinor field of one parity (or both, parity = WD_FULL);
+ * 0 on invalid arguments. */
+size_t wd_spinor_bytes(const int dims[4], int parity, int prec);
+
+/* Bytes of a packed gauge field (all 4 directions, both parities); 0 on
+ * invalid arguments (e.g. WD_F16 with recon 18). */
+size_t wd_gauge_bytes(const int dims[4], int prec, int recon);
+
+/* Canonical FP64 gauge field (device) -> packed gauge of (prec, recon),
+ * split by parity of the link's base site. */
+int wd_pack_gauge(void *dst, const double *src_canonical, const int dims[4],
+                  int prec, int recon);
+
+/* Canonical FP64 spinor (device; half layout for parity 0/1, full layout for
+ * WD_FULL) -> packed spinor of prec. */
+int wd_pack_spinor(void *dst, const double *src_canonical, const int dims[4],
+                   int parity, int prec);
+
+/* Packed spinor -> canonical FP64 (device), inverse of wd_pack_spinor. */
+int wd_unpack_spinor(double *dst_canonical, const void *src, const int dims[4],
+                     int parity, int prec);
+
+/* Packed spinor of src_prec -> packed spinor of dst_prec (same parity). */
+int wd_convert_spinor(void *dst, int dst_prec, const void *src, int src_prec,
+                      const int dims[4], int parity);
+
+/* ------------------------------------------------------------------ */
+/* the hopping operator (paper, section "Wilson inverter")             */
+/* ------------------------------------------------------------------ */
+
+/*
+ * wd_dslash: parity p in {WD_EVEN, WD_ODD}:
+ *     out_p = -kappa * H_{p,1-p} in_{1-p}
+ * (in is the packed half field of the opposite parity, out of parity p);
+ * parity WD_FULL:
+ *     out = in - kappa * H in = D in    (packed full fields).
+ * gauge is packed with the same prec and recon 12 (use wd_dslash_ex for
+ * recon 18).  out must not alias in (WD_ERR_ALIAS).
+ */
+int wd_dslash(void *out, const void *in, const void *gauge, double kappa,
+              int parity, const int dims[4], int prec);
+
+/* Same with H^+ (projectors exchanged): D^+ = gamma_5 D gamma_5. */
+int wd_dslash_dag(void *out, const void *in, const void *gauge, double kappa,
+                  int parity, const int dims[4], int prec);
+
+/*
+ * General parity-restricted hopping application with a fused epilogue:
+ *     out_p = a * H_{p,1-p} in_{1-p}  [+ bx * x_p]  [+ cy * y_p]
+ * (H^+ when dagger != 0).  x and y may be NULL (term dropped) and may alias
+ * out; in must not.  If norm2 != NULL (device double*), ||out_p||^2 is
+ * written there (FP64, deterministic reduction order).  recon is 12 or 18.
+ */
+int wd_dslash_ex(void *out, const void *in, const void *gauge, int parity, int dagger,
+                 double a, const void *x, double bx, const void *y, double cy,
+                 double *norm2, const int dims[4], int prec, int recon);
+
+/*
+ * Even-odd preconditioned operator on the even sub-lattice (paper Fig. 1):
+ *     out_e = (1 - kappa^2 H_eo H_oe) in_e          (dagger = 0)
+ *     out_e = (1 - kappa^2 H^+_eo H^+_oe) in_e      (dagger = 1, its adjoint)
+ * tmp is a caller-owned packed odd half field of the same prec.
+ */
+int wd_mhat(void *out, const void *in, const void *gauge, void *tmp, double kappa,
+            int dagger, const int dims[4], int prec, int recon);
+
+/* ------------------------------------------------------------------ */
+/* BLAS-like kernels and FP64 reductions (paper: dot product by        */
+/* parallel reduction in double precision; "BLAS-like" vector kernels) */
+/* ------------------------------------------------------------------ */
+
+/* result[0] = ||x||^2 (device double*), FP64 accumulation. */
+int wd_norm2(double *result, const void *x, const int dims[4], int parity, int prec);
+
+/* result[0..1] = <x, y> = sum conj(x) y (re, im), FP64 accumulation. */
+int wd_cdot(double *result, const void *x, const void *y, const int dims[4],
+            int parity, int prec);
+
+/* y = a x + b y (real a, b), elementwise in the storage precision's
+ * arithmetic (FP32 for WD_F16). */
+int wd_axpby(double a, const void *x, double b, void *y, const int dims[4],
+             int parity, int prec);
+
+/* ------------------------------------------------------------------ */
+/* solver (paper: even-odd preconditioned CG; Fig. 2)                  */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int inner_prec;          /* WD_F64 (plain FP64 CG), WD_F32 or WD_F16 */
+    int inner_recon;         /* link format of the inner operator: 12 or 18 */
+    int outer_recon;         /* link format of the FP64 operator: 12 or 18 */
+    int reliable_interval;   /* FP64 reliable update every n iterations (50) */
+    int check_interval;      /* iterations between host convergence checks (10) */
+    int maxiter;             /* iteration cap (default 100000) */
+    int use_graph;           /* capture check_interval iterations as a CUDA graph */
+    int use_initial_guess;   /* x holds a starting guess (restart / resume) */
+    double tol;              /* target ||b - D x|| / ||b|| (default 1e-10) */
+} wd_solve_params;
+
+typedef struct {
+    int iters;               /* inner iterations */
+    int reliable_updates;    /* FP64 residual recomputations */
+    int status;              /* WD_* */
+    double true_residual;    /* ||b - D x|| / ||b||, FP64 on the full lattice */
+    double seconds;          /* wall time of the solve inside wd_solve_ex */
+    double dslash_calls;     /* hopping applications issued (all precisions) */
+} wd_solve_info;
+
+/* Fill p with the defaults above (inner_prec WD_F32, recon 12 / 18). */
+void wd_solve_params_default(wd_solve_params *p);
+
+/*
+ * Solve D x = b on the full lattice to ||b - D x||_2 / ||b||_2 <= tol, with
+ * the even-odd Schur complement (1 - kappa^2 H_eo H_oe) x_e = b_e + kappa
+ * H_eo b_o, CG on its normal equations (CGLS form), mixed precision with
+ * FP64 reliable updates, then x_o = b_o + kappa H_oe x_e.
+ * x, b: canonical FP64 full spinors; gauge: canonical FP64 gauge field.  Each
+ * may be a host or a device pointer (detected per pointer); host data are
+ * staged through library workspace.  Returns after the solve.
+ */
+int wd_solve(double *x, const double *b, const double *gauge, double kappa,
+             double tol, const int dims[4]);
+
+int wd_solve_ex(double *x, const double *b, const double *gauge, double kappa,
+                const int dims[4], const wd_solve_params *params,
+                wd_solve_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WD_H */

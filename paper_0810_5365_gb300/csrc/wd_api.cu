@@ -1,0 +1,276 @@
+// The extern "C" entry points of libwd (declared and documented in
+// include/wd.h): argument validation, status codes, and dispatch to the
+// kernels.  No C++ exception crosses this boundary.
+#include <cstdint>
+#include <cstring>
+
+#include "wd_internal.h"
+
+namespace wd {
+int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
+               const wd_solve_params* prm, wd_solve_info* info);
+void solver_finalize();
+}  // namespace wd
+
+using namespace wd;
+
+namespace {
+
+int check_dims(const int* dims) {
+  if (!dims) return WD_ERR_NULL;
+  long long V = 1;
+  for (int i = 0; i < 4; i++) {
+    if (dims[i] < 2 || (dims[i] & 1)) return WD_ERR_DIMS;
+    V *= dims[i];
+    if (V > (1LL << 30)) return WD_ERR_DIMS;  // checkerboard indices stay in int32
+  }
+  return WD_OK;
+}
+
+bool aligned(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_prec(int prec) { return (prec >= WD_F64 && prec <= WD_F16) ? WD_OK : WD_ERR_PREC; }
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return WD_OK;
+  state().last_cuda_error = (int)e;
+  return WD_ERR_CUDA;
+}
+
+#define WD_TRY(expr)            \
+  do {                          \
+    int rc_ = (expr);           \
+    if (rc_ != WD_OK) return rc_; \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int wd_set_stream(void* s) {
+  state().stream = (cudaStream_t)s;
+  return WD_OK;
+}
+
+void* wd_get_stream(void) { return (void*)state().stream; }
+
+const char* wd_error_string(int status) {
+  switch (status) {
+    case WD_OK: return "WD_OK";
+    case WD_ERR_NULL: return "WD_ERR_NULL: a required pointer is NULL";
+    case WD_ERR_DIMS: return "WD_ERR_DIMS: every extent must be even and >= 2";
+    case WD_ERR_PREC: return "WD_ERR_PREC: unknown or unsupported precision / link format";
+    case WD_ERR_ALIGN: return "WD_ERR_ALIGN: device buffers must be 16-byte aligned";
+    case WD_ERR_ALIAS: return "WD_ERR_ALIAS: output aliases an input read at neighbour sites";
+    case WD_ERR_NOCONV: return "WD_ERR_NOCONV: solver did not reach the tolerance";
+    case WD_ERR_NONFINITE: return "WD_ERR_NONFINITE: NaN or Inf in a residual";
+    case WD_ERR_TIMEOUT: return "WD_ERR_TIMEOUT: a bounded device wait gave up";
+    case WD_ERR_CUDA: return "WD_ERR_CUDA: a CUDA runtime call failed";
+    case WD_ERR_ARG: return "WD_ERR_ARG: argument out of range";
+    case WD_ERR_BREAKDOWN: return "WD_ERR_BREAKDOWN: Krylov breakdown";
+  }
+  return "unknown status";
+}
+
+int wd_last_cuda_error(void) { return state().last_cuda_error; }
+
+void wd_finalize(void) {
+  cudaDeviceSynchronize();
+  solver_finalize();
+  State& s = state();
+  if (s.partials) cudaFree(s.partials);
+  if (s.counter) cudaFree(s.counter);
+  s.partials = nullptr;
+  s.counter = nullptr;
+  s.partials_cap = 0;
+}
+
+size_t wd_spinor_bytes(const int dims[4], int parity, int prec) {
+  if (check_dims(dims) != WD_OK || check_prec(prec) != WD_OK) return 0;
+  if (parity != WD_EVEN && parity != WD_ODD && parity != WD_FULL) return 0;
+  Geom g = make_geom(dims);
+  size_t h = spinor_half_bytes(g, prec);
+  return parity == WD_FULL ? 2 * h : h;
+}
+
+size_t wd_gauge_bytes(const int dims[4], int prec, int recon) {
+  if (check_dims(dims) != WD_OK || check_prec(prec) != WD_OK) return 0;
+  if (link_bytes(prec, recon) == 0) return 0;
+  return gauge_bytes(make_geom(dims), prec, recon);
+}
+
+int wd_pack_gauge(void* dst, const double* src, const int dims[4], int prec, int recon) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!dst || !src) return WD_ERR_NULL;
+  if (!aligned(dst) || !aligned(src)) return WD_ERR_ALIGN;
+  if (link_bytes(prec, recon) == 0) return WD_ERR_PREC;
+  return cuda_status(pack_gauge(dst, src, make_geom(dims), prec, recon, state().stream));
+}
+
+int wd_pack_spinor(void* dst, const double* src, const int dims[4], int parity, int prec) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!dst || !src) return WD_ERR_NULL;
+  if (!aligned(dst) || !aligned(src)) return WD_ERR_ALIGN;
+  if (parity != WD_EVEN && parity != WD_ODD && parity != WD_FULL) return WD_ERR_ARG;
+  return cuda_status(pack_spinor(dst, src, make_geom(dims), parity, prec, state().stream));
+}
+
+int wd_unpack_spinor(double* dst, const void* src, const int dims[4], int parity, int prec) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!dst || !src) return WD_ERR_NULL;
+  if (!aligned(dst) || !aligned(src)) return WD_ERR_ALIGN;
+  if (parity != WD_EVEN && parity != WD_ODD && parity != WD_FULL) return WD_ERR_ARG;
+  return cuda_status(unpack_spinor(dst, src, make_geom(dims), parity, prec, state().stream));
+}
+
+int wd_convert_spinor(void* dst, int dst_prec, const void* src, int src_prec, const int dims[4],
+                      int parity) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(dst_prec));
+  WD_TRY(check_prec(src_prec));
+  if (!dst || !src) return WD_ERR_NULL;
+  if (!aligned(dst) || !aligned(src)) return WD_ERR_ALIGN;
+  if (parity != WD_EVEN && parity != WD_ODD && parity != WD_FULL) return WD_ERR_ARG;
+  if (dst == src && dst_prec != src_prec) return WD_ERR_ALIAS;
+  return cuda_status(convert_spinor(dst, dst_prec, src, src_prec, make_geom(dims),
+                                    parity == WD_FULL ? 2 : 1, state().stream));
+}
+
+int wd_dslash_ex(void* out, const void* in, const void* gauge, int parity, int dagger, double a,
+                 const void* x, double bx, const void* y, double cy, double* norm2,
+                 const int dims[4], int prec, int recon) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!out || !in || !gauge) return WD_ERR_NULL;
+  if (!aligned(out) || !aligned(in) || !aligned(gauge) || (x && !aligned(x)) ||
+      (y && !aligned(y)) || (norm2 && ((uintptr_t)norm2 & 7u)))
+    return WD_ERR_ALIGN;
+  if (parity != WD_EVEN && parity != WD_ODD) return WD_ERR_ARG;
+  if (link_bytes(prec, recon) == 0) return WD_ERR_PREC;
+  if (out == in) return WD_ERR_ALIAS;
+  Geom g = make_geom(dims);
+  if (norm2) {
+    cudaError_t e = ensure_scratch((size_t)((g.Vh + DSLASH_BS - 1) / DSLASH_BS) * 2);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  DslashArgs d;
+  d.out = out;
+  d.in = in;
+  d.gauge = gauge;
+  d.x = x;
+  d.y = y;
+  d.a = a;
+  d.bx = bx;
+  d.cy = cy;
+  d.norm_out = norm2;
+  d.rs = scratch();
+  d.g = g;
+  d.parity = parity;
+  return cuda_status(launch_dslash(prec, d, recon, dagger != 0, state().stream));
+}
+
+static int dslash_common(void* out, const void* in, const void* gauge, double kappa, int parity,
+                         const int dims[4], int prec, int dagger) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!out || !in || !gauge) return WD_ERR_NULL;
+  if (parity == WD_FULL) {
+    if (out == in) return WD_ERR_ALIAS;
+    size_t h = spinor_half_bytes(make_geom(dims), prec);
+    char* o = (char*)out;
+    const char* i = (const char*)in;
+    // out_e = in_e - kappa H_eo in_o ; out_o = in_o - kappa H_oe in_e
+    WD_TRY(wd_dslash_ex(o, i + h, gauge, WD_EVEN, dagger, -kappa, i, 1.0, nullptr, 0.0, nullptr,
+                        dims, prec, 12));
+    return wd_dslash_ex(o + h, i, gauge, WD_ODD, dagger, -kappa, i + h, 1.0, nullptr, 0.0, nullptr,
+                        dims, prec, 12);
+  }
+  return wd_dslash_ex(out, in, gauge, parity, dagger, -kappa, nullptr, 0.0, nullptr, 0.0, nullptr,
+                      dims, prec, 12);
+}
+
+int wd_dslash(void* out, const void* in, const void* gauge, double kappa, int parity,
+              const int dims[4], int prec) {
+  return dslash_common(out, in, gauge, kappa, parity, dims, prec, 0);
+}
+
+int wd_dslash_dag(void* out, const void* in, const void* gauge, double kappa, int parity,
+                  const int dims[4], int prec) {
+  return dslash_common(out, in, gauge, kappa, parity, dims, prec, 1);
+}
+
+int wd_mhat(void* out, const void* in, const void* gauge, void* tmp, double kappa, int dagger,
+            const int dims[4], int prec, int recon) {
+  if (!tmp) return WD_ERR_NULL;
+  if (tmp == in || tmp == out) return WD_ERR_ALIAS;
+  WD_TRY(wd_dslash_ex(tmp, in, gauge, WD_ODD, dagger, 1.0, nullptr, 0.0, nullptr, 0.0, nullptr,
+                      dims, prec, recon));
+  return wd_dslash_ex(out, tmp, gauge, WD_EVEN, dagger, -kappa * kappa, in, 1.0, nullptr, 0.0,
+                      nullptr, dims, prec, recon);
+}
+
+int wd_norm2(double* result, const void* x, const int dims[4], int parity, int prec) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!result || !x) return WD_ERR_NULL;
+  if (!aligned(x) || ((uintptr_t)result & 7u)) return WD_ERR_ALIGN;
+  if (parity != WD_EVEN && parity != WD_ODD && parity != WD_FULL) return WD_ERR_ARG;
+  return cuda_status(norm2(result, x, make_geom(dims), prec, parity == WD_FULL ? 2 : 1,
+                           state().stream));
+}
+
+int wd_cdot(double* result, const void* x, const void* y, const int dims[4], int parity,
+            int prec) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!result || !x || !y) return WD_ERR_NULL;
+  if (!aligned(x) || !aligned(y) || ((uintptr_t)result & 7u)) return WD_ERR_ALIGN;
+  if (parity != WD_EVEN && parity != WD_ODD && parity != WD_FULL) return WD_ERR_ARG;
+  return cuda_status(cdot(result, x, y, make_geom(dims), prec, parity == WD_FULL ? 2 : 1,
+                          state().stream));
+}
+
+int wd_axpby(double a, const void* x, double b, void* y, const int dims[4], int parity, int prec) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!x || !y) return WD_ERR_NULL;
+  if (!aligned(x) || !aligned(y)) return WD_ERR_ALIGN;
+  if (parity != WD_EVEN && parity != WD_ODD && parity != WD_FULL) return WD_ERR_ARG;
+  return cuda_status(axpby(a, x, b, y, make_geom(dims), prec, parity == WD_FULL ? 2 : 1,
+                           state().stream));
+}
+
+void wd_solve_params_default(wd_solve_params* p) {
+  if (!p) return;
+  p->inner_prec = WD_F32;
+  p->inner_recon = 12;
+  p->outer_recon = 18;
+  p->reliable_interval = 50;
+  p->check_interval = 10;
+  p->maxiter = 100000;
+  p->use_graph = 1;
+  p->use_initial_guess = 0;
+  p->tol = 1e-10;
+}
+
+int wd_solve_ex(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
+                const wd_solve_params* params, wd_solve_info* info) {
+  WD_TRY(check_dims(dims));
+  if (!x || !b || !gauge) return WD_ERR_NULL;
+  if (!aligned(x) || !aligned(b) || !aligned(gauge)) return WD_ERR_ALIGN;
+  if (x == b) return WD_ERR_ALIAS;
+  return solve_impl(x, b, gauge, kappa, dims, params, info);
+}
+
+int wd_solve(double* x, const double* b, const double* gauge, double kappa, double tol,
+             const int dims[4]) {
+  wd_solve_params p;
+  wd_solve_params_default(&p);
+  p.tol = tol;
+  return wd_solve_ex(x, b, gauge, kappa, dims, &p, nullptr);
+}
+
+}  // extern "C"

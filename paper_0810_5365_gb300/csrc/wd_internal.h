@@ -1,0 +1,84 @@
+// Host-side internals of libwd shared by its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wd_common.cuh"
+
+namespace wd {
+
+// threads per block of the hopping kernel
+constexpr int DSLASH_BS = 128;
+
+struct DslashArgs {
+  void* out;
+  const void* in;
+  const void* gauge;
+  const void* x;     // optional (may alias out)
+  const void* y;     // optional (may alias out)
+  double a, bx, cy;
+  double* norm_out;  // ||out||^2 when the kernel reduces
+  RedScratch rs;
+  Geom g;
+  int parity;        // parity of the output sites
+};
+
+cudaError_t launch_dslash_f64(const DslashArgs& a, int recon, bool dagger, cudaStream_t st);
+cudaError_t launch_dslash_f32(const DslashArgs& a, int recon, bool dagger, cudaStream_t st);
+cudaError_t launch_dslash_f16(const DslashArgs& a, int recon, bool dagger, cudaStream_t st);
+
+inline cudaError_t launch_dslash(int prec, const DslashArgs& a, int recon, bool dagger,
+                                 cudaStream_t st) {
+  switch (prec) {
+    case WD_F64: return launch_dslash_f64(a, recon, dagger, st);
+    case WD_F32: return launch_dslash_f32(a, recon, dagger, st);
+    case WD_F16: return launch_dslash_f16(a, recon, dagger, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// library state
+// ---------------------------------------------------------------------------
+
+struct State {
+  cudaStream_t stream = nullptr;
+  int last_cuda_error = 0;
+  // reduction scratch shared by every reducing kernel; kernels on one stream
+  // run in order, so one set suffices (calls that overlap on the GPU race)
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  size_t partials_cap = 0;  // doubles
+  int num_sms = 0;
+};
+
+State& state();
+
+// grow the reduction scratch to hold `doubles` partial sums (not during capture)
+cudaError_t ensure_scratch(size_t doubles);
+RedScratch scratch();
+int num_sms();
+
+// grid of the grid-stride BLAS/reduction kernels for n sites
+int blas_grid(long long n, int bs);
+
+// ---------------------------------------------------------------------------
+// layout and BLAS (wd_blas.cu)
+// ---------------------------------------------------------------------------
+
+cudaError_t pack_spinor(void* dst, const double* src, const Geom& g, int parity, int prec,
+                        cudaStream_t st);
+cudaError_t unpack_spinor(double* dst, const void* src, const Geom& g, int parity, int prec,
+                          cudaStream_t st);
+cudaError_t pack_gauge(void* dst, const double* src, const Geom& g, int prec, int recon,
+                       cudaStream_t st);
+// nh = 1 (one parity) or 2 (both halves, laid out even then odd)
+cudaError_t convert_spinor(void* dst, int dprec, const void* src, int sprec, const Geom& g,
+                           int nh, cudaStream_t st);
+cudaError_t norm2(double* res, const void* x, const Geom& g, int prec, int nh, cudaStream_t st);
+cudaError_t cdot(double* res, const void* x, const void* y, const Geom& g, int prec, int nh,
+                 cudaStream_t st);
+cudaError_t axpby(double a, const void* x, double b, void* y, const Geom& g, int prec, int nh,
+                  cudaStream_t st);
+
+}  // namespace wd

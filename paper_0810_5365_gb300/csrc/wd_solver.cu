@@ -1,0 +1,509 @@
+// Even-odd preconditioned, mixed-precision CG solver for D x = b.
+//
+// The paper's inverter is an even-odd preconditioned conjugate gradient built
+// from separate kernels (Dslash, Dslash^+, an FP64 dot product and BLAS-like
+// updates) with negligible host-device traffic (section "Wilson inverter:
+// Main features"; performance in its Fig. 2).  This file realises it as:
+//
+//  * Schur complement on the even sites:
+//      Mhat = 1 - kappa^2 H_eo H_oe,  bhat_e = b_e + kappa H_eo b_o,
+//      x_o = b_o + kappa H_oe x_e   (then D x = b exactly on the odd rows, and
+//      the even-row residual equals bhat_e - Mhat x_e);
+//  * CG on the normal equations Mhat^+ Mhat x_e = Mhat^+ bhat_e in the CGLS
+//    arrangement, which tracks r = bhat - Mhat x itself;
+//  * inner ("sloppy") iterations in FP32 or FP16 with FP64 reliable updates
+//    (Sleijpen and van der Vorst, Computing 56, 1996): every
+//    `reliable_interval` iterations, and whenever the sloppy residual looks
+//    converged, the sloppy solution is folded into an FP64 accumulator and
+//    the true residual is recomputed with the FP64 operator;
+//  * all CG scalars stay on the device; each block of `check_interval`
+//    iterations is one captured CUDA graph; the host reads four doubles per
+//    block to decide on convergence.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "wd_internal.h"
+
+namespace wd {
+
+struct CgScalars {
+  double gamma[2];  // ||s||^2, ping-pong between consecutive iterations
+  double qq;        // ||q||^2, q = Mhat p
+  double rr;        // ||r||^2 of the sloppy residual
+  double r64;       // ||bhat - Mhat x64||^2 (FP64)
+  double bnorm2;    // ||b||^2 of the full right-hand side
+  double res_e, res_o;  // ||b - D x||^2 on even / odd sites
+};
+
+// r -= alpha q ; rr = ||r||^2 ; alpha = gamma[kp] / qq
+template <int P, int BS>
+__global__ void __launch_bounds__(BS) cg_update_r(char* r, const char* __restrict__ q,
+                                                  CgScalars* sc, int kp, Geom g, RedScratch rs) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  const R alpha = (R)(sc->gamma[kp] / sc->qq);
+  double acc[1] = {0.0};
+  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+    cx<R> a[12], b[12];
+    load_spinor_rw<P, R>(a, r, cb, g.Vh_pad);
+    load_spinor_rw<P, R>(b, q, cb, g.Vh_pad);
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      a[k].r = fma(-alpha, b[k].r, a[k].r);
+      a[k].i = fma(-alpha, b[k].i, a[k].i);
+      t += (double)a[k].r * a[k].r + (double)a[k].i * a[k].i;
+    }
+    store_spinor<P, R>(r, cb, g.Vh_pad, a);
+    acc[0] += t;
+  }
+  double tot[1];
+  if (grid_reduce<1, BS>(acc, rs, tot) && threadIdx.x == 0) sc->rr = tot[0];
+}
+
+// x += alpha p ; p = s + beta p ; beta = gamma[1-kp] / gamma[kp]
+template <int P, int PX, int BS>
+__global__ void __launch_bounds__(BS) cg_update_xp(char* x, char* p, const char* __restrict__ s,
+                                                   const CgScalars* sc, int kp, Geom g) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  using RX = typename std::conditional<PX == WD_F64, double, float>::type;
+  const double g0 = sc->gamma[kp];
+  const RX alpha = (RX)(g0 / sc->qq);
+  const R beta = (R)(sc->gamma[1 - kp] / g0);
+  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+    cx<R> pv[12], sv[12];
+    cx<RX> xv[12];
+    load_spinor_rw<P, R>(pv, p, cb, g.Vh_pad);
+    load_spinor_rw<P, R>(sv, s, cb, g.Vh_pad);
+    load_spinor_rw<PX, RX>(xv, x, cb, g.Vh_pad);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      xv[k].r = fma(alpha, (RX)pv[k].r, xv[k].r);
+      xv[k].i = fma(alpha, (RX)pv[k].i, xv[k].i);
+      pv[k].r = fma(beta, pv[k].r, sv[k].r);
+      pv[k].i = fma(beta, pv[k].i, sv[k].i);
+    }
+    store_spinor<PX, RX>(x, cb, g.Vh_pad, xv);
+    store_spinor<P, R>(p, cb, g.Vh_pad, pv);
+  }
+}
+
+// x64 += xs ; xs = 0
+template <int PX, int BS>
+__global__ void __launch_bounds__(BS) ru_accumulate(char* x64, char* xs, Geom g) {
+  using RX = typename std::conditional<PX == WD_F64, double, float>::type;
+  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+    cx<double> a[12];
+    cx<RX> b[12];
+    load_spinor_rw<WD_F64, double>(a, x64, cb, g.Vh_pad);
+    load_spinor_rw<PX, RX>(b, xs, cb, g.Vh_pad);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      a[k].r += (double)b[k].r;
+      a[k].i += (double)b[k].i;
+      b[k] = mk<RX>(0, 0);
+    }
+    store_spinor<WD_F64, double>(x64, cb, g.Vh_pad, a);
+    store_spinor<PX, RX>(xs, cb, g.Vh_pad, b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+
+struct Workspace {
+  int dims[4] = {0, 0, 0, 0};
+  int sprec = -1, srecon = 0, orecon = 0;
+  Geom g{};
+  void* g64 = nullptr;   // FP64 gauge (outer_recon)
+  void* gs = nullptr;    // sloppy gauge (may alias g64)
+  void* b64 = nullptr;   // full FP64 rhs (even half, odd half)
+  void* x64 = nullptr;   // full FP64 solution
+  void* rf64 = nullptr;  // full FP64 residual b - D x
+  void* bhat = nullptr;  // even FP64
+  void* r64 = nullptr;   // even FP64
+  void* t64 = nullptr;   // odd FP64 temporary
+  void* p = nullptr;     // sloppy even fields
+  void* q = nullptr;
+  void* r = nullptr;
+  void* s = nullptr;
+  void* ts = nullptr;    // sloppy odd temporary
+  void* xs = nullptr;    // sloppy solution accumulator (FP32 for FP16 inner)
+  double* canon_spinor = nullptr;  // staging for host spinors
+  double* canon_gauge = nullptr;   // staging for a host gauge field
+  CgScalars* sc = nullptr;
+  CgScalars* sc_host = nullptr;    // pinned
+  cudaStream_t cap = nullptr;      // private capture stream
+};
+
+static Workspace& ws() {
+  static Workspace w;
+  return w;
+}
+
+static void ws_free() {
+  Workspace& w = ws();
+  void* bufs[] = {w.g64, w.b64, w.x64, w.rf64, w.bhat, w.r64, w.t64, w.p, w.q, w.r,
+                  w.s, w.ts, w.xs, w.canon_spinor, w.canon_gauge, w.sc};
+  if (w.gs && w.gs != w.g64) cudaFree(w.gs);
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (w.sc_host) cudaFreeHost(w.sc_host);
+  if (w.cap) cudaStreamDestroy(w.cap);
+  w = Workspace();
+}
+
+void solver_finalize() { ws_free(); }
+
+static int sloppy_x_prec(int sprec) { return sprec == WD_F64 ? WD_F64 : WD_F32; }
+
+#define WD_CK(call)                                        \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) {                               \
+      state().last_cuda_error = (int)e_;                   \
+      return WD_ERR_CUDA;                                  \
+    }                                                      \
+  } while (0)
+
+static int ws_ensure(const int dims[4], int sprec, int srecon, int orecon) {
+  Workspace& w = ws();
+  if (w.sc && std::memcmp(w.dims, dims, sizeof(w.dims)) == 0 && w.sprec == sprec &&
+      w.srecon == srecon && w.orecon == orecon)
+    return WD_OK;
+  cudaDeviceSynchronize();
+  ws_free();
+  Geom g = make_geom(dims);
+  std::memcpy(w.dims, dims, sizeof(w.dims));
+  w.sprec = sprec;
+  w.srecon = srecon;
+  w.orecon = orecon;
+  w.g = g;
+  size_t h64 = spinor_half_bytes(g, WD_F64), hs = spinor_half_bytes(g, sprec);
+  size_t hx = spinor_half_bytes(g, sloppy_x_prec(sprec));
+  WD_CK(cudaMalloc(&w.g64, gauge_bytes(g, WD_F64, orecon)));
+  if (sprec == WD_F64 && srecon == orecon)
+    w.gs = w.g64;
+  else
+    WD_CK(cudaMalloc(&w.gs, gauge_bytes(g, sprec, srecon)));
+  WD_CK(cudaMalloc(&w.b64, 2 * h64));
+  WD_CK(cudaMalloc(&w.x64, 2 * h64));
+  WD_CK(cudaMalloc(&w.rf64, 2 * h64));
+  WD_CK(cudaMalloc(&w.bhat, h64));
+  WD_CK(cudaMalloc(&w.r64, h64));
+  WD_CK(cudaMalloc(&w.t64, h64));
+  WD_CK(cudaMalloc(&w.p, hs));
+  WD_CK(cudaMalloc(&w.q, hs));
+  WD_CK(cudaMalloc(&w.r, hs));
+  WD_CK(cudaMalloc(&w.s, hs));
+  WD_CK(cudaMalloc(&w.ts, hs));
+  WD_CK(cudaMalloc(&w.xs, hx));
+  WD_CK(cudaMalloc(&w.sc, sizeof(CgScalars)));
+  WD_CK(cudaMemset(w.sc, 0, sizeof(CgScalars)));
+  WD_CK(cudaMallocHost(&w.sc_host, sizeof(CgScalars)));
+  WD_CK(cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
+  // the largest reduction grid used below is a dslash over Vh sites
+  WD_CK(ensure_scratch((size_t)((g.Vh + 127) / 128) * 2 + 1024));
+  return WD_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// the solve
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Ctx {
+  Workspace* w;
+  cudaStream_t st;
+  double kappa;
+  int sprec, srecon, orecon, xprec;
+  double dslash_calls = 0;
+};
+
+cudaError_t dsl(Ctx& c, int prec, int recon, const void* gauge, void* out, const void* in,
+                int parity, int dagger, double a, const void* x, double bx, const void* y,
+                double cy, double* norm, cudaStream_t st) {
+  DslashArgs d;
+  d.out = out;
+  d.in = in;
+  d.gauge = gauge;
+  d.x = x;
+  d.y = y;
+  d.a = a;
+  d.bx = bx;
+  d.cy = cy;
+  d.norm_out = norm;
+  d.rs = scratch();
+  d.g = c.w->g;
+  d.parity = parity;
+  c.dslash_calls += 1;
+  return launch_dslash(prec, d, recon, dagger != 0, st);
+}
+
+// q = Mhat p (sloppy), with ||q||^2 -> sc->qq
+cudaError_t mhat_sloppy(Ctx& c, void* out, const void* in, int dagger, double* norm,
+                        cudaStream_t st) {
+  Workspace& w = *c.w;
+  cudaError_t e = dsl(c, c.sprec, c.srecon, w.gs, w.ts, in, WD_ODD, dagger, 1.0, nullptr, 0,
+                      nullptr, 0, nullptr, st);
+  if (e != cudaSuccess) return e;
+  return dsl(c, c.sprec, c.srecon, w.gs, out, w.ts, WD_EVEN, dagger, -c.kappa * c.kappa, in, 1.0,
+             nullptr, 0, norm, st);
+}
+
+template <int P, int PX>
+cudaError_t iteration_t(Ctx& c, int kp, cudaStream_t st) {
+  Workspace& w = *c.w;
+  const Geom& g = w.g;
+  cudaError_t e = mhat_sloppy(c, w.q, w.p, 0, &w.sc->qq, st);
+  if (e != cudaSuccess) return e;
+  int grid = blas_grid(g.Vh, 256);
+  cg_update_r<P, 256><<<grid, 256, 0, st>>>((char*)w.r, (const char*)w.q, w.sc, kp, g, scratch());
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = mhat_sloppy(c, w.s, w.r, 1, &w.sc->gamma[1 - kp], st);
+  if (e != cudaSuccess) return e;
+  cg_update_xp<P, PX, 256><<<grid, 256, 0, st>>>((char*)w.xs, (char*)w.p, (const char*)w.s, w.sc,
+                                                  kp, g);
+  return cudaGetLastError();
+}
+
+cudaError_t iteration(Ctx& c, int kp, cudaStream_t st) {
+  switch (c.sprec) {
+    case WD_F64: return iteration_t<WD_F64, WD_F64>(c, kp, st);
+    case WD_F32: return iteration_t<WD_F32, WD_F32>(c, kp, st);
+    case WD_F16: return iteration_t<WD_F16, WD_F32>(c, kp, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// fold xs into x64 (even half), recompute r64 = bhat - Mhat x64 in FP64, and
+// restart the sloppy recurrences: r = r64, s = Mhat^+ r, p = s, gamma[0] = ||s||^2
+cudaError_t reliable_update(Ctx& c, bool accumulate, cudaStream_t st) {
+  Workspace& w = *c.w;
+  const Geom& g = w.g;
+  cudaError_t e;
+  if (accumulate) {
+    int grid = blas_grid(g.Vh, 256);
+    if (c.xprec == WD_F64)
+      ru_accumulate<WD_F64, 256><<<grid, 256, 0, st>>>((char*)w.x64, (char*)w.xs, g);
+    else
+      ru_accumulate<WD_F32, 256><<<grid, 256, 0, st>>>((char*)w.x64, (char*)w.xs, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // t64 = H_oe x64_e ; r64 = kappa^2 H_eo t64 - x64_e + bhat
+  e = dsl(c, WD_F64, c.orecon, w.g64, w.t64, w.x64, WD_ODD, 0, 1.0, nullptr, 0, nullptr, 0,
+          nullptr, st);
+  if (e != cudaSuccess) return e;
+  e = dsl(c, WD_F64, c.orecon, w.g64, w.r64, w.t64, WD_EVEN, 0, c.kappa * c.kappa, w.x64, -1.0,
+          w.bhat, 1.0, &w.sc->r64, st);
+  if (e != cudaSuccess) return e;
+  if ((e = convert_spinor(w.r, c.sprec, w.r64, WD_F64, g, 1, st)) != cudaSuccess) return e;
+  e = mhat_sloppy(c, w.s, w.r, 1, &w.sc->gamma[0], st);
+  if (e != cudaSuccess) return e;
+  return convert_spinor(w.p, c.sprec, w.s, c.sprec, g, 1, st);
+}
+
+cudaError_t read_scalars(Ctx& c) {
+  Workspace& w = *c.w;
+  cudaError_t e = cudaMemcpyAsync(w.sc_host, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c.st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c.st);
+}
+
+}  // namespace
+
+int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
+               const wd_solve_params* prm, wd_solve_info* info) {
+  auto t0 = std::chrono::steady_clock::now();
+  wd_solve_params P;
+  wd_solve_params_default(&P);
+  if (prm) P = *prm;
+  wd_solve_info I;
+  std::memset(&I, 0, sizeof(I));
+  if (P.inner_prec < WD_F64 || P.inner_prec > WD_F16) return WD_ERR_PREC;
+  if (link_bytes(P.inner_prec, P.inner_recon) == 0 || link_bytes(WD_F64, P.outer_recon) == 0)
+    return WD_ERR_PREC;
+  if (!(P.tol > 0) || P.maxiter < 0 || P.reliable_interval < 1) return WD_ERR_ARG;
+  int chunk = P.check_interval < 2 ? 2 : (P.check_interval & ~1);
+
+  int rc = ws_ensure(dims, P.inner_prec, P.inner_recon, P.outer_recon);
+  if (rc != WD_OK) return rc;
+  Workspace& w = ws();
+  const Geom& g = w.g;
+  Ctx c;
+  c.w = &w;
+  c.st = state().stream;
+  c.kappa = kappa;
+  c.sprec = P.inner_prec;
+  c.srecon = P.inner_recon;
+  c.orecon = P.outer_recon;
+  c.xprec = sloppy_x_prec(P.inner_prec);
+  cudaStream_t st = c.st;
+  const size_t V = 2 * (size_t)g.Vh;
+  const size_t h64 = spinor_half_bytes(g, WD_F64);
+  char* b_e = (char*)w.b64;
+  char* b_o = b_e + h64;
+  char* x_e = (char*)w.x64;
+  char* x_o = x_e + h64;
+
+  // ---- stage and pack the inputs ----
+  const double* bdev = b;
+  if (!is_device_ptr(b)) {
+    if (!w.canon_spinor) WD_CK(cudaMalloc(&w.canon_spinor, V * 24 * sizeof(double)));
+    WD_CK(cudaMemcpyAsync(w.canon_spinor, b, V * 24 * sizeof(double), cudaMemcpyHostToDevice, st));
+    bdev = w.canon_spinor;
+  }
+  const double* gdev = gauge;
+  if (!is_device_ptr(gauge)) {
+    if (!w.canon_gauge) WD_CK(cudaMalloc(&w.canon_gauge, 4 * V * 18 * sizeof(double)));
+    WD_CK(cudaMemcpyAsync(w.canon_gauge, gauge, 4 * V * 18 * sizeof(double),
+                          cudaMemcpyHostToDevice, st));
+    gdev = w.canon_gauge;
+  }
+  WD_CK(pack_gauge(w.g64, gdev, g, WD_F64, P.outer_recon, st));
+  if (w.gs != w.g64) WD_CK(pack_gauge(w.gs, gdev, g, P.inner_prec, P.inner_recon, st));
+  WD_CK(pack_spinor(w.b64, bdev, g, WD_FULL, WD_F64, st));
+  WD_CK(norm2(&w.sc->bnorm2, w.b64, g, WD_F64, 2, st));
+  const bool x_dev = is_device_ptr(x);
+  if (P.use_initial_guess) {
+    const double* xdev = x;
+    if (!x_dev) {
+      if (!w.canon_spinor) WD_CK(cudaMalloc(&w.canon_spinor, V * 24 * sizeof(double)));
+      WD_CK(cudaMemcpyAsync(w.canon_spinor, x, V * 24 * sizeof(double), cudaMemcpyHostToDevice, st));
+      xdev = w.canon_spinor;
+    }
+    WD_CK(pack_spinor(w.x64, xdev, g, WD_FULL, WD_F64, st));
+  } else {
+    WD_CK(cudaMemsetAsync(w.x64, 0, 2 * h64, st));
+  }
+  WD_CK(cudaMemsetAsync(w.xs, 0, spinor_half_bytes(g, c.xprec), st));
+  // bhat_e = b_e + kappa H_eo b_o
+  WD_CK(dsl(c, WD_F64, c.orecon, w.g64, w.bhat, b_o, WD_EVEN, 0, kappa, b_e, 1.0, nullptr, 0,
+            nullptr, st));
+  WD_CK(reliable_update(c, false, st));
+  WD_CK(read_scalars(c));
+  int ru = 0;
+  const double bnorm = std::sqrt(w.sc_host->bnorm2);
+  if (!(bnorm > 0) || !std::isfinite(bnorm)) {
+    // b = 0 gives x = 0; a non-finite b is an error
+    if (!std::isfinite(bnorm)) return WD_ERR_NONFINITE;
+  }
+  double target = P.tol * bnorm * 0.9;
+  int status = WD_ERR_NOCONV;
+  int iters = 0, last_ru = 0;
+  int reliable_interval = P.inner_prec == WD_F64 ? 0x7fffffff : P.reliable_interval;
+
+  // ---- the iteration graph ----
+  cudaGraphExec_t exec = nullptr;
+  if (P.use_graph) {
+    cudaGraph_t graph = nullptr;
+    WD_CK(cudaStreamBeginCapture(w.cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < chunk && ce == cudaSuccess; k++) ce = iteration(c, k & 1, w.cap);
+    cudaError_t ee = cudaStreamEndCapture(w.cap, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      state().last_cuda_error = (int)(ce != cudaSuccess ? ce : ee);
+      return WD_ERR_CUDA;
+    }
+    c.dslash_calls -= 4.0 * chunk;  // captured, not yet run
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      state().last_cuda_error = (int)ie;
+      return WD_ERR_CUDA;
+    }
+  }
+
+  double r64 = std::sqrt(w.sc_host->r64);
+  bool converged = !(bnorm > 0) || r64 <= target;
+  while (!converged) {
+    if (!std::isfinite(w.sc_host->r64) || !std::isfinite(w.sc_host->gamma[0])) {
+      status = WD_ERR_NONFINITE;
+      break;
+    }
+    if (iters >= P.maxiter) break;
+    if (!(w.sc_host->gamma[0] > 0)) {
+      status = WD_ERR_BREAKDOWN;
+      break;
+    }
+    // one block of iterations
+    if (exec) {
+      cudaError_t e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) { state().last_cuda_error = (int)e; status = WD_ERR_CUDA; break; }
+      c.dslash_calls += 4.0 * chunk;
+    } else {
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < chunk && e == cudaSuccess; k++) e = iteration(c, k & 1, st);
+      if (e != cudaSuccess) { state().last_cuda_error = (int)e; status = WD_ERR_CUDA; break; }
+    }
+    iters += chunk;
+    if (read_scalars(c) != cudaSuccess) { status = WD_ERR_CUDA; break; }
+    const double rr = w.sc_host->rr;
+    if (!std::isfinite(rr) || !std::isfinite(w.sc_host->gamma[0])) {
+      status = WD_ERR_NONFINITE;
+      break;
+    }
+    if (!(w.sc_host->qq > 0)) {
+      status = WD_ERR_BREAKDOWN;
+      break;
+    }
+    const bool looks_done = std::sqrt(rr) <= target;
+    if (looks_done || iters - last_ru >= reliable_interval || iters >= P.maxiter) {
+      cudaError_t e = reliable_update(c, true, st);
+      if (e == cudaSuccess) e = read_scalars(c);
+      if (e != cudaSuccess) { state().last_cuda_error = (int)e; status = WD_ERR_CUDA; break; }
+      ru++;
+      last_ru = iters;
+      r64 = std::sqrt(w.sc_host->r64);
+      if (!std::isfinite(r64)) { status = WD_ERR_NONFINITE; break; }
+      if (r64 <= target) converged = true;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (converged) status = WD_OK;
+  if (status == WD_ERR_CUDA) return status;
+
+  // ---- reconstruct the odd sites and measure the true residual ----
+  // x_o = b_o + kappa H_oe x_e
+  WD_CK(dsl(c, WD_F64, c.orecon, w.g64, x_o, x_e, WD_ODD, 0, kappa, b_o, 1.0, nullptr, 0, nullptr, st));
+  char* rf_e = (char*)w.rf64;
+  char* rf_o = rf_e + h64;
+  // r_e = kappa H_eo x_o + b_e - x_e ; r_o = kappa H_oe x_e + b_o - x_o
+  WD_CK(dsl(c, WD_F64, c.orecon, w.g64, rf_e, x_o, WD_EVEN, 0, kappa, b_e, 1.0, x_e, -1.0,
+            &w.sc->res_e, st));
+  WD_CK(dsl(c, WD_F64, c.orecon, w.g64, rf_o, x_e, WD_ODD, 0, kappa, b_o, 1.0, x_o, -1.0,
+            &w.sc->res_o, st));
+  // ---- unpack the solution ----
+  double* xdev = x_dev ? x : w.canon_spinor;
+  if (!x_dev && !w.canon_spinor) WD_CK(cudaMalloc(&w.canon_spinor, V * 24 * sizeof(double)));
+  xdev = x_dev ? x : w.canon_spinor;
+  WD_CK(unpack_spinor(xdev, w.x64, g, WD_FULL, WD_F64, st));
+  if (!x_dev)
+    WD_CK(cudaMemcpyAsync(x, xdev, V * 24 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WD_CK(read_scalars(c));
+  double rel = bnorm > 0 ? std::sqrt(w.sc_host->res_e + w.sc_host->res_o) / bnorm : 0.0;
+  if (status == WD_OK && !(rel <= P.tol)) status = WD_ERR_NOCONV;
+
+  I.iters = iters;
+  I.reliable_updates = ru;
+  I.status = status;
+  I.true_residual = rel;
+  I.dslash_calls = c.dslash_calls;
+  I.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = I;
+  return status;
+}
+
+}  // namespace wd

@@ -1,0 +1,267 @@
+"""Python binding of libwd: the same entry points as include/wd.h, by ctypes.
+
+Argument marshalling only.  Buffers may be torch tensors (their data_ptr()
+is passed), raw integer addresses, or numpy arrays (host pointers, accepted
+where the C entry point accepts host memory, i.e. ``wd_solve``/``wd_solve_ex``).
+Every step of the computation runs inside libwd's CUDA kernels; if the
+library has not been built, importing functions from here raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB
+
+WD_F64, WD_F32, WD_F16 = 0, 1, 2
+WD_EVEN, WD_ODD, WD_FULL = 0, 1, -1
+
+WD_OK = 0
+WD_ERR_NULL = 1
+WD_ERR_DIMS = 2
+WD_ERR_PREC = 3
+WD_ERR_ALIGN = 4
+WD_ERR_ALIAS = 5
+WD_ERR_NOCONV = 6
+WD_ERR_NONFINITE = 7
+WD_ERR_TIMEOUT = 8
+WD_ERR_CUDA = 9
+WD_ERR_ARG = 10
+WD_ERR_BREAKDOWN = 11
+
+# every function declared in include/wd.h
+EXPORTS = [
+    "wd_set_stream", "wd_get_stream", "wd_error_string", "wd_last_cuda_error", "wd_finalize",
+    "wd_spinor_bytes", "wd_gauge_bytes", "wd_pack_gauge", "wd_pack_spinor", "wd_unpack_spinor",
+    "wd_convert_spinor", "wd_dslash", "wd_dslash_dag", "wd_dslash_ex", "wd_mhat", "wd_norm2",
+    "wd_cdot", "wd_axpby", "wd_solve_params_default", "wd_solve", "wd_solve_ex",
+]
+
+
+class WdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.wd_error_string(status).decode() if _lib is not None else str(status)
+        if status == WD_ERR_CUDA and _lib is not None:
+            msg += f" (cudaError {_lib.wd_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+
+
+class wd_solve_params(C.Structure):
+    _fields_ = [("inner_prec", C.c_int), ("inner_recon", C.c_int), ("outer_recon", C.c_int),
+                ("reliable_interval", C.c_int), ("check_interval", C.c_int),
+                ("maxiter", C.c_int), ("use_graph", C.c_int), ("use_initial_guess", C.c_int),
+                ("tol", C.c_double)]
+
+
+class wd_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("reliable_updates", C.c_int), ("status", C.c_int),
+                ("true_residual", C.c_double), ("seconds", C.c_double),
+                ("dslash_calls", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libwd.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"libwd is not built ({LIB} missing): run __graft_entry__.build() "
+                           "on a machine with nvcc; there is no fallback implementation")
+    L = C.CDLL(LIB)
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.c_void_p
+    i4 = C.c_int * 4
+    sig = {
+        "wd_set_stream": (C.c_int, [vp]),
+        "wd_get_stream": (vp, []),
+        "wd_error_string": (C.c_char_p, [C.c_int]),
+        "wd_last_cuda_error": (C.c_int, []),
+        "wd_finalize": (None, []),
+        "wd_spinor_bytes": (C.c_size_t, [i4, C.c_int, C.c_int]),
+        "wd_gauge_bytes": (C.c_size_t, [i4, C.c_int, C.c_int]),
+        "wd_pack_gauge": (C.c_int, [vp, dp, i4, C.c_int, C.c_int]),
+        "wd_pack_spinor": (C.c_int, [vp, dp, i4, C.c_int, C.c_int]),
+        "wd_unpack_spinor": (C.c_int, [dp, vp, i4, C.c_int, C.c_int]),
+        "wd_convert_spinor": (C.c_int, [vp, C.c_int, vp, C.c_int, i4, C.c_int]),
+        "wd_dslash": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, i4, C.c_int]),
+        "wd_dslash_dag": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, i4, C.c_int]),
+        "wd_dslash_ex": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
+                                   vp, C.c_double, dp, i4, C.c_int, C.c_int]),
+        "wd_mhat": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_int, i4, C.c_int, C.c_int]),
+        "wd_norm2": (C.c_int, [dp, vp, i4, C.c_int, C.c_int]),
+        "wd_cdot": (C.c_int, [dp, vp, vp, i4, C.c_int, C.c_int]),
+        "wd_axpby": (C.c_int, [C.c_double, vp, C.c_double, vp, i4, C.c_int, C.c_int]),
+        "wd_solve_params_default": (None, [C.POINTER(wd_solve_params)]),
+        "wd_solve": (C.c_int, [dp, dp, dp, C.c_double, C.c_double, i4]),
+        "wd_solve_ex": (C.c_int, [dp, dp, dp, C.c_double, i4, C.POINTER(wd_solve_params),
+                                  C.POINTER(wd_solve_info)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _p(t):
+    """Address of a buffer: torch tensor, numpy array, int or None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    raise TypeError(f"cannot take the address of {type(t)}")
+
+
+def _d(dims):
+    return (C.c_int * 4)(*[int(v) for v in dims])
+
+
+def _ck(rc, where):
+    if rc != WD_OK:
+        raise WdError(rc, where)
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names and argument order as include/wd.h)
+# ---------------------------------------------------------------------------
+
+def wd_set_stream(stream=None):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t address, or None."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _ck(lib().wd_set_stream(stream), "wd_set_stream")
+
+
+def wd_get_stream():
+    return lib().wd_get_stream()
+
+
+def wd_error_string(status):
+    return lib().wd_error_string(int(status)).decode()
+
+
+def wd_last_cuda_error():
+    return lib().wd_last_cuda_error()
+
+
+def wd_finalize():
+    lib().wd_finalize()
+
+
+def wd_spinor_bytes(dims, parity, prec):
+    return int(lib().wd_spinor_bytes(_d(dims), int(parity), int(prec)))
+
+
+def wd_gauge_bytes(dims, prec, recon=12):
+    return int(lib().wd_gauge_bytes(_d(dims), int(prec), int(recon)))
+
+
+def wd_pack_gauge(dst, src_canonical, dims, prec, recon=12):
+    _ck(lib().wd_pack_gauge(_p(dst), _p(src_canonical), _d(dims), int(prec), int(recon)),
+        "wd_pack_gauge")
+
+
+def wd_pack_spinor(dst, src_canonical, dims, parity, prec):
+    _ck(lib().wd_pack_spinor(_p(dst), _p(src_canonical), _d(dims), int(parity), int(prec)),
+        "wd_pack_spinor")
+
+
+def wd_unpack_spinor(dst_canonical, src, dims, parity, prec):
+    _ck(lib().wd_unpack_spinor(_p(dst_canonical), _p(src), _d(dims), int(parity), int(prec)),
+        "wd_unpack_spinor")
+
+
+def wd_convert_spinor(dst, dst_prec, src, src_prec, dims, parity):
+    _ck(lib().wd_convert_spinor(_p(dst), int(dst_prec), _p(src), int(src_prec), _d(dims),
+                                int(parity)), "wd_convert_spinor")
+
+
+def wd_dslash(out, inp, gauge, kappa, parity, dims, prec):
+    _ck(lib().wd_dslash(_p(out), _p(inp), _p(gauge), float(kappa), int(parity), _d(dims),
+                        int(prec)), "wd_dslash")
+
+
+def wd_dslash_dag(out, inp, gauge, kappa, parity, dims, prec):
+    _ck(lib().wd_dslash_dag(_p(out), _p(inp), _p(gauge), float(kappa), int(parity), _d(dims),
+                            int(prec)), "wd_dslash_dag")
+
+
+def wd_dslash_ex(out, inp, gauge, parity, dagger, a, x, bx, y, cy, norm2, dims, prec, recon=12):
+    _ck(lib().wd_dslash_ex(_p(out), _p(inp), _p(gauge), int(parity), int(dagger), float(a),
+                           _p(x), float(bx), _p(y), float(cy), _p(norm2), _d(dims), int(prec),
+                           int(recon)), "wd_dslash_ex")
+
+
+def wd_mhat(out, inp, gauge, tmp, kappa, dagger, dims, prec, recon=12):
+    _ck(lib().wd_mhat(_p(out), _p(inp), _p(gauge), _p(tmp), float(kappa), int(dagger), _d(dims),
+                      int(prec), int(recon)), "wd_mhat")
+
+
+def wd_norm2(result, x, dims, parity, prec):
+    _ck(lib().wd_norm2(_p(result), _p(x), _d(dims), int(parity), int(prec)), "wd_norm2")
+
+
+def wd_cdot(result, x, y, dims, parity, prec):
+    _ck(lib().wd_cdot(_p(result), _p(x), _p(y), _d(dims), int(parity), int(prec)), "wd_cdot")
+
+
+def wd_axpby(a, x, b, y, dims, parity, prec):
+    _ck(lib().wd_axpby(float(a), _p(x), float(b), _p(y), _d(dims), int(parity), int(prec)),
+        "wd_axpby")
+
+
+def wd_solve_params_default():
+    p = wd_solve_params()
+    lib().wd_solve_params_default(C.byref(p))
+    return p
+
+
+def wd_solve(x, b, gauge, kappa, tol, dims):
+    _ck(lib().wd_solve(_p(x), _p(b), _p(gauge), float(kappa), float(tol), _d(dims)), "wd_solve")
+
+
+def wd_solve_ex(x, b, gauge, kappa, dims, params=None, check=True):
+    """Returns the wd_solve_info as a dict (status included); raises on a
+    non-zero status unless check=False."""
+    info = wd_solve_info()
+    p = params if params is not None else wd_solve_params_default()
+    rc = lib().wd_solve_ex(_p(x), _p(b), _p(gauge), float(kappa), _d(dims), C.byref(p),
+                           C.byref(info))
+    out = info.as_dict()
+    out["status"] = rc
+    if check:
+        _ck(rc, "wd_solve_ex")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# buffer helpers (torch owns the memory; sizes come from libwd)
+# ---------------------------------------------------------------------------
+
+def alloc_spinor(dims, parity, prec, device="cuda"):
+    """Uninitialised packed spinor buffer (torch uint8 tensor)."""
+    import torch
+    n = wd_spinor_bytes(dims, parity, prec)
+    if n == 0:
+        raise WdError(WD_ERR_ARG, "alloc_spinor")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def alloc_gauge(dims, prec, recon=12, device="cuda"):
+    """Uninitialised packed gauge buffer (torch uint8 tensor)."""
+    import torch
+    n = wd_gauge_bytes(dims, prec, recon)
+    if n == 0:
+        raise WdError(WD_ERR_PREC, "alloc_gauge")
+    return torch.empty(n, dtype=torch.uint8, device=device)

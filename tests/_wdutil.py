@@ -1,0 +1,52 @@
+"""Helpers for the GPU tests: move canonical numpy fields through libwd's
+pack/unpack entry points (argument marshalling only)."""
+import numpy as np
+import torch
+
+import paper_0810_5365_gb300 as W
+
+PREC_TOL = {W.WD_F64: 1e-13, W.WD_F32: 1e-6, W.WD_F16: 5e-3}
+PREC_NAME = {W.WD_F64: "f64", W.WD_F32: "f32", W.WD_F16: "f16"}
+
+
+def dev(a):
+    """complex128 numpy array -> contiguous float64 CUDA tensor (same bytes)."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return torch.from_numpy(a.view(np.float64).copy()).cuda()
+
+
+def host(t, shape):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(np.complex128).reshape(shape)
+
+
+def pack_spinor(psi, dims, parity, prec):
+    buf = W.alloc_spinor(dims, parity, prec)
+    src = dev(psi)
+    W.wd_pack_spinor(buf, src, dims, parity, prec)
+    torch.cuda.synchronize()
+    return buf
+
+
+def unpack_spinor(buf, dims, parity, prec):
+    V = int(np.prod(dims))
+    n = V if parity == W.WD_FULL else V // 2
+    out = torch.empty(n * 24, dtype=torch.float64, device="cuda")
+    W.wd_unpack_spinor(out, buf, dims, parity, prec)
+    return host(out, (n, 4, 3))
+
+
+def pack_gauge(U, dims, prec, recon):
+    buf = W.alloc_gauge(dims, prec, recon)
+    W.wd_pack_gauge(buf, dev(U), dims, prec, recon)
+    torch.cuda.synchronize()
+    return buf
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rel_max(a, b):
+    """largest elementwise error relative to the largest reference magnitude"""
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
