@@ -168,7 +168,7 @@ def cpu_baseline(U, psi, dims, budget_s=12.0):
     oracle.set_threads(cores)
     Vh = int(np.prod(dims)) // 2
     n, t = 0, 0.0
-    while t < budget_s and n < 50:
+    while t < budget_s and n < 400:
         t0 = time.perf_counter()
         oracle.hop(psi, U, dims, dagger=False, out_parity=0)
         t += time.perf_counter() - t0
