@@ -78,7 +78,8 @@ enum {
     WD_ERR_TIMEOUT = 8,    /* a bounded device-side wait gave up */
     WD_ERR_CUDA = 9,       /* a CUDA runtime call failed */
     WD_ERR_ARG = 10,       /* another argument is out of range */
-    WD_ERR_BREAKDOWN = 11  /* Krylov breakdown (p^+ A p <= 0) */
+    WD_ERR_BREAKDOWN = 11, /* Krylov breakdown (p^+ A p <= 0) */
+    WD_ERR_SCRATCH = 12    /* lattice too large for wd_dslash_ex_noalloc's fixed scratch */
 };
 
 /* ------------------------------------------------------------------ */
@@ -159,6 +160,36 @@ int wd_dslash_dag(void *out, const void *in, const void *gauge, double kappa,
 int wd_dslash_ex(void *out, const void *in, const void *gauge, int parity, int dagger,
                  double a, const void *x, double bx, const void *y, double cy,
                  double *norm2, const int dims[4], int prec, int recon);
+
+/*
+ * wd_dslash_ex_noalloc: wd_dslash_ex (same arguments, same results) for
+ * callers that cannot let the library allocate device memory.  The paper has
+ * no counterpart; this is an interface addition.
+ *
+ * Who needs it: code that records its launches into a CUDA graph by stream
+ * capture (allocating during a capture is not allowed), applications whose
+ * device memory is owned by another allocator (e.g. a framework's caching
+ * allocator that has reserved the GPU), and latency-critical loops that must
+ * not hit the device-wide synchronisation of cudaMalloc/cudaFree.
+ * wd_dslash_ex may allocate its reduction scratch on first use or when a
+ * larger lattice needs more; this variant never calls cudaMalloc, cudaFree or
+ * any allocating routine.
+ *
+ * Its reduction scratch is a fixed array compiled into libwd (16384 FP64
+ * partial sums plus a counter, about 128 KB), held by every GPU that loads
+ * the library until the process exits.  Limit: V/2 <= 2,097,152 sites
+ * (16384 CTAs of 128 sites); larger lattices return WD_ERR_SCRATCH before
+ * any work is queued.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and it keeps
+ * the last call's contents: each call clears the counter itself (an
+ * asynchronous memset on the stream) when norm2 != NULL.  Calls that overlap
+ * on the GPU (several streams, or several host threads) race on the array.
+ */
+int wd_dslash_ex_noalloc(void *out, const void *in, const void *gauge, int parity,
+                         int dagger, double a, const void *x, double bx, const void *y,
+                         double cy, double *norm2, const int dims[4], int prec, int recon);
 
 /*
  * Even-odd preconditioned operator on the even sub-lattice (paper Fig. 1):

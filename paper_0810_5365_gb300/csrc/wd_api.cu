@@ -68,6 +68,9 @@ const char* wd_error_string(int status) {
     case WD_ERR_CUDA: return "WD_ERR_CUDA: a CUDA runtime call failed";
     case WD_ERR_ARG: return "WD_ERR_ARG: argument out of range";
     case WD_ERR_BREAKDOWN: return "WD_ERR_BREAKDOWN: Krylov breakdown";
+    case WD_ERR_SCRATCH:
+      return "WD_ERR_SCRATCH: lattice exceeds the fixed scratch of wd_dslash_ex_noalloc "
+             "(V/2 <= 2097152 sites)";
   }
   return "unknown status";
 }

@@ -28,6 +28,7 @@ WD_ERR_TIMEOUT = 8
 WD_ERR_CUDA = 9
 WD_ERR_ARG = 10
 WD_ERR_BREAKDOWN = 11
+WD_ERR_SCRATCH = 12
 
 # every function declared in include/wd.h
 EXPORTS = [
@@ -35,6 +36,7 @@ EXPORTS = [
     "wd_spinor_bytes", "wd_gauge_bytes", "wd_pack_gauge", "wd_pack_spinor", "wd_unpack_spinor",
     "wd_convert_spinor", "wd_dslash", "wd_dslash_dag", "wd_dslash_ex", "wd_mhat", "wd_norm2",
     "wd_cdot", "wd_axpby", "wd_solve_params_default", "wd_solve", "wd_solve_ex",
+    "wd_dslash_ex_noalloc",
 ]
 
 
@@ -93,6 +95,9 @@ def lib():
         "wd_dslash_dag": (C.c_int, [vp, vp, vp, C.c_double, C.c_int, i4, C.c_int]),
         "wd_dslash_ex": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
                                    vp, C.c_double, dp, i4, C.c_int, C.c_int]),
+        "wd_dslash_ex_noalloc": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp,
+                                           C.c_double, vp, C.c_double, dp, i4, C.c_int,
+                                           C.c_int]),
         "wd_mhat": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_int, i4, C.c_int, C.c_int]),
         "wd_norm2": (C.c_int, [dp, vp, i4, C.c_int, C.c_int]),
         "wd_cdot": (C.c_int, [dp, vp, vp, i4, C.c_int, C.c_int]),
@@ -201,6 +206,17 @@ def wd_dslash_ex(out, inp, gauge, parity, dagger, a, x, bx, y, cy, norm2, dims, 
     _ck(lib().wd_dslash_ex(_p(out), _p(inp), _p(gauge), int(parity), int(dagger), float(a),
                            _p(x), float(bx), _p(y), float(cy), _p(norm2), _d(dims), int(prec),
                            int(recon)), "wd_dslash_ex")
+
+
+def wd_dslash_ex_noalloc(out, inp, gauge, parity, dagger, a, x, bx, y, cy, norm2, dims, prec,
+                         recon=12):
+    """wd_dslash_ex without any device allocation (fixed scratch inside libwd;
+    V/2 <= 2,097,152 sites).  For callers that cannot let the library call
+    cudaMalloc: stream-capturing code, foreign-allocator applications,
+    latency-critical loops."""
+    _ck(lib().wd_dslash_ex_noalloc(_p(out), _p(inp), _p(gauge), int(parity), int(dagger),
+                                   float(a), _p(x), float(bx), _p(y), float(cy), _p(norm2),
+                                   _d(dims), int(prec), int(recon)), "wd_dslash_ex_noalloc")
 
 
 def wd_mhat(out, inp, gauge, tmp, kappa, dagger, dims, prec, recon=12):

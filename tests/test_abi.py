@@ -97,7 +97,7 @@ def test_null_alias_align_parity(W):
 
 
 def test_error_strings(W):
-    for s in range(12):
+    for s in range(13):
         assert W.wd_error_string(s).startswith("WD_")
     assert W.wd_error_string(999) == "unknown status"
 
