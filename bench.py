@@ -45,7 +45,7 @@ def dslash_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0810_5365_gb300", "csrc")
     for f in ("wd_common.cuh", "wd_dslash.cuh", "wd_internal.h", "wd_dslash_f32.cu",
-              "wd_dslash_f16.cu"):
+              "wd_dslash_f16.cu", "wd_dslash_f64.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -216,16 +216,18 @@ def run_reference(args, rank, world):
 # the GPU path
 # ---------------------------------------------------------------------------
 
-def time_dslash(W, torch, prec_id, gauge, bufs, dims, steps, warmup, stream):
+def time_dslash(W, torch, prec_id, recon, gauge, bufs, dims, steps, warmup, stream):
     """K back-to-back parity dslash launches (ping-pong), CUDA events on the
     launching stream.  Returns elapsed seconds."""
     a, b = bufs
 
     def step(k):
         if k & 1:
-            W.wd_dslash(a, b, gauge, KAPPA, W.WD_ODD, dims, prec_id)
+            W.wd_dslash_ex(a, b, gauge, W.WD_ODD, 0, -KAPPA, None, 0.0, None, 0.0, None, dims,
+                           prec_id, recon)
         else:
-            W.wd_dslash(b, a, gauge, KAPPA, W.WD_EVEN, dims, prec_id)
+            W.wd_dslash_ex(b, a, gauge, W.WD_EVEN, 0, -KAPPA, None, 0.0, None, 0.0, None, dims,
+                           prec_id, recon)
 
     for k in range(warmup):
         step(k)
@@ -238,6 +240,67 @@ def time_dslash(W, torch, prec_id, gauge, bufs, dims, steps, warmup, stream):
     e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / 1e3
+
+
+SOLVE_DIMS = (24, 24, 24, 48)
+SOLVE_KAPPA = 0.1370
+
+
+def solve_section(W, torch, reps=3):
+    """Time to a 1e-10 true residual on 24^3x48, kappa = 0.137: mixed
+    precision (FP16 / FP32 inner, FP64 reliable updates every 50) against
+    plain FP64 CG (the same even-odd CGLS, all FP64), on the same GPU.
+    Device-resident canonical inputs; one warm-up solve per precision; the
+    median of `reps` timed solves.  Also one solve from host (numpy) buffers
+    per precision, copies included."""
+    from synth import fields
+    dims = SOLVE_DIMS
+    U = fields.su3_links(dims)
+    b = fields.gaussian_spinor(dims, seed=2025)
+    Ud = torch.from_numpy(U.view(np.float64).reshape(-1)).cuda()
+    bd = torch.from_numpy(b.view(np.float64).reshape(-1)).cuda()
+    x = torch.zeros_like(bd)
+    xh = np.zeros_like(b)
+    out = {}
+    Vh = int(np.prod(dims)) // 2
+    for name, inner in (("f16", W.WD_F16), ("f32", W.WD_F32), ("f64", W.WD_F64)):
+        p = W.wd_solve_params_default()
+        p.inner_prec = inner
+        p.maxiter = 100000
+        runs = []
+        for r in range(reps + 1):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = W.wd_solve_ex(x, bd, Ud, SOLVE_KAPPA, dims, p, check=False)
+            torch.cuda.synchronize()
+            info["wall_s"] = time.perf_counter() - t0
+            if r > 0:
+                runs.append(info)
+        runs.sort(key=lambda d: d["wall_s"])
+        med = runs[len(runs) // 2]
+        xh[:] = 0
+        t0 = time.perf_counter()
+        ih = W.wd_solve_ex(xh, b, U, SOLVE_KAPPA, dims, p, check=False)
+        host_wall = time.perf_counter() - t0
+        out[name] = {
+            "wall_s": med["wall_s"], "iters": med["iters"],
+            "reliable_updates": med["reliable_updates"], "status": med["status"],
+            "true_residual": med["true_residual"],
+            "phase_s": {k: med[k] for k in ("setup_seconds", "iterate_seconds",
+                                             "reliable_seconds", "final_seconds")},
+            "dslash_calls": med["dslash_calls"],
+            "dslash_gflops_in_solve": FLOPS_PER_SITE * Vh * med["dslash_calls"]
+            / med["wall_s"] / 1e9,
+            "host_buffers_wall_s": host_wall, "host_buffers_status": ih["status"],
+            "all_wall_s": [d["wall_s"] for d in runs],
+        }
+    for name in ("f16", "f32"):
+        out[name]["speedup_vs_f64"] = out["f64"]["wall_s"] / out[name]["wall_s"]
+    out["config"] = {"dims": list(dims), "kappa": SOLVE_KAPPA, "tol": 1e-10,
+                     "rhs": "complex Gaussian (seed 2025)", "links": "eps=0.3, seed 1234",
+                     "reliable_interval": 50, "timing": f"median of {reps} after 1 warm-up"}
+    return out
 
 
 def run_ours(args, rank, world, local):
@@ -262,27 +325,31 @@ def run_ours(args, rank, world, local):
     results = {}
     peaks, peak_kind = measured_peaks()
     gauges = {}
+    variants = [("f32", W.WD_F32, 12, args.steps), ("f16", W.WD_F16, 12, args.steps),
+                ("f64", W.WD_F64, 18, max(1, args.steps // 8))]
+    if args.quick:
+        variants = variants[:1]
     with ClockSampler(local) as clk:
-        for name, pid in (("f32", W.WD_F32), ("f16", W.WD_F16)):
-            g = W.alloc_gauge(dims, pid, 12)
-            W.wd_pack_gauge(g, Ud, dims, pid, 12)
+        for name, pid, recon, steps in variants:
+            g = W.alloc_gauge(dims, pid, recon)
+            W.wd_pack_gauge(g, Ud, dims, pid, recon)
             a = W.alloc_spinor(dims, W.WD_ODD, pid)
             b = W.alloc_spinor(dims, W.WD_EVEN, pid)
             W.wd_pack_spinor(a, srcd, dims, W.WD_ODD, pid)
             W.wd_pack_spinor(b, srcd, dims, W.WD_EVEN, pid)
-            gauges[name] = (g, a, b, pid)
+            if name == "f32":
+                gauges[name] = (g, a, b, pid)
             if world > 1:
                 torch.distributed.barrier()
             torch.cuda.synchronize()
-            dt = time_dslash(W, torch, pid, g, (a, b), dims, args.steps, args.warmup, stream)
+            dt = time_dslash(W, torch, pid, recon, g, (a, b), dims, steps, args.warmup, stream)
             if world > 1:
                 t = torch.tensor([dt], dtype=torch.float64, device="cuda")
                 torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
                 dt = t.item()
                 torch.distributed.barrier()
-            results[name] = dt
-            if args.quick:
-                break
+            results[name] = (dt, steps)
+            del g, a, b
         # end to end through the C ABI with pinned host buffers
         g, a, b, pid = gauges["f32"]
         nb = W.wd_spinor_bytes(dims, W.WD_ODD, W.WD_F32)
@@ -308,15 +375,16 @@ def run_ours(args, rank, world, local):
         e1.synchronize()
         dt_e2e = e0.elapsed_time(e1) / 1e3
     clocks = clk.summary()
+    del gauges, g, a, b, Ud, srcd
+    torch.cuda.empty_cache()
 
-    dt = results["f32"]
-    gflops = FLOPS_PER_SITE * Vh * args.steps * world / dt / 1e9
-    launch_s = dt / args.steps
+    dt, steps = results["f32"]
+    gflops = FLOPS_PER_SITE * Vh * steps * world / dt / 1e9
+    launch_s = dt / steps
     achieved = BYTES_PER_SITE["f32"] * Vh / launch_s / 1e9
-    traffic = profiled_traffic("f32")
     line = {
         "metric": METRIC, "value": gflops, "unit": "Gflops", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": DATA,
         "config": {"workload": "even-odd dslash 32^3x64, FP32, 12-real links, kappa=0.1365, "
@@ -327,24 +395,30 @@ def run_ours(args, rank, world, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "dslash_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": profiled_traffic("f32"),
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                      "bytes_per_site": BYTES_PER_SITE["f32"]},
-        "gpu_launches": args.steps,
+        "gpu_launches": steps,
+        "variants": {},
     }
-    if "f16" in results:
-        d16 = results["f16"]
-        ach16 = BYTES_PER_SITE["f16"] * Vh / (d16 / args.steps) / 1e9
-        line["variants"] = {"f16": {
-            "value": FLOPS_PER_SITE * Vh * args.steps * world / d16 / 1e9, "unit": "Gflops",
-            "ms_per_step": 1e3 * d16 / args.steps, "dslash_gbs": ach16,
-            "frac": ach16 / peaks["hbm_gbs"], "bytes_per_site": BYTES_PER_SITE["f16"],
-            "traffic": profiled_traffic("f16")}}
-        line["gpu_launches"] += args.steps
+    for name in ("f16", "f64"):
+        if name not in results:
+            continue
+        d, st = results[name]
+        ach = BYTES_PER_SITE[name] * Vh / (d / st) / 1e9
+        line["variants"][name] = {
+            "value": FLOPS_PER_SITE * Vh * st * world / d / 1e9, "unit": "Gflops",
+            "steps": st, "ms_per_step": 1e3 * d / st, "dslash_gbs": ach,
+            "frac": ach / peaks["hbm_gbs"], "bytes_per_site": BYTES_PER_SITE[name],
+            "recon": 18 if name == "f64" else 12, "traffic": profiled_traffic(name)}
+        line["gpu_launches"] += st
     line["e2e"] = {"value": FLOPS_PER_SITE * Vh * k_e2e * world / dt_e2e / 1e9, "unit": "Gflops",
                    "steps": k_e2e, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
     line["gpu_launches"] += k_e2e
     line["clocks"] = clocks
+    if not args.no_solve and not args.quick:
+        line["solve"] = solve_section(W, torch)
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(U, psi, dims)
     if rank == 0:
@@ -361,7 +435,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--quick", action="store_true", help="FP32 only")
+    ap.add_argument("--quick", action="store_true", help="FP32 dslash only")
+    ap.add_argument("--no-solve", action="store_true", help="skip the 24^3x48 solver comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

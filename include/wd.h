@@ -240,6 +240,10 @@ typedef struct {
     double true_residual;    /* ||b - D x|| / ||b||, FP64 on the full lattice */
     double seconds;          /* wall time of the solve inside wd_solve_ex */
     double dslash_calls;     /* hopping applications issued (all precisions) */
+    double setup_seconds;    /* staging, packing, right-hand side, first residual */
+    double iterate_seconds;  /* inner iterations (graph launches + checks) */
+    double reliable_seconds; /* FP64 reliable updates inside the loop */
+    double final_seconds;    /* odd-site reconstruction, true residual, unpack */
 } wd_solve_info;
 
 /* Fill p with the defaults above (inner_prec WD_F32, recon 12 / 18). */

@@ -44,16 +44,22 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          out_dir: str | None = None, defines: tuple = ()) -> str:
+    """Compile and link libwd; returns the library path.  ``out_dir`` and
+    ``defines`` (e.g. ("WD_DSLASH_BS=256",)) build a variant elsewhere."""
+    out = out_dir or OUT
+    lib_path = os.path.join(out, "libwd.so")
+    os.makedirs(out, exist_ok=True)
+    dflags = [f"-D{d}" for d in defines]
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = _headers()
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + hdrs):
-            cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+            cmd = [cc, *ARCH, *FLAGS, *dflags, "-c", src, "-o", obj + ".tmp"]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             r = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,14 +73,14 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     n = jobs or min(len(srcs), os.cpu_count() or 1)
     with ThreadPoolExecutor(max_workers=max(1, n)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

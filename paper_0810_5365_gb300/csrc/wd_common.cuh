@@ -22,6 +22,32 @@ namespace wd {
 // or 1024-byte (FP64) fully coalesced request of 128-bit vectors.
 constexpr int SB = 32;
 
+// Exact division by an invariant d for 0 <= n < 2^31 by one 64-bit multiply
+// and a shift (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): with s = ceil(log2 d) and M = ceil(2^(32+s)/d),
+// floor(n/d) = (n * M) >> (32 + s), since the rounding error of M contributes
+// less than n / 2^(32+s) < 1/(2d).
+struct FastDiv {
+  unsigned long long M;
+  int shift;  // 32 + s
+  int d;
+};
+
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  int s = 0;
+  while ((1LL << s) < d) s++;
+  unsigned __int128 num = (unsigned __int128)1 << (32 + s);
+  f.M = (unsigned long long)((num + (unsigned)d - 1) / (unsigned)d);
+  f.shift = 32 + s;
+  f.d = d;
+  return f;
+}
+
+__host__ __device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+  return (int)(((unsigned long long)(unsigned)n * f.M) >> f.shift);
+}
+
 struct Geom {
   int L[4];    // extents
   int Lh0;     // L0 / 2
@@ -30,6 +56,7 @@ struct Geom {
   int S1;      // checkerboard stride of +y  (Lh0)
   int S2;      // checkerboard stride of +z  (Lh0 * L1)
   int S3;      // checkerboard stride of +t  (Lh0 * L1 * L2)
+  FastDiv dLh0, dL1, dL2;
 };
 
 inline Geom make_geom(const int d[4]) {
@@ -42,7 +69,22 @@ inline Geom make_geom(const int d[4]) {
   g.S1 = g.Lh0;
   g.S2 = g.Lh0 * d[1];
   g.S3 = g.Lh0 * d[1] * d[2];
+  g.dLh0 = make_fastdiv(g.Lh0);
+  g.dL1 = make_fastdiv(d[1]);
+  g.dL2 = make_fastdiv(d[2]);
   return g;
+}
+
+// Checkerboard site cb of parity p -> coordinates (x0..x3).
+__host__ __device__ __forceinline__ void cb_coords(int cb, int p, const Geom& g, int& x0, int& x1, int& x2,
+                                          int& x3) {
+  const int r0 = fdiv(cb, g.dLh0);
+  const int xh = cb - r0 * g.Lh0;
+  const int r1 = fdiv(r0, g.dL1);
+  x1 = r0 - r1 * g.L[1];
+  x3 = fdiv(r1, g.dL2);
+  x2 = r1 - x3 * g.L[2];
+  x0 = 2 * xh + ((p + x1 + x2 + x3) & 1);
 }
 
 // vector index of component group k (of NC) of checkerboard site cb

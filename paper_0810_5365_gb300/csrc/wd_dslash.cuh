@@ -45,45 +45,130 @@ __device__ __forceinline__ void project(const cx<R> (&p)[12], cx<R> (&h)[6]) {
   }
 }
 
-// Expansion of the transported half spinor t back to four spins, added to acc.
-template <int MU, int S, typename R>
-__device__ __forceinline__ void expand_add(cx<R> (&acc)[12], const cx<R> (&t)[6]) {
+// Expansion of the transported half spinor t back to four spins, scaled by
+// sc and added to acc (sc carries the FP16 site scale and the antiperiodic
+// sign; SC1 marks sc == 1 known at compile time).
+template <int MU, int S, bool SC1, typename R>
+__device__ __forceinline__ void expand_add(cx<R> (&acc)[12], const cx<R> (&t)[6], R sc) {
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    acc[c] = acc[c] + t[c];
-    acc[3 + c] = acc[3 + c] + t[3 + c];
-    if constexpr (MU == 0) {          // lower = (-S i t1, -S i t0)
-      acc[6 + c] = addS<-S>(acc[6 + c], ti(t[3 + c]));
-      acc[9 + c] = addS<-S>(acc[9 + c], ti(t[c]));
-    } else if constexpr (MU == 1) {   // lower = (-S t1, S t0)
-      acc[6 + c] = addS<-S>(acc[6 + c], t[3 + c]);
-      acc[9 + c] = addS<S>(acc[9 + c], t[c]);
-    } else if constexpr (MU == 2) {   // lower = (-S i t0, S i t1)
-      acc[6 + c] = addS<-S>(acc[6 + c], ti(t[c]));
-      acc[9 + c] = addS<S>(acc[9 + c], ti(t[3 + c]));
-    } else {                          // lower = (-S t0, -S t1)
-      acc[6 + c] = addS<-S>(acc[6 + c], t[c]);
-      acc[9 + c] = addS<-S>(acc[9 + c], t[3 + c]);
+    if constexpr (SC1) {
+      acc[c] = acc[c] + t[c];
+      acc[3 + c] = acc[3 + c] + t[3 + c];
+      if constexpr (MU == 0) {          // lower = (-S i t1, -S i t0)
+        acc[6 + c] = addS<-S>(acc[6 + c], ti(t[3 + c]));
+        acc[9 + c] = addS<-S>(acc[9 + c], ti(t[c]));
+      } else if constexpr (MU == 1) {   // lower = (-S t1, S t0)
+        acc[6 + c] = addS<-S>(acc[6 + c], t[3 + c]);
+        acc[9 + c] = addS<S>(acc[9 + c], t[c]);
+      } else if constexpr (MU == 2) {   // lower = (-S i t0, S i t1)
+        acc[6 + c] = addS<-S>(acc[6 + c], ti(t[c]));
+        acc[9 + c] = addS<S>(acc[9 + c], ti(t[3 + c]));
+      } else {                          // lower = (-S t0, -S t1)
+        acc[6 + c] = addS<-S>(acc[6 + c], t[c]);
+        acc[9 + c] = addS<-S>(acc[9 + c], t[3 + c]);
+      }
+    } else {
+      const R sp = (R)S * sc;  // S * sc
+      acc[c].r = fma(sc, t[c].r, acc[c].r);
+      acc[c].i = fma(sc, t[c].i, acc[c].i);
+      acc[3 + c].r = fma(sc, t[3 + c].r, acc[3 + c].r);
+      acc[3 + c].i = fma(sc, t[3 + c].i, acc[3 + c].i);
+      if constexpr (MU == 0) {          // -S i t1 = (S t1.i, -S t1.r)
+        acc[6 + c].r = fma(sp, t[3 + c].i, acc[6 + c].r);
+        acc[6 + c].i = fma(-sp, t[3 + c].r, acc[6 + c].i);
+        acc[9 + c].r = fma(sp, t[c].i, acc[9 + c].r);
+        acc[9 + c].i = fma(-sp, t[c].r, acc[9 + c].i);
+      } else if constexpr (MU == 1) {   // -S t1, S t0
+        acc[6 + c].r = fma(-sp, t[3 + c].r, acc[6 + c].r);
+        acc[6 + c].i = fma(-sp, t[3 + c].i, acc[6 + c].i);
+        acc[9 + c].r = fma(sp, t[c].r, acc[9 + c].r);
+        acc[9 + c].i = fma(sp, t[c].i, acc[9 + c].i);
+      } else if constexpr (MU == 2) {   // -S i t0 = (S t0.i, -S t0.r) ; S i t1 = (-S t1.i, S t1.r)
+        acc[6 + c].r = fma(sp, t[c].i, acc[6 + c].r);
+        acc[6 + c].i = fma(-sp, t[c].r, acc[6 + c].i);
+        acc[9 + c].r = fma(-sp, t[3 + c].i, acc[9 + c].r);
+        acc[9 + c].i = fma(sp, t[3 + c].r, acc[9 + c].i);
+      } else {                          // -S t0, -S t1
+        acc[6 + c].r = fma(-sp, t[c].r, acc[6 + c].r);
+        acc[6 + c].i = fma(-sp, t[c].i, acc[6 + c].i);
+        acc[9 + c].r = fma(-sp, t[3 + c].r, acc[9 + c].r);
+        acc[9 + c].i = fma(-sp, t[3 + c].i, acc[9 + c].i);
+      }
     }
   }
 }
 
+// Half-precision projection on packed (re, im) pairs: the stored values are
+// scaled to |v| <= 1, so the rank-2 combination is formed in half2 and only
+// the six results are widened; the site scale is applied at accumulation.
+template <int MU, int S>
+__device__ __forceinline__ void project_h2(const __half2 (&p)[12], __half2 (&h)[6]) {
+  // S i p = (-S p.i, S p.r) = swap(p) * (-S, S)
+  const __half2 iS = __floats2half2_rn((float)-S, (float)S);
+  const __half2 iN = __floats2half2_rn((float)S, (float)-S);  // -S i
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    if constexpr (MU == 0) {          // h0 = p0 + S i p3 ; h1 = p1 + S i p2
+      h[c] = __hfma2(__lowhigh2highlow(p[9 + c]), iS, p[c]);
+      h[3 + c] = __hfma2(__lowhigh2highlow(p[6 + c]), iS, p[3 + c]);
+    } else if constexpr (MU == 1) {   // h0 = p0 + S p3 ; h1 = p1 - S p2
+      h[c] = S > 0 ? __hadd2(p[c], p[9 + c]) : __hsub2(p[c], p[9 + c]);
+      h[3 + c] = S > 0 ? __hsub2(p[3 + c], p[6 + c]) : __hadd2(p[3 + c], p[6 + c]);
+    } else if constexpr (MU == 2) {   // h0 = p0 + S i p2 ; h1 = p1 - S i p3
+      h[c] = __hfma2(__lowhigh2highlow(p[6 + c]), iS, p[c]);
+      h[3 + c] = __hfma2(__lowhigh2highlow(p[9 + c]), iN, p[3 + c]);
+    } else {                          // h0 = p0 - S p2 ; h1 = p1 - S p3
+      h[c] = S > 0 ? __hsub2(p[c], p[6 + c]) : __hadd2(p[c], p[6 + c]);
+      h[3 + c] = S > 0 ? __hsub2(p[3 + c], p[9 + c]) : __hadd2(p[3 + c], p[9 + c]);
+    }
+  }
+}
+
+// Load the neighbour spinor and project it: h receives the half spinor, the
+// return value the factor still to apply (the FP16 site scale, else 1).
+template <int P, int MU, int S, typename R>
+__device__ __forceinline__ R load_project(cx<R> (&h)[6], const void* __restrict__ in, int nb,
+                                          int Vh_pad) {
+  if constexpr (P == WD_F16) {
+    const int4* p = (const int4*)in;
+    const float* scp = (const float*)((const char*)in + (size_t)Vh_pad * 48);
+    __half2 v[12];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      int4 w = __ldg(p + sbi(nb, k, 3));
+      const __half2* q = reinterpret_cast<const __half2*>(&w);
+#pragma unroll
+      for (int j = 0; j < 4; j++) v[4 * k + j] = q[j];
+    }
+    const float scale = __ldg(scp + nb);
+    __half2 hh[6];
+    project_h2<MU, S>(v, hh);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      float2 f = __half22float2(hh[k]);
+      h[k] = mk<R>(f.x, f.y);
+    }
+    return scale;
+  } else {
+    cx<R> psi[12];
+    load_spinor<P, R>(psi, in, nb, Vh_pad);
+    project<MU, S>(psi, h);
+    return (R)1;
+  }
+}
+
 // One hop: neighbour site nb (opposite parity), link in `region` at site lcb.
-// FWD: U h ; backward: U^+ h.  flip: negate (antiperiodic crossing).
+// FWD: U h ; backward: U^+ h.  flip: the hop crosses the antiperiodic time
+// boundary (applied as a sign at accumulation).
 template <int P, int RC, int MU, int S, bool FWD, typename R>
 __device__ __forceinline__ void hop(cx<R> (&acc)[12], const void* __restrict__ in,
                                     const void* __restrict__ gauge, int nb, int region, int lcb,
                                     bool flip, int Vh_pad) {
-  cx<R> psi[12];
-  load_spinor<P, R>(psi, in, nb, Vh_pad);
+  cx<R> h[6];
+  R sc = load_project<P, MU, S, R>(h, in, nb, Vh_pad);
   cx<R> u[9];
   load_link<P, RC, R>(u, gauge, region, lcb, Vh_pad);
-  cx<R> h[6];
-  project<MU, S>(psi, h);
-  if (MU == 3 && flip) {
-#pragma unroll
-    for (int k = 0; k < 6; k++) h[k] = mk<R>(-h[k].r, -h[k].i);
-  }
   cx<R> t[6];
 #pragma unroll
   for (int hs = 0; hs < 2; hs++) {
@@ -100,25 +185,109 @@ __device__ __forceinline__ void hop(cx<R> (&acc)[12], const void* __restrict__ i
       t[hs * 3 + c] = v;
     }
   }
-  expand_add<MU, S>(acc, t);
+  if constexpr (P == WD_F16) {
+    if (MU == 3 && flip) sc = -sc;
+    expand_add<MU, S, false>(acc, t, sc);
+  } else if constexpr (MU == 3) {
+    expand_add<MU, S, false>(acc, t, flip ? (R)-1 : (R)1);
+  } else {
+    expand_add<MU, S, true>(acc, t, (R)1);
+  }
 }
 
+// ---------------------------------------------------------------------------
+// FP16: the hop split into a fetch (raw 128-bit loads into registers) and a
+// compute step, so that the kernel keeps the next hops' loads in flight while
+// it computes the current one.  FP16 moves half the bytes of FP32 per hop, so
+// without this the SM runs out of outstanding loads before HBM saturates.
+// ---------------------------------------------------------------------------
+
+struct RawF16 {
+  int4 s[3];   // 24 halves of the neighbour spinor
+  float sc;    // its site scale
+  int4 la;     // link U00 U01 U02 U10
+  int2 lb;     // link U11 U12
+};
+
+__device__ __forceinline__ RawF16 fetch_f16(const void* __restrict__ in,
+                                            const void* __restrict__ gauge, int nb, int region,
+                                            int lcb, int VP) {
+  RawF16 r;
+  const int4* p = (const int4*)in;
+#pragma unroll
+  for (int k = 0; k < 3; k++) r.s[k] = __ldg(p + sbi(nb, k, 3));
+  r.sc = __ldg((const float*)((const char*)in + (size_t)VP * 48) + nb);
+  r.la = __ldg((const int4*)gauge + (size_t)region * VP + lcb);
+  r.lb = __ldg((const int2*)((const char*)gauge + (size_t)8 * VP * 16) + (size_t)region * VP + lcb);
+  return r;
+}
+
+template <int MU, int S, bool FWD>
+__device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& r, bool flip) {
+  __half2 v[12];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const __half2* q = reinterpret_cast<const __half2*>(&r.s[k]);
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[4 * k + j] = q[j];
+  }
+  __half2 hh[6];
+  project_h2<MU, S>(v, hh);
+  cx<float> h[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    float2 f = __half22float2(hh[k]);
+    h[k] = mk<float>(f.x, f.y);
+  }
+  cx<float> u[9];
+  const __half2* ha = reinterpret_cast<const __half2*>(&r.la);
+  const __half2* hb = reinterpret_cast<const __half2*>(&r.lb);
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    float2 f = __half22float2(ha[j]);
+    u[j] = mk<float>(f.x, f.y);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    float2 f = __half22float2(hb[j]);
+    u[4 + j] = mk<float>(f.x, f.y);
+  }
+  reconstruct_row2(u);
+  cx<float> t[6];
+#pragma unroll
+  for (int hs = 0; hs < 2; hs++) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      cx<float> w = mk<float>(0, 0);
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        if (FWD)
+          w = cmadd(u[c * 3 + d], h[hs * 3 + d], w);
+        else
+          w = cjmadd(u[d * 3 + c], h[hs * 3 + d], w);
+      }
+      t[hs * 3 + c] = w;
+    }
+  }
+  const float sc = (MU == 3 && flip) ? -r.sc : r.sc;
+  expand_add<MU, S, false>(acc, t, sc);
+}
+
+#ifndef WD_F16_PREFETCH
+#define WD_F16_PREFETCH 2
+#endif
+
 template <int P, int RC, bool DAG, bool NORM, int BS>
-__global__ void __launch_bounds__(BS) dslash_kernel(const DslashArgs a) {
+__global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_kernel(const DslashArgs a) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
   const Geom& g = a.g;
   const int cb = blockIdx.x * BS + threadIdx.x;
   double nrm = 0.0;
   if (cb < g.Vh) {
     const int p = a.parity;
-    const int xh = cb % g.Lh0;
-    int r = cb / g.Lh0;
-    const int x1 = r % g.L[1];
-    r /= g.L[1];
-    const int x2 = r % g.L[2];
-    const int x3 = r / g.L[2];
-    const int x0 = 2 * xh + ((p + x1 + x2 + x3) & 1);
-    const int row = cb - xh;
+    int x0, x1, x2, x3;
+    cb_coords(cb, p, g, x0, x1, x2, x3);
+    const int row = cb - (x0 >> 1);
 
     const int f0 = row + ((x0 + 1 == g.L[0] ? 0 : x0 + 1) >> 1);
     const int b0 = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
@@ -141,14 +310,55 @@ __global__ void __launch_bounds__(BS) dslash_kernel(const DslashArgs a) {
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
 
-    hop<P, RC, 0, SF, true>(acc, a.in, a.gauge, f0, 0 + p, cb, false, VP);
-    hop<P, RC, 0, SB_, false>(acc, a.in, a.gauge, b0, 0 + q, b0, false, VP);
-    hop<P, RC, 1, SF, true>(acc, a.in, a.gauge, f1, 2 + p, cb, false, VP);
-    hop<P, RC, 1, SB_, false>(acc, a.in, a.gauge, b1, 2 + q, b1, false, VP);
-    hop<P, RC, 2, SF, true>(acc, a.in, a.gauge, f2, 4 + p, cb, false, VP);
-    hop<P, RC, 2, SB_, false>(acc, a.in, a.gauge, b2, 4 + q, b2, false, VP);
-    hop<P, RC, 3, SF, true>(acc, a.in, a.gauge, f3, 6 + p, cb, fflip, VP);
-    hop<P, RC, 3, SB_, false>(acc, a.in, a.gauge, b3, 6 + q, b3, bflip, VP);
+    if constexpr (P == WD_F16) {
+      const void* in = a.in;
+      const void* ga = a.gauge;
+#define WD_F(nb, reg, lcb) fetch_f16(in, ga, nb, reg, lcb, VP)
+#if WD_F16_PREFETCH >= 2
+      RawF16 r0 = WD_F(f0, 0 + p, cb), r1 = WD_F(b0, 0 + q, b0);
+      RawF16 r2 = WD_F(f1, 2 + p, cb);
+      compute_f16<0, SF, true>(acc, r0, false);
+      RawF16 r3 = WD_F(b1, 2 + q, b1);
+      compute_f16<0, SB_, false>(acc, r1, false);
+      r0 = WD_F(f2, 4 + p, cb);
+      compute_f16<1, SF, true>(acc, r2, false);
+      r1 = WD_F(b2, 4 + q, b2);
+      compute_f16<1, SB_, false>(acc, r3, false);
+      r2 = WD_F(f3, 6 + p, cb);
+      compute_f16<2, SF, true>(acc, r0, false);
+      r3 = WD_F(b3, 6 + q, b3);
+      compute_f16<2, SB_, false>(acc, r1, false);
+      compute_f16<3, SF, true>(acc, r2, fflip);
+      compute_f16<3, SB_, false>(acc, r3, bflip);
+#else
+      RawF16 r0 = WD_F(f0, 0 + p, cb);
+      RawF16 r1 = WD_F(b0, 0 + q, b0);
+      compute_f16<0, SF, true>(acc, r0, false);
+      r0 = WD_F(f1, 2 + p, cb);
+      compute_f16<0, SB_, false>(acc, r1, false);
+      r1 = WD_F(b1, 2 + q, b1);
+      compute_f16<1, SF, true>(acc, r0, false);
+      r0 = WD_F(f2, 4 + p, cb);
+      compute_f16<1, SB_, false>(acc, r1, false);
+      r1 = WD_F(b2, 4 + q, b2);
+      compute_f16<2, SF, true>(acc, r0, false);
+      r0 = WD_F(f3, 6 + p, cb);
+      compute_f16<2, SB_, false>(acc, r1, false);
+      r1 = WD_F(b3, 6 + q, b3);
+      compute_f16<3, SF, true>(acc, r0, fflip);
+      compute_f16<3, SB_, false>(acc, r1, bflip);
+#endif
+#undef WD_F
+    } else {
+      hop<P, RC, 0, SF, true>(acc, a.in, a.gauge, f0, 0 + p, cb, false, VP);
+      hop<P, RC, 0, SB_, false>(acc, a.in, a.gauge, b0, 0 + q, b0, false, VP);
+      hop<P, RC, 1, SF, true>(acc, a.in, a.gauge, f1, 2 + p, cb, false, VP);
+      hop<P, RC, 1, SB_, false>(acc, a.in, a.gauge, b1, 2 + q, b1, false, VP);
+      hop<P, RC, 2, SF, true>(acc, a.in, a.gauge, f2, 4 + p, cb, false, VP);
+      hop<P, RC, 2, SB_, false>(acc, a.in, a.gauge, b2, 4 + q, b2, false, VP);
+      hop<P, RC, 3, SF, true>(acc, a.in, a.gauge, f3, 6 + p, cb, fflip, VP);
+      hop<P, RC, 3, SB_, false>(acc, a.in, a.gauge, b3, 6 + q, b3, bflip, VP);
+    }
 
     const R ca = (R)a.a;
 #pragma unroll

@@ -7,8 +7,36 @@
 
 namespace wd {
 
-// threads per block of the hopping kernel
-constexpr int DSLASH_BS = 128;
+// threads per block of the hopping kernel, and the minimum number of its
+// blocks per SM that the register allocation must allow
+#ifndef WD_DSLASH_BS
+#define WD_DSLASH_BS 128
+#endif
+// Register budgets from a sweep on GB300 (32^3x64): FP32 is fastest with 7
+// resident 128-thread blocks per SM (<= 72 registers), FP16 with 5 (<= 102
+// registers, two hops of loads in flight); FP64 is ALU-bound and gets 3
+// (168 registers, no spills).
+#ifndef WD_DSLASH_MINB_F64
+#define WD_DSLASH_MINB_F64 3
+#endif
+#ifndef WD_DSLASH_MINB_F32
+#define WD_DSLASH_MINB_F32 7
+#endif
+#ifndef WD_DSLASH_MINB_F32_NORM
+#define WD_DSLASH_MINB_F32_NORM 6
+#endif
+#ifndef WD_DSLASH_MINB_F16
+#define WD_DSLASH_MINB_F16 5
+#endif
+constexpr int DSLASH_BS = WD_DSLASH_BS;
+// (the fused-norm FP32 variant needs 80 registers to stay free of spills)
+template <int P, bool NORM>
+struct DslashMinBlocks {
+  static constexpr int value =
+      P == WD_F64   ? WD_DSLASH_MINB_F64
+      : P == WD_F32 ? (NORM ? WD_DSLASH_MINB_F32_NORM : WD_DSLASH_MINB_F32)
+                    : WD_DSLASH_MINB_F16;
+};
 
 struct DslashArgs {
   void* out;

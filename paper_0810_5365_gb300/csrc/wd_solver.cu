@@ -404,6 +404,7 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
   int iters = 0, last_ru = 0;
   int reliable_interval = P.inner_prec == WD_F64 ? 0x7fffffff : P.reliable_interval;
 
+  WD_CK(cudaStreamSynchronize(st));
   // ---- the iteration graph ----
   cudaGraphExec_t exec = nullptr;
   if (P.use_graph) {
@@ -426,6 +427,13 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
     }
   }
 
+  auto now = [] { return std::chrono::steady_clock::now(); };
+  auto secs = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+    return std::chrono::duration<double>(b - a).count();
+  };
+  const auto t_loop = now();
+  I.setup_seconds = secs(t0, t_loop);
+  double t_ru = 0.0;
   double r64 = std::sqrt(w.sc_host->r64);
   bool converged = !(bnorm > 0) || r64 <= target;
   while (!converged) {
@@ -461,8 +469,10 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
     }
     const bool looks_done = std::sqrt(rr) <= target;
     if (looks_done || iters - last_ru >= reliable_interval || iters >= P.maxiter) {
+      const auto t_a = now();
       cudaError_t e = reliable_update(c, true, st);
       if (e == cudaSuccess) e = read_scalars(c);
+      t_ru += secs(t_a, now());
       if (e != cudaSuccess) { state().last_cuda_error = (int)e; status = WD_ERR_CUDA; break; }
       ru++;
       last_ru = iters;
@@ -472,6 +482,9 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
     }
   }
   if (exec) cudaGraphExecDestroy(exec);
+  const auto t_fin = now();
+  I.reliable_seconds = t_ru;
+  I.iterate_seconds = secs(t_loop, t_fin) - t_ru;
   if (converged) status = WD_OK;
   if (status == WD_ERR_CUDA) return status;
 
@@ -501,7 +514,8 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
   I.status = status;
   I.true_residual = rel;
   I.dslash_calls = c.dslash_calls;
-  I.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  I.seconds = secs(t0, now());
+  I.final_seconds = secs(t_fin, now());
   if (info) *info = I;
   return status;
 }

@@ -59,7 +59,9 @@ class wd_solve_params(C.Structure):
 class wd_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("reliable_updates", C.c_int), ("status", C.c_int),
                 ("true_residual", C.c_double), ("seconds", C.c_double),
-                ("dslash_calls", C.c_double)]
+                ("dslash_calls", C.c_double), ("setup_seconds", C.c_double),
+                ("iterate_seconds", C.c_double), ("reliable_seconds", C.c_double),
+                ("final_seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
