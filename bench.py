@@ -242,6 +242,22 @@ def time_dslash(W, torch, prec_id, recon, gauge, bufs, dims, steps, warmup, stre
     return e0.elapsed_time(e1) / 1e3
 
 
+def max_over_ranks(seconds: float, device: str) -> float:
+    """Replicas report the slowest rank's time (the job ends when it does);
+    a barrier follows so that no rank starts the next phase early."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest time."""
+    return units_per_rank * world / seconds
+
+
 SOLVE_DIMS = (24, 24, 24, 48)
 SOLVE_KAPPA = 0.1370
 
@@ -303,6 +319,116 @@ def solve_section(W, torch, reps=3):
     return out
 
 
+BATCH_KAPPA = 0.1360
+
+
+def batch_section(W, torch):
+    """Batched multi-right-hand-side solves (FP32 inner, FP64 reliable
+    updates, 1e-10 true residual):
+    (a) 12 point sources (one per spin-colour index at the origin) on 24^3x48;
+    (b) a mixed batch, 4 Gaussian right-hand sides on each of 8^4, 16^3x32
+        and 24^3x48 -- one batched launch per step for all 12;
+    each against the same right-hand sides solved one at a time with the
+    single-right-hand-side mixed solver and with plain FP64 CG, plus the
+    multi-RHS hopping kernel's throughput (12 right-hand sides, 24^3x48)."""
+    from synth import fields
+    out = {}
+
+    def run_batch(spec, name):
+        probs, singles = [], []
+        for dims, nrhs, kind, seed in spec:
+            U = fields.su3_links(dims, seed=seed)
+            if kind == "point":
+                bs = [fields.point_source(dims, 0, r // 3, r % 3) for r in range(nrhs)]
+            else:
+                bs = [fields.gaussian_spinor(dims, seed=seed + 1 + r) for r in range(nrhs)]
+            b = torch.from_numpy(np.ascontiguousarray(np.stack(bs)).view(np.float64)).cuda()
+            Ud = torch.from_numpy(U.view(np.float64).reshape(-1)).cuda()
+            probs.append({"dims": dims, "kappa": BATCH_KAPPA, "nrhs": nrhs, "gauge": Ud, "b": b,
+                          "x": torch.zeros_like(b)})
+        p = W.wd_solve_params_default()
+        p.inner_prec = W.WD_F32
+        W.wd_solve_batch(probs, p, check=False)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, infos = W.wd_solve_batch(probs, p, check=False)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        seq = {}
+        for label, inner in (("single_rhs_f32", W.WD_F32), ("plain_f64", W.WD_F64)):
+            q = W.wd_solve_params_default()
+            q.inner_prec = inner
+            tot, its, worst = 0.0, [], 0.0
+            for pr in probs:
+                n = pr["nrhs"]
+                fl = pr["b"].numel() // n
+                x = torch.zeros(fl, dtype=torch.float64, device="cuda")
+                W.wd_solve_ex(x, pr["b"][:fl], pr["gauge"], BATCH_KAPPA, pr["dims"], q,
+                              check=False)  # warm-up of this shape
+                for r in range(n):
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    i = W.wd_solve_ex(x, pr["b"][r * fl:(r + 1) * fl], pr["gauge"], BATCH_KAPPA,
+                                      pr["dims"], q, check=False)
+                    torch.cuda.synchronize()
+                    tot += time.perf_counter() - t0
+                    its.append(i["iters"])
+                    worst = max(worst, i["true_residual"])
+            seq[label] = {"wall_s": tot, "iters": its, "max_true_residual": worst}
+        out[name] = {
+            "status": rc, "wall_s": t_batch, "iters": [d["iters"] for d in infos],
+            "max_true_residual": max(d["true_residual"] for d in infos),
+            "sequential": seq,
+            "speedup_vs_sequential_f32": seq["single_rhs_f32"]["wall_s"] / t_batch,
+            "speedup_vs_plain_f64": seq["plain_f64"]["wall_s"] / t_batch,
+            "problems": [{"dims": list(d), "nrhs": n, "rhs": k} for d, n, k, _ in spec],
+        }
+        del probs
+
+    run_batch([((24, 24, 24, 48), 12, "point", 1234)], "point_sources_24x48")
+    run_batch([((8, 8, 8, 8), 4, "gauss", 1234), ((16, 16, 16, 32), 4, "gauss", 2234),
+               ((24, 24, 24, 48), 4, "gauss", 3234)], "mixed_lattices")
+
+    # the multi-RHS hopping kernel alone: 12 right-hand sides on 24^3x48
+    dims = (24, 24, 24, 48)
+    Vh = int(np.prod(dims)) // 2
+    U = fields.su3_links(dims)
+    Ud = torch.from_numpy(U.view(np.float64).reshape(-1)).cuda()
+    g = W.alloc_gauge(dims, W.WD_F32, 12)
+    W.wd_pack_gauge(g, Ud, dims, W.WD_F32, 12)
+    nr = 12
+    h = W.wd_spinor_bytes(dims, 0, W.WD_F32)
+    a = torch.zeros(nr * h, dtype=torch.uint8, device="cuda")
+    b = torch.zeros_like(a)
+    src = torch.from_numpy(fields.gaussian_spinor(dims, nsites=Vh).view(np.float64)
+                           .reshape(-1)).cuda()
+    for r in range(nr):
+        W.wd_pack_spinor(a[r * h:(r + 1) * h], src, dims, 1, W.WD_F32)
+    n_steps = 200
+    for k in range(10):
+        W.wd_dslash_mrhs(b, a, g, 0, 0, -BATCH_KAPPA, None, 0.0, nr, None, dims, W.WD_F32, 12)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(n_steps):
+        if k & 1:
+            W.wd_dslash_mrhs(a, b, g, 1, 0, -BATCH_KAPPA, None, 0.0, nr, None, dims, W.WD_F32, 12)
+        else:
+            W.wd_dslash_mrhs(b, a, g, 0, 0, -BATCH_KAPPA, None, 0.0, nr, None, dims, W.WD_F32, 12)
+    e1.record()
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / n_steps
+    bps = 8 * 48 / nr + 96 + 96
+    out["mrhs_dslash"] = {"dims": list(dims), "nrhs": nr, "prec": "f32",
+                          "us_per_launch": dt * 1e6,
+                          "gflops": FLOPS_PER_SITE * Vh * nr / dt / 1e9,
+                          "bytes_per_rhs_site": bps,
+                          "gbs": bps * Vh * nr / dt / 1e9}
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
@@ -344,10 +470,7 @@ def run_ours(args, rank, world, local):
             torch.cuda.synchronize()
             dt = time_dslash(W, torch, pid, recon, g, (a, b), dims, steps, args.warmup, stream)
             if world > 1:
-                t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                dt = t.item()
-                torch.distributed.barrier()
+                dt = max_over_ranks(dt, "cuda")
             results[name] = (dt, steps)
             del g, a, b
         # end to end through the C ABI with pinned host buffers
@@ -379,7 +502,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.empty_cache()
 
     dt, steps = results["f32"]
-    gflops = FLOPS_PER_SITE * Vh * steps * world / dt / 1e9
+    gflops = replica_value(FLOPS_PER_SITE * Vh * steps, world, dt) / 1e9
     launch_s = dt / steps
     achieved = BYTES_PER_SITE["f32"] * Vh / launch_s / 1e9
     line = {
@@ -419,6 +542,9 @@ def run_ours(args, rank, world, local):
     line["clocks"] = clocks
     if not args.no_solve and not args.quick:
         line["solve"] = solve_section(W, torch)
+        torch.cuda.empty_cache()
+        line["batch"] = batch_section(W, torch)
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(U, psi, dims)
     if rank == 0:

@@ -200,6 +200,21 @@ int wd_dslash_ex_noalloc(void *out, const void *in, const void *gauge, int parit
 int wd_mhat(void *out, const void *in, const void *gauge, void *tmp, double kappa,
             int dagger, const int dims[4], int prec, int recon);
 
+/*
+ * Multi-right-hand-side hopping application (batched form of wd_dslash_ex):
+ * nrhs packed half fields laid out back to back (consecutive fields
+ * wd_spinor_bytes(dims, parity, prec) apart) share one gauge field:
+ *     out_r = a * H_{p,1-p} in_r  [+ bx * x_r]          r = 0 .. nrhs-1
+ * (H^+ when dagger != 0).  Each link is read from memory once per site and
+ * applied to every right-hand side (links staged in shared memory for the
+ * 12-real FP32/FP16 formats).  x may be NULL or alias out; in must not.  If
+ * norm2 != NULL (device, nrhs doubles) it receives ||out_r||^2.
+ * 1 <= nrhs <= 32.
+ */
+int wd_dslash_mrhs(void *out, const void *in, const void *gauge, int parity, int dagger,
+                   double a, const void *x, double bx, int nrhs, double *norm2,
+                   const int dims[4], int prec, int recon);
+
 /* ------------------------------------------------------------------ */
 /* BLAS-like kernels and FP64 reductions (paper: dot product by        */
 /* parallel reduction in double precision; "BLAS-like" vector kernels) */
@@ -264,6 +279,33 @@ int wd_solve(double *x, const double *b, const double *gauge, double kappa,
 int wd_solve_ex(double *x, const double *b, const double *gauge, double kappa,
                 const int dims[4], const wd_solve_params *params,
                 wd_solve_info *info);
+
+/*
+ * Batched solves (many right-hand sides; several lattices, possibly of
+ * different sizes).  Problem j solves D_j x = b for each of its nrhs
+ * right-hand sides; b and x hold nrhs canonical FP64 full spinors back to
+ * back (V_j * 24 doubles each), host or device memory; gauge is the
+ * canonical FP64 gauge field of problem j.  Every right-hand side runs the
+ * algorithm of wd_solve_ex with its own scalars and stops on its own
+ * convergence; each iteration step is one launch over all problems and
+ * right-hand sides (links reused across right-hand sides), and
+ * check_interval iterations are one captured CUDA graph.
+ * Limits: 1 <= nproblems <= 16, 1 <= nrhs <= 32 per problem.
+ * info (optional): one wd_solve_info per right-hand side, in problem order.
+ * Returns WD_OK if every right-hand side converged, else the first failing
+ * status (the per-right-hand-side statuses are in info).
+ */
+typedef struct {
+    int dims[4];
+    double kappa;
+    int nrhs;
+    const double *gauge;
+    const double *b;
+    double *x;
+} wd_batch_problem;
+
+int wd_solve_batch(const wd_batch_problem *problems, int nproblems,
+                   const wd_solve_params *params, wd_solve_info *info);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,11 @@
 #include "wd_internal.h"
 
 namespace wd {
+int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_params* prm,
+                     wd_solve_info* infos);
+cudaError_t dslash_mrhs(void* out, const void* in, const void* gauge, int parity, int dagger,
+                        double a, const void* x, double bx, int nrhs, double* norms,
+                        const Geom& g, int prec, int recon, cudaStream_t st);
 int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
                const wd_solve_params* prm, wd_solve_info* info);
 void solver_finalize();
@@ -213,6 +218,38 @@ int wd_mhat(void* out, const void* in, const void* gauge, void* tmp, double kapp
                       dims, prec, recon));
   return wd_dslash_ex(out, tmp, gauge, WD_EVEN, dagger, -kappa * kappa, in, 1.0, nullptr, 0.0,
                       nullptr, dims, prec, recon);
+}
+
+int wd_dslash_mrhs(void* out, const void* in, const void* gauge, int parity, int dagger, double a,
+                   const void* x, double bx, int nrhs, double* norm2, const int dims[4], int prec,
+                   int recon) {
+  WD_TRY(check_dims(dims));
+  WD_TRY(check_prec(prec));
+  if (!out || !in || !gauge) return WD_ERR_NULL;
+  if (!aligned(out) || !aligned(in) || !aligned(gauge) || (x && !aligned(x)) ||
+      (norm2 && ((uintptr_t)norm2 & 7u)))
+    return WD_ERR_ALIGN;
+  if (parity != WD_EVEN && parity != WD_ODD) return WD_ERR_ARG;
+  if (nrhs < 1 || nrhs > 32) return WD_ERR_ARG;
+  if (link_bytes(prec, recon) == 0) return WD_ERR_PREC;
+  if (out == in) return WD_ERR_ALIAS;
+  return cuda_status(dslash_mrhs(out, in, gauge, parity, dagger, a, x, bx, nrhs, norm2,
+                                 make_geom(dims), prec, recon, state().stream));
+}
+
+int wd_solve_batch(const wd_batch_problem* problems, int nproblems, const wd_solve_params* params,
+                   wd_solve_info* info) {
+  if (!problems) return WD_ERR_NULL;
+  if (nproblems < 1 || nproblems > 16) return WD_ERR_ARG;
+  for (int j = 0; j < nproblems; j++) {
+    WD_TRY(check_dims(problems[j].dims));
+    if (!problems[j].gauge || !problems[j].b || !problems[j].x) return WD_ERR_NULL;
+    if (!aligned(problems[j].gauge) || !aligned(problems[j].b) || !aligned(problems[j].x))
+      return WD_ERR_ALIGN;
+    if (problems[j].nrhs < 1 || problems[j].nrhs > 32) return WD_ERR_ARG;
+    if ((const void*)problems[j].x == (const void*)problems[j].b) return WD_ERR_ALIAS;
+  }
+  return solve_batch_impl(problems, nproblems, params, info);
 }
 
 int wd_norm2(double* result, const void* x, const int dims[4], int parity, int prec) {

@@ -1,0 +1,795 @@
+// Batched multi-right-hand-side solves: many right-hand sides on one gauge
+// field, and several lattices of different sizes, advanced together.
+//
+// The algorithm per right-hand side is the one of wd_solver.cu (even-odd
+// Schur complement, CGLS on its normal equations, FP32/FP16 inner
+// iterations, FP64 reliable updates every `reliable_interval` iterations).
+// What changes is the execution: every step of an iteration is ONE launch
+// over all problems and right-hand sides (the multi-RHS hopping kernel of
+// wd_mrhs.cuh reuses each staged link across the right-hand sides of its
+// problem; the BLAS steps walk the same tile list), CG scalars are per
+// right-hand side on the device, a convergence mask switches finished
+// right-hand sides off, and each block of `check_interval` iterations is one
+// captured CUDA graph.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "wd_mrhs.cuh"
+
+namespace wd {
+
+cudaError_t launch_mrhs_f64(const MrhsBatch& bt, int recon, bool dagger, const int* active,
+                            RedScratch rs, double* norm_out, int grid, cudaStream_t st);
+cudaError_t launch_mrhs_f32(const MrhsBatch& bt, int recon, bool dagger, const int* active,
+                            RedScratch rs, double* norm_out, int grid, cudaStream_t st);
+cudaError_t launch_mrhs_f16(const MrhsBatch& bt, int recon, bool dagger, const int* active,
+                            RedScratch rs, double* norm_out, int grid, cudaStream_t st);
+
+static cudaError_t launch_mrhs(int prec, const MrhsBatch& bt, int recon, bool dagger,
+                               const int* active, RedScratch rs, double* norm_out, cudaStream_t st) {
+  int grid = bt.ntiles < num_sms() * 4 ? bt.ntiles : num_sms() * 4;
+  if (grid < 1) grid = 1;
+  switch (prec) {
+    case WD_F64: return launch_mrhs_f64(bt, recon, dagger, active, rs, norm_out, grid, st);
+    case WD_F32: return launch_mrhs_f32(bt, recon, dagger, active, rs, norm_out, grid, st);
+    case WD_F16: return launch_mrhs_f16(bt, recon, dagger, active, rs, norm_out, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// batched BLAS over the same tile list
+// ---------------------------------------------------------------------------
+
+struct BlasProblem {
+  Geom g;
+  int nrhs, rhs0, tile0, ntiles;
+  char* f[3];
+  size_t s[3];
+};
+
+struct BlasBatch {
+  int nprob, ntiles;
+  BlasProblem p[MRHS_MAX_PROBLEMS];
+};
+
+// sums the per-(tile, rhs) partials of every active right-hand side in tile
+// order; called by every thread of every CTA at the end of a reducing kernel
+__device__ __forceinline__ void batch_finalize(const BlasBatch& bt, const int* active,
+                                               RedScratch rs, double* out, double* red) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t = atomicAdd(rs.counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int j = 0; j < bt.nprob; j++) {
+    const BlasProblem& pr = bt.p[j];
+    for (int r = 0; r < pr.nrhs; r++) {
+      if (active[pr.rhs0 + r] == 0) continue;
+      double v[1] = {0.0};
+      for (int t = threadIdx.x; t < pr.ntiles; t += MRHS_BS)
+        v[0] += __ldcg(rs.partials + (size_t)(pr.tile0 + t) * MRHS_MAX + r);
+      block_sum<1, MRHS_BS>(v, red);
+      if (threadIdx.x == 0) out[pr.rhs0 + r] = v[0];
+    }
+  }
+  if (threadIdx.x == 0) *rs.counter = 0u;
+}
+
+#define WD_TILE_LOOP                                                   \
+  for (int tile = blockIdx.x; tile < bt.ntiles; tile += gridDim.x) {   \
+    int j = 0;                                                         \
+    while (j + 1 < bt.nprob && tile >= bt.p[j + 1].tile0) j++;         \
+    const BlasProblem& pr = bt.p[j];                                   \
+    const int cb = (tile - pr.tile0) * MRHS_BS + threadIdx.x;          \
+    const bool valid = cb < pr.g.Vh;                                   \
+    const int VP = pr.g.Vh_pad;
+
+// r -= alpha q (f0 = r, f1 = q); rr = ||r||^2 ; alpha = gk / qq per rhs
+template <int P>
+__global__ void __launch_bounds__(MRHS_BS) batch_update_r(const BlasBatch bt, const int* active,
+                                                          const double* gk, const double* qq,
+                                                          RedScratch rs, double* rr) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  __shared__ double red[MRHS_BS / 32];
+  WD_TILE_LOOP
+  for (int r = 0; r < pr.nrhs; r++) {
+    const int gi = pr.rhs0 + r;
+    if (active[gi] == 0) continue;
+    double t = 0.0;
+    if (valid) {
+      const R alpha = (R)(gk[gi] / qq[gi]);
+      char* fr = pr.f[0] + r * pr.s[0];
+      const char* fq = pr.f[1] + r * pr.s[1];
+      cx<R> a[12], b[12];
+      load_spinor_rw<P, R>(a, fr, cb, VP);
+      load_spinor_rw<P, R>(b, fq, cb, VP);
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        a[k].r = fma(-alpha, b[k].r, a[k].r);
+        a[k].i = fma(-alpha, b[k].i, a[k].i);
+        t += (double)a[k].r * a[k].r + (double)a[k].i * a[k].i;
+      }
+      store_spinor<P, R>(fr, cb, VP, a);
+    }
+    double v[1] = {t};
+    block_sum<1, MRHS_BS>(v, red);
+    if (threadIdx.x == 0) rs.partials[(size_t)tile * MRHS_MAX + r] = v[0];
+  }
+  }
+  batch_finalize(bt, active, rs, rr, red);
+}
+
+// x += alpha p ; p = s + beta p   (f0 = x [PX], f1 = p, f2 = s)
+template <int P, int PX>
+__global__ void __launch_bounds__(MRHS_BS) batch_update_xp(const BlasBatch bt, const int* active,
+                                                           const double* gk, const double* gk1,
+                                                           const double* qq) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  using RX = typename std::conditional<PX == WD_F64, double, float>::type;
+  WD_TILE_LOOP
+  if (!valid) continue;
+  for (int r = 0; r < pr.nrhs; r++) {
+    const int gi = pr.rhs0 + r;
+    if (active[gi] == 0) continue;
+    const RX alpha = (RX)(gk[gi] / qq[gi]);
+    const R beta = (R)(gk1[gi] / gk[gi]);
+    char* fx = pr.f[0] + r * pr.s[0];
+    char* fp = pr.f[1] + r * pr.s[1];
+    const char* fs = pr.f[2] + r * pr.s[2];
+    cx<R> pv[12], sv[12];
+    cx<RX> xv[12];
+    load_spinor_rw<P, R>(pv, fp, cb, VP);
+    load_spinor_rw<P, R>(sv, fs, cb, VP);
+    load_spinor_rw<PX, RX>(xv, fx, cb, VP);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      xv[k].r = fma(alpha, (RX)pv[k].r, xv[k].r);
+      xv[k].i = fma(alpha, (RX)pv[k].i, xv[k].i);
+      pv[k].r = fma(beta, pv[k].r, sv[k].r);
+      pv[k].i = fma(beta, pv[k].i, sv[k].i);
+    }
+    store_spinor<PX, RX>(fx, cb, VP, xv);
+    store_spinor<P, R>(fp, cb, VP, pv);
+  }
+  }
+}
+
+// x64 += xs ; xs = 0   (f0 = x64 even half, f1 = xs [PX])
+template <int PX>
+__global__ void __launch_bounds__(MRHS_BS) batch_ru_accumulate(const BlasBatch bt,
+                                                               const int* active) {
+  using RX = typename std::conditional<PX == WD_F64, double, float>::type;
+  WD_TILE_LOOP
+  if (!valid) continue;
+  for (int r = 0; r < pr.nrhs; r++) {
+    if (active[pr.rhs0 + r] == 0) continue;
+    char* fx = pr.f[0] + r * pr.s[0];
+    char* fs = pr.f[1] + r * pr.s[1];
+    cx<double> a[12];
+    cx<RX> b[12];
+    load_spinor_rw<WD_F64, double>(a, fx, cb, VP);
+    load_spinor_rw<PX, RX>(b, fs, cb, VP);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      a[k].r += (double)b[k].r;
+      a[k].i += (double)b[k].i;
+      b[k] = mk<RX>(0, 0);
+    }
+    store_spinor<WD_F64, double>(fx, cb, VP, a);
+    store_spinor<PX, RX>(fs, cb, VP, b);
+  }
+  }
+}
+
+// dst = src (f0 = dst [PD], f1 = src [PS])
+template <int PD, int PS>
+__global__ void __launch_bounds__(MRHS_BS) batch_convert(const BlasBatch bt, const int* active) {
+  using R = typename std::conditional<PD == WD_F64 || PS == WD_F64, double, float>::type;
+  WD_TILE_LOOP
+  if (!valid) continue;
+  for (int r = 0; r < pr.nrhs; r++) {
+    if (active[pr.rhs0 + r] == 0) continue;
+    cx<R> v[12];
+    load_spinor_rw<PS, R>(v, pr.f[1] + r * pr.s[1], cb, VP);
+    store_spinor<PD, R>(pr.f[0] + r * pr.s[0], cb, VP, v);
+  }
+  }
+}
+#undef WD_TILE_LOOP
+
+// ---------------------------------------------------------------------------
+// the batched solver
+// ---------------------------------------------------------------------------
+
+struct BatchProblemWs {
+  int dims[4];
+  double kappa;
+  int nrhs, rhs0, tile0, ntiles;
+  Geom g;
+  void* g64 = nullptr;
+  void* gs = nullptr;
+  char* b64 = nullptr;   // nrhs full FP64 fields (even, odd)
+  char* x64 = nullptr;   // nrhs full FP64
+  char* rf64 = nullptr;  // nrhs full FP64
+  char* bhat = nullptr;  // nrhs even FP64
+  char* r64 = nullptr;   // nrhs even FP64
+  char* t64 = nullptr;   // nrhs odd FP64
+  char* p = nullptr;     // nrhs sloppy even
+  char* q = nullptr;
+  char* r = nullptr;
+  char* s = nullptr;
+  char* ts = nullptr;    // nrhs sloppy odd
+  char* xs = nullptr;    // nrhs sloppy-x even
+  double* canon = nullptr;  // staging for host b / x (nrhs full canonical)
+  double* canon_gauge = nullptr;
+};
+
+struct BatchScalars {
+  double* gamma[2];
+  double* qq;
+  double* rr;
+  double* r64;
+  double* bnorm2;
+  double* res_e;
+  double* res_o;
+};
+
+namespace {
+
+struct BatchCtx {
+  std::vector<BatchProblemWs> pw;
+  int nr = 0, sprec = WD_F32, srecon = 12, orecon = 18, xprec = WD_F32;
+  double* scal = nullptr;     // 8 * nr doubles
+  double* scal_h = nullptr;   // pinned copy
+  int* active = nullptr;      // device mask
+  int* active_h = nullptr;    // pinned
+  BatchScalars sc;
+  cudaStream_t cap = nullptr;
+  std::vector<void*> allocs;
+  double dslash_calls = 0;
+};
+
+void free_ctx(BatchCtx& c) {
+  for (void* p : c.allocs) cudaFree(p);
+  c.allocs.clear();
+  if (c.scal_h) cudaFreeHost(c.scal_h);
+  if (c.active_h) cudaFreeHost(c.active_h);
+  if (c.cap) cudaStreamDestroy(c.cap);
+  c.scal_h = nullptr;
+  c.active_h = nullptr;
+  c.cap = nullptr;
+}
+
+cudaError_t dalloc(BatchCtx& c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) c.allocs.push_back(*p);
+  return e;
+}
+
+MrhsProblem mproblem(const BatchProblemWs& w, int parity, const void* gauge, double a, void* out,
+                     size_t s_out, const void* in, size_t s_in, const void* x, size_t s_x,
+                     double bx, const void* y, size_t s_y, double cy) {
+  MrhsProblem m;
+  std::memset(&m, 0, sizeof(m));
+  m.g = w.g;
+  m.gauge = gauge;
+  m.nrhs = w.nrhs;
+  m.rhs0 = w.rhs0;
+  m.tile0 = w.tile0;
+  m.ntiles = w.ntiles;
+  m.parity = parity;
+  m.a = a;
+  m.bx = bx;
+  m.cy = cy;
+  m.out = out;
+  m.in = in;
+  m.x = x;
+  m.y = y;
+  m.s_out = s_out;
+  m.s_in = s_in;
+  m.s_x = s_x;
+  m.s_y = s_y;
+  return m;
+}
+
+BlasProblem bproblem(const BatchProblemWs& w, char* f0, size_t s0, char* f1, size_t s1,
+                     char* f2 = nullptr, size_t s2 = 0) {
+  BlasProblem b;
+  std::memset(&b, 0, sizeof(b));
+  b.g = w.g;
+  b.nrhs = w.nrhs;
+  b.rhs0 = w.rhs0;
+  b.tile0 = w.tile0;
+  b.ntiles = w.ntiles;
+  b.f[0] = f0;
+  b.f[1] = f1;
+  b.f[2] = f2;
+  b.s[0] = s0;
+  b.s[1] = s1;
+  b.s[2] = s2;
+  return b;
+}
+
+// the batch descriptors of every step, built once per solve
+struct Plan {
+  MrhsBatch d_oe_p, d_eo_q, d_oe_r_dag, d_eo_s_dag;  // sloppy operator steps
+  MrhsBatch r_t64, r_r64;                            // FP64 residual
+  MrhsBatch bhat, xo, rf_e, rf_o;                    // FP64 setup / final
+  BlasBatch upd_r, upd_xp, ru, cvt_r, cvt_p;
+  int ntiles;
+};
+
+void build_plan(BatchCtx& c, Plan& pl) {
+  std::memset(&pl, 0, sizeof(pl));
+  const int np = (int)c.pw.size();
+  MrhsBatch* ms[] = {&pl.d_oe_p, &pl.d_eo_q, &pl.d_oe_r_dag, &pl.d_eo_s_dag, &pl.r_t64,
+                     &pl.r_r64,  &pl.bhat,   &pl.xo,         &pl.rf_e,       &pl.rf_o};
+  BlasBatch* bs[] = {&pl.upd_r, &pl.upd_xp, &pl.ru, &pl.cvt_r, &pl.cvt_p};
+  int nt = 0;
+  for (auto& w : c.pw) nt = w.tile0 + w.ntiles;
+  pl.ntiles = nt;
+  for (MrhsBatch* m : ms) { m->nprob = np; m->ntiles = nt; }
+  for (BlasBatch* b : bs) { b->nprob = np; b->ntiles = nt; }
+  for (int j = 0; j < np; j++) {
+    BatchProblemWs& w = c.pw[j];
+    const double k = w.kappa, k2 = k * k;
+    const size_t h64 = spinor_half_bytes(w.g, WD_F64);
+    const size_t hs = spinor_half_bytes(w.g, c.sprec);
+    const size_t hx = spinor_half_bytes(w.g, c.xprec);
+    const size_t f64 = 2 * h64;  // full FP64 field
+    // sloppy operator: ts = H_oe p ; q = p - k^2 H_eo ts ; and the dagger pair on r -> s
+    pl.d_oe_p.p[j] = mproblem(w, WD_ODD, w.gs, 1.0, w.ts, hs, w.p, hs, nullptr, 0, 0, nullptr, 0, 0);
+    pl.d_eo_q.p[j] = mproblem(w, WD_EVEN, w.gs, -k2, w.q, hs, w.ts, hs, w.p, hs, 1.0, nullptr, 0, 0);
+    pl.d_oe_r_dag.p[j] = mproblem(w, WD_ODD, w.gs, 1.0, w.ts, hs, w.r, hs, nullptr, 0, 0, nullptr, 0, 0);
+    pl.d_eo_s_dag.p[j] = mproblem(w, WD_EVEN, w.gs, -k2, w.s, hs, w.ts, hs, w.r, hs, 1.0, nullptr, 0, 0);
+    // FP64: t64 = H_oe x_e ; r64 = k^2 H_eo t64 - x_e + bhat
+    pl.r_t64.p[j] = mproblem(w, WD_ODD, w.g64, 1.0, w.t64, h64, w.x64, f64, nullptr, 0, 0, nullptr, 0, 0);
+    pl.r_r64.p[j] = mproblem(w, WD_EVEN, w.g64, k2, w.r64, h64, w.t64, h64, w.x64, f64, -1.0, w.bhat, h64, 1.0);
+    // bhat = b_e + k H_eo b_o
+    pl.bhat.p[j] = mproblem(w, WD_EVEN, w.g64, k, w.bhat, h64, w.b64 + h64, f64, w.b64, f64, 1.0, nullptr, 0, 0);
+    // x_o = b_o + k H_oe x_e ; rf_e = k H_eo x_o + b_e - x_e ; rf_o = k H_oe x_e + b_o - x_o
+    pl.xo.p[j] = mproblem(w, WD_ODD, w.g64, k, w.x64 + h64, f64, w.x64, f64, w.b64 + h64, f64, 1.0, nullptr, 0, 0);
+    pl.rf_e.p[j] = mproblem(w, WD_EVEN, w.g64, k, w.rf64, f64, w.x64 + h64, f64, w.b64, f64, 1.0, w.x64, f64, -1.0);
+    pl.rf_o.p[j] = mproblem(w, WD_ODD, w.g64, k, w.rf64 + h64, f64, w.x64, f64, w.b64 + h64, f64, 1.0, w.x64 + h64, f64, -1.0);
+    pl.upd_r.p[j] = bproblem(w, w.r, hs, w.q, hs);
+    pl.upd_xp.p[j] = bproblem(w, w.xs, hx, w.p, hs, w.s, hs);
+    pl.ru.p[j] = bproblem(w, w.x64, f64, w.xs, hx);
+    pl.cvt_r.p[j] = bproblem(w, w.r, hs, w.r64, h64);
+    pl.cvt_p.p[j] = bproblem(w, w.p, hs, w.s, hs);
+  }
+}
+
+int blas_grid_tiles(int ntiles) {
+  int g = num_sms() * 6;
+  return ntiles < g ? (ntiles > 0 ? ntiles : 1) : g;
+}
+
+template <int P, int PX>
+cudaError_t batch_iteration_t(BatchCtx& c, const Plan& pl, int kp, cudaStream_t st) {
+  RedScratch rs = scratch();
+  const BatchScalars& sc = c.sc;
+  cudaError_t e;
+  const int grid = blas_grid_tiles(pl.ntiles);
+  c.dslash_calls += 4;
+  if ((e = launch_mrhs(c.sprec, pl.d_oe_p, c.srecon, false, c.active, rs, nullptr, st))) return e;
+  if ((e = launch_mrhs(c.sprec, pl.d_eo_q, c.srecon, false, c.active, rs, sc.qq, st))) return e;
+  batch_update_r<P><<<grid, MRHS_BS, 0, st>>>(pl.upd_r, c.active, sc.gamma[kp], sc.qq, rs, sc.rr);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_mrhs(c.sprec, pl.d_oe_r_dag, c.srecon, true, c.active, rs, nullptr, st))) return e;
+  if ((e = launch_mrhs(c.sprec, pl.d_eo_s_dag, c.srecon, true, c.active, rs, sc.gamma[1 - kp], st)))
+    return e;
+  batch_update_xp<P, PX><<<grid, MRHS_BS, 0, st>>>(pl.upd_xp, c.active, sc.gamma[kp],
+                                                   sc.gamma[1 - kp], sc.qq);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_iteration(BatchCtx& c, const Plan& pl, int kp, cudaStream_t st) {
+  switch (c.sprec) {
+    case WD_F64: return batch_iteration_t<WD_F64, WD_F64>(c, pl, kp, st);
+    case WD_F32: return batch_iteration_t<WD_F32, WD_F32>(c, pl, kp, st);
+    case WD_F16: return batch_iteration_t<WD_F16, WD_F32>(c, pl, kp, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int PD, int PS>
+void convert_b(const BlasBatch& b, const int* active, int grid, cudaStream_t st) {
+  batch_convert<PD, PS><<<grid, MRHS_BS, 0, st>>>(b, active);
+}
+
+cudaError_t batch_reliable_update(BatchCtx& c, const Plan& pl, bool accumulate, cudaStream_t st) {
+  RedScratch rs = scratch();
+  const int grid = blas_grid_tiles(pl.ntiles);
+  cudaError_t e;
+  if (accumulate) {
+    if (c.xprec == WD_F64)
+      batch_ru_accumulate<WD_F64><<<grid, MRHS_BS, 0, st>>>(pl.ru, c.active);
+    else
+      batch_ru_accumulate<WD_F32><<<grid, MRHS_BS, 0, st>>>(pl.ru, c.active);
+    if ((e = cudaGetLastError())) return e;
+  }
+  c.dslash_calls += 4;
+  if ((e = launch_mrhs(WD_F64, pl.r_t64, c.orecon, false, c.active, rs, nullptr, st))) return e;
+  if ((e = launch_mrhs(WD_F64, pl.r_r64, c.orecon, false, c.active, rs, c.sc.r64, st))) return e;
+  switch (c.sprec) {
+    case WD_F64: convert_b<WD_F64, WD_F64>(pl.cvt_r, c.active, grid, st); break;
+    case WD_F32: convert_b<WD_F32, WD_F64>(pl.cvt_r, c.active, grid, st); break;
+    case WD_F16: convert_b<WD_F16, WD_F64>(pl.cvt_r, c.active, grid, st); break;
+  }
+  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_mrhs(c.sprec, pl.d_oe_r_dag, c.srecon, true, c.active, rs, nullptr, st))) return e;
+  if ((e = launch_mrhs(c.sprec, pl.d_eo_s_dag, c.srecon, true, c.active, rs, c.sc.gamma[0], st)))
+    return e;
+  switch (c.sprec) {
+    case WD_F64: convert_b<WD_F64, WD_F64>(pl.cvt_p, c.active, grid, st); break;
+    case WD_F32: convert_b<WD_F32, WD_F32>(pl.cvt_p, c.active, grid, st); break;
+    case WD_F16: convert_b<WD_F16, WD_F16>(pl.cvt_p, c.active, grid, st); break;
+  }
+  return cudaGetLastError();
+}
+
+bool dev_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+#define WD_BCK(call)                          \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) {                  \
+      state().last_cuda_error = (int)e_;      \
+      free_ctx(c);                            \
+      return WD_ERR_CUDA;                     \
+    }                                         \
+  } while (0)
+
+int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_params* prm,
+                     wd_solve_info* infos) {
+  const auto t0 = std::chrono::steady_clock::now();
+  auto secs = [&](std::chrono::steady_clock::time_point a) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+  };
+  wd_solve_params P;
+  wd_solve_params_default(&P);
+  if (prm) P = *prm;
+  if (P.inner_prec < WD_F64 || P.inner_prec > WD_F16) return WD_ERR_PREC;
+  if (link_bytes(P.inner_prec, P.inner_recon) == 0 || link_bytes(WD_F64, P.outer_recon) == 0)
+    return WD_ERR_PREC;
+  if (!(P.tol > 0) || P.maxiter < 0 || P.reliable_interval < 1) return WD_ERR_ARG;
+  const int chunk = P.check_interval < 2 ? 2 : (P.check_interval & ~1);
+  cudaStream_t st = state().stream;
+
+  BatchCtx c;
+  c.sprec = P.inner_prec;
+  c.srecon = P.inner_recon;
+  c.orecon = P.outer_recon;
+  c.xprec = P.inner_prec == WD_F64 ? WD_F64 : WD_F32;
+  int tile0 = 0, nr = 0;
+  for (int j = 0; j < nprob; j++) {
+    BatchProblemWs w;
+    std::memcpy(w.dims, probs[j].dims, sizeof(w.dims));
+    w.kappa = probs[j].kappa;
+    w.nrhs = probs[j].nrhs;
+    w.rhs0 = nr;
+    w.g = make_geom(w.dims);
+    w.tile0 = tile0;
+    w.ntiles = (w.g.Vh + MRHS_BS - 1) / MRHS_BS;
+    tile0 += w.ntiles;
+    nr += w.nrhs;
+    c.pw.push_back(w);
+  }
+  c.nr = nr;
+
+  // ---- allocation ----
+  for (auto& w : c.pw) {
+    const size_t h64 = spinor_half_bytes(w.g, WD_F64), hs = spinor_half_bytes(w.g, c.sprec);
+    const size_t hx = spinor_half_bytes(w.g, c.xprec), n = (size_t)w.nrhs;
+    WD_BCK(dalloc(c, &w.g64, gauge_bytes(w.g, WD_F64, c.orecon)));
+    if (c.sprec == WD_F64 && c.srecon == c.orecon)
+      w.gs = w.g64;
+    else
+      WD_BCK(dalloc(c, &w.gs, gauge_bytes(w.g, c.sprec, c.srecon)));
+    void* v;
+    WD_BCK(dalloc(c, &v, n * 2 * h64)); w.b64 = (char*)v;
+    WD_BCK(dalloc(c, &v, n * 2 * h64)); w.x64 = (char*)v;
+    WD_BCK(dalloc(c, &v, n * 2 * h64)); w.rf64 = (char*)v;
+    WD_BCK(dalloc(c, &v, n * h64)); w.bhat = (char*)v;
+    WD_BCK(dalloc(c, &v, n * h64)); w.r64 = (char*)v;
+    WD_BCK(dalloc(c, &v, n * h64)); w.t64 = (char*)v;
+    WD_BCK(dalloc(c, &v, n * hs)); w.p = (char*)v;
+    WD_BCK(dalloc(c, &v, n * hs)); w.q = (char*)v;
+    WD_BCK(dalloc(c, &v, n * hs)); w.r = (char*)v;
+    WD_BCK(dalloc(c, &v, n * hs)); w.s = (char*)v;
+    WD_BCK(dalloc(c, &v, n * hs)); w.ts = (char*)v;
+    WD_BCK(dalloc(c, &v, n * hx)); w.xs = (char*)v;
+  }
+  {
+    void* v;
+    WD_BCK(dalloc(c, &v, 8 * (size_t)nr * sizeof(double)));
+    c.scal = (double*)v;
+    WD_BCK(cudaMemsetAsync(c.scal, 0, 8 * (size_t)nr * sizeof(double), st));
+    WD_BCK(cudaMallocHost(&c.scal_h, 8 * (size_t)nr * sizeof(double)));
+    WD_BCK(dalloc(c, &v, (size_t)nr * sizeof(int)));
+    c.active = (int*)v;
+    WD_BCK(cudaMallocHost(&c.active_h, (size_t)nr * sizeof(int)));
+    double* s = c.scal;
+    c.sc.gamma[0] = s; c.sc.gamma[1] = s + nr; c.sc.qq = s + 2 * nr; c.sc.rr = s + 3 * nr;
+    c.sc.r64 = s + 4 * nr; c.sc.bnorm2 = s + 5 * nr; c.sc.res_e = s + 6 * nr;
+    c.sc.res_o = s + 7 * nr;
+    WD_BCK(cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking));
+    WD_BCK(ensure_scratch((size_t)tile0 * MRHS_MAX + 4096));
+  }
+  for (int g = 0; g < nr; g++) c.active_h[g] = 1;
+  WD_BCK(cudaMemcpyAsync(c.active, c.active_h, nr * sizeof(int), cudaMemcpyHostToDevice, st));
+
+  // ---- stage and pack ----
+  for (int j = 0; j < nprob; j++) {
+    BatchProblemWs& w = c.pw[j];
+    const size_t V = 2 * (size_t)w.g.Vh, fb = V * 24 * sizeof(double);
+    const size_t h64 = spinor_half_bytes(w.g, WD_F64);
+    const double* gd = probs[j].gauge;
+    if (!dev_ptr(gd)) {
+      void* v;
+      WD_BCK(dalloc(c, &v, 4 * V * 18 * sizeof(double)));
+      WD_BCK(cudaMemcpyAsync(v, gd, 4 * V * 18 * sizeof(double), cudaMemcpyHostToDevice, st));
+      gd = (const double*)v;
+    }
+    WD_BCK(pack_gauge(w.g64, gd, w.g, WD_F64, c.orecon, st));
+    if (w.gs != w.g64) WD_BCK(pack_gauge(w.gs, gd, w.g, c.sprec, c.srecon, st));
+    const double* bd = probs[j].b;
+    if (!dev_ptr(bd)) {
+      void* v;
+      WD_BCK(dalloc(c, &v, (size_t)w.nrhs * fb));
+      w.canon = (double*)v;
+      WD_BCK(cudaMemcpyAsync(w.canon, bd, (size_t)w.nrhs * fb, cudaMemcpyHostToDevice, st));
+      bd = w.canon;
+    }
+    for (int r = 0; r < w.nrhs; r++) {
+      WD_BCK(pack_spinor(w.b64 + r * 2 * h64, bd + (size_t)r * V * 24, w.g, WD_FULL, WD_F64, st));
+      WD_BCK(norm2(c.sc.bnorm2 + w.rhs0 + r, w.b64 + r * 2 * h64, w.g, WD_F64, 2, st));
+    }
+    if (P.use_initial_guess) {
+      const double* xd = probs[j].x;
+      if (!dev_ptr(xd)) {
+        if (!w.canon) {
+          void* v;
+          WD_BCK(dalloc(c, &v, (size_t)w.nrhs * fb));
+          w.canon = (double*)v;
+        }
+        WD_BCK(cudaMemcpyAsync(w.canon, xd, (size_t)w.nrhs * fb, cudaMemcpyHostToDevice, st));
+        xd = w.canon;
+      }
+      for (int r = 0; r < w.nrhs; r++)
+        WD_BCK(pack_spinor(w.x64 + r * 2 * h64, xd + (size_t)r * V * 24, w.g, WD_FULL, WD_F64, st));
+    } else {
+      WD_BCK(cudaMemsetAsync(w.x64, 0, (size_t)w.nrhs * 2 * h64, st));
+    }
+    WD_BCK(cudaMemsetAsync(w.xs, 0, (size_t)w.nrhs * spinor_half_bytes(w.g, c.xprec), st));
+  }
+  Plan pl;
+  build_plan(c, pl);
+  {
+    RedScratch rs = scratch();
+    c.dslash_calls += 1;
+    WD_BCK(launch_mrhs(WD_F64, pl.bhat, c.orecon, false, c.active, rs, nullptr, st));
+  }
+  WD_BCK(batch_reliable_update(c, pl, false, st));
+  auto read_scal = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(c.scal_h, c.scal, 8 * (size_t)nr * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+  };
+  WD_BCK(read_scal());
+  const double* H = c.scal_h;
+  std::vector<double> target(nr);
+  std::vector<int> status(nr, WD_ERR_NOCONV), iters(nr, 0), rus(nr, 0);
+  int nact = 0;
+  for (int g = 0; g < nr; g++) {
+    double bn = std::sqrt(H[5 * nr + g]);
+    target[g] = P.tol * bn * 0.9;
+    if (!std::isfinite(bn)) {
+      status[g] = WD_ERR_NONFINITE;
+      c.active_h[g] = 0;
+    } else if (!(bn > 0) || std::sqrt(H[4 * nr + g]) <= target[g]) {
+      status[g] = WD_OK;
+      c.active_h[g] = 0;
+    } else {
+      nact++;
+    }
+  }
+  WD_BCK(cudaMemcpyAsync(c.active, c.active_h, nr * sizeof(int), cudaMemcpyHostToDevice, st));
+  const double t_setup = secs(t0);
+
+  // ---- the iteration graph ----
+  cudaGraphExec_t exec = nullptr;
+  if (P.use_graph && nact > 0) {
+    cudaGraph_t graph = nullptr;
+    WD_BCK(cudaStreamBeginCapture(c.cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    const double calls = c.dslash_calls;
+    for (int k = 0; k < chunk && ce == cudaSuccess; k++) ce = batch_iteration(c, pl, k & 1, c.cap);
+    c.dslash_calls = calls;
+    cudaError_t ee = cudaStreamEndCapture(c.cap, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      state().last_cuda_error = (int)(ce != cudaSuccess ? ce : ee);
+      free_ctx(c);
+      return WD_ERR_CUDA;
+    }
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      state().last_cuda_error = (int)ie;
+      free_ctx(c);
+      return WD_ERR_CUDA;
+    }
+  }
+
+  int it = 0, last_ru = 0;
+  double t_ru = 0.0;
+  const auto t_loop = std::chrono::steady_clock::now();
+  int err = WD_OK;
+  while (nact > 0 && it < P.maxiter) {
+    cudaError_t e;
+    if (exec) {
+      e = cudaGraphLaunch(exec, st);
+      c.dslash_calls += 4.0 * chunk;
+    } else {
+      e = cudaSuccess;
+      for (int k = 0; k < chunk && e == cudaSuccess; k++) e = batch_iteration(c, pl, k & 1, st);
+    }
+    if (e == cudaSuccess) e = read_scal();
+    if (e != cudaSuccess) { state().last_cuda_error = (int)e; err = WD_ERR_CUDA; break; }
+    it += chunk;
+    bool any_done = false;
+    for (int g = 0; g < nr; g++) {
+      if (!c.active_h[g]) continue;
+      iters[g] += chunk;
+      const double rr = H[3 * nr + g], qq = H[2 * nr + g], ga = H[g];
+      if (!std::isfinite(rr) || !std::isfinite(ga)) {
+        status[g] = WD_ERR_NONFINITE;
+        c.active_h[g] = 0;
+        nact--;
+      } else if (!(qq > 0) || !(ga > 0)) {
+        status[g] = WD_ERR_BREAKDOWN;
+        c.active_h[g] = 0;
+        nact--;
+      } else if (std::sqrt(rr) <= target[g]) {
+        any_done = true;
+      }
+    }
+    if (nact > 0 && (any_done || it - last_ru >= (c.sprec == WD_F64 ? 0x7fffffff : P.reliable_interval) ||
+                     it >= P.maxiter)) {
+      const auto ta = std::chrono::steady_clock::now();
+      e = batch_reliable_update(c, pl, true, st);
+      if (e == cudaSuccess) e = read_scal();
+      t_ru += secs(ta);
+      if (e != cudaSuccess) { state().last_cuda_error = (int)e; err = WD_ERR_CUDA; break; }
+      last_ru = it;
+      for (int g = 0; g < nr; g++) {
+        if (!c.active_h[g]) continue;
+        rus[g]++;
+        const double r = std::sqrt(H[4 * nr + g]);
+        if (!std::isfinite(r)) {
+          status[g] = WD_ERR_NONFINITE;
+          c.active_h[g] = 0;
+          nact--;
+        } else if (r <= target[g]) {
+          status[g] = WD_OK;
+          c.active_h[g] = 0;
+          nact--;
+        }
+      }
+    }
+    e = cudaMemcpyAsync(c.active, c.active_h, nr * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { state().last_cuda_error = (int)e; err = WD_ERR_CUDA; break; }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  const double t_iter = secs(t_loop) - t_ru;
+  if (err != WD_OK) {
+    free_ctx(c);
+    return err;
+  }
+  // right-hand sides still active at maxiter keep their last reliable update
+  const auto t_fin = std::chrono::steady_clock::now();
+  for (int g = 0; g < nr; g++) c.active_h[g] = 1;
+  WD_BCK(cudaMemcpyAsync(c.active, c.active_h, nr * sizeof(int), cudaMemcpyHostToDevice, st));
+  {
+    RedScratch rs = scratch();
+    c.dslash_calls += 3;
+    WD_BCK(launch_mrhs(WD_F64, pl.xo, c.orecon, false, c.active, rs, nullptr, st));
+    WD_BCK(launch_mrhs(WD_F64, pl.rf_e, c.orecon, false, c.active, rs, c.sc.res_e, st));
+    WD_BCK(launch_mrhs(WD_F64, pl.rf_o, c.orecon, false, c.active, rs, c.sc.res_o, st));
+  }
+  for (int j = 0; j < nprob; j++) {
+    BatchProblemWs& w = c.pw[j];
+    const size_t V = 2 * (size_t)w.g.Vh, fb = V * 24 * sizeof(double);
+    const size_t h64 = spinor_half_bytes(w.g, WD_F64);
+    double* xo = probs[j].x;
+    const bool xdev = dev_ptr(xo);
+    double* dst = xdev ? xo : w.canon;
+    if (!dst) {
+      void* v;
+      WD_BCK(dalloc(c, &v, (size_t)w.nrhs * fb));
+      w.canon = (double*)v;
+      dst = w.canon;
+    }
+    for (int r = 0; r < w.nrhs; r++)
+      WD_BCK(unpack_spinor(dst + (size_t)r * V * 24, w.x64 + r * 2 * h64, w.g, WD_FULL, WD_F64, st));
+    if (!xdev)
+      WD_BCK(cudaMemcpyAsync(xo, dst, (size_t)w.nrhs * fb, cudaMemcpyDeviceToHost, st));
+  }
+  WD_BCK(read_scal());
+  const double t_final = secs(t_fin);
+  const double total = secs(t0);
+  int worst = WD_OK;
+  for (int g = 0; g < nr; g++) {
+    const double bn = std::sqrt(H[5 * nr + g]);
+    const double rel = bn > 0 ? std::sqrt(H[6 * nr + g] + H[7 * nr + g]) / bn : 0.0;
+    if (status[g] == WD_OK && !(rel <= P.tol)) status[g] = WD_ERR_NOCONV;
+    if (status[g] != WD_OK && worst == WD_OK) worst = status[g];
+    if (infos) {
+      wd_solve_info& I = infos[g];
+      std::memset(&I, 0, sizeof(I));
+      I.iters = iters[g];
+      I.reliable_updates = rus[g];
+      I.status = status[g];
+      I.true_residual = rel;
+      I.seconds = total;
+      I.dslash_calls = c.dslash_calls;
+      I.setup_seconds = t_setup;
+      I.iterate_seconds = t_iter;
+      I.reliable_seconds = t_ru;
+      I.final_seconds = t_final;
+    }
+  }
+  free_ctx(c);
+  return worst;
+}
+
+// single problem, many right-hand sides: one hopping application
+cudaError_t dslash_mrhs(void* out, const void* in, const void* gauge, int parity, int dagger,
+                        double a, const void* x, double bx, int nrhs, double* norms,
+                        const Geom& g, int prec, int recon, cudaStream_t st) {
+  MrhsBatch bt;
+  std::memset(&bt, 0, sizeof(bt));
+  bt.nprob = 1;
+  bt.ntiles = (g.Vh + MRHS_BS - 1) / MRHS_BS;
+  MrhsProblem& m = bt.p[0];
+  const size_t h = spinor_half_bytes(g, prec);
+  m.g = g;
+  m.gauge = gauge;
+  m.nrhs = nrhs;
+  m.rhs0 = 0;
+  m.tile0 = 0;
+  m.ntiles = bt.ntiles;
+  m.parity = parity;
+  m.a = a;
+  m.bx = bx;
+  m.out = out;
+  m.in = in;
+  m.x = x;
+  m.s_out = m.s_in = m.s_x = h;
+  if (norms) {
+    cudaError_t e = ensure_scratch((size_t)bt.ntiles * MRHS_MAX + 1024);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_mrhs(prec, bt, recon, dagger != 0, nullptr, scratch(), norms, st);
+}
+
+}  // namespace wd

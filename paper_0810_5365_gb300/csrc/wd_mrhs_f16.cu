@@ -1,0 +1,11 @@
+// Instances of the multi-right-hand-side hopping kernel for WD_F16 fields.
+#include "wd_mrhs.cuh"
+
+namespace wd {
+
+cudaError_t launch_mrhs_f16(const MrhsBatch& bt, int recon, bool dagger, const int* active,
+                            RedScratch rs, double* norm_out, int grid, cudaStream_t st) {
+  return launch_mrhs_prec<WD_F16>(bt, recon, dagger, active, rs, norm_out, grid, st);
+}
+
+}  // namespace wd

@@ -36,7 +36,7 @@ EXPORTS = [
     "wd_spinor_bytes", "wd_gauge_bytes", "wd_pack_gauge", "wd_pack_spinor", "wd_unpack_spinor",
     "wd_convert_spinor", "wd_dslash", "wd_dslash_dag", "wd_dslash_ex", "wd_mhat", "wd_norm2",
     "wd_cdot", "wd_axpby", "wd_solve_params_default", "wd_solve", "wd_solve_ex",
-    "wd_dslash_ex_noalloc",
+    "wd_dslash_ex_noalloc", "wd_dslash_mrhs", "wd_solve_batch",
 ]
 
 
@@ -54,6 +54,11 @@ class wd_solve_params(C.Structure):
                 ("reliable_interval", C.c_int), ("check_interval", C.c_int),
                 ("maxiter", C.c_int), ("use_graph", C.c_int), ("use_initial_guess", C.c_int),
                 ("tol", C.c_double)]
+
+
+class wd_batch_problem(C.Structure):
+    _fields_ = [("dims", C.c_int * 4), ("kappa", C.c_double), ("nrhs", C.c_int),
+                ("gauge", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p)]
 
 
 class wd_solve_info(C.Structure):
@@ -101,6 +106,10 @@ def lib():
                                            C.c_double, vp, C.c_double, dp, i4, C.c_int,
                                            C.c_int]),
         "wd_mhat": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_int, i4, C.c_int, C.c_int]),
+        "wd_dslash_mrhs": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
+                                     C.c_int, dp, i4, C.c_int, C.c_int]),
+        "wd_solve_batch": (C.c_int, [C.POINTER(wd_batch_problem), C.c_int,
+                                     C.POINTER(wd_solve_params), C.POINTER(wd_solve_info)]),
         "wd_norm2": (C.c_int, [dp, vp, i4, C.c_int, C.c_int]),
         "wd_cdot": (C.c_int, [dp, vp, vp, i4, C.c_int, C.c_int]),
         "wd_axpby": (C.c_int, [C.c_double, vp, C.c_double, vp, i4, C.c_int, C.c_int]),
@@ -219,6 +228,35 @@ def wd_dslash_ex_noalloc(out, inp, gauge, parity, dagger, a, x, bx, y, cy, norm2
     _ck(lib().wd_dslash_ex_noalloc(_p(out), _p(inp), _p(gauge), int(parity), int(dagger),
                                    float(a), _p(x), float(bx), _p(y), float(cy), _p(norm2),
                                    _d(dims), int(prec), int(recon)), "wd_dslash_ex_noalloc")
+
+
+def wd_dslash_mrhs(out, inp, gauge, parity, dagger, a, x, bx, nrhs, norm2, dims, prec, recon=12):
+    _ck(lib().wd_dslash_mrhs(_p(out), _p(inp), _p(gauge), int(parity), int(dagger), float(a),
+                             _p(x), float(bx), int(nrhs), _p(norm2), _d(dims), int(prec),
+                             int(recon)), "wd_dslash_mrhs")
+
+
+def wd_solve_batch(problems, params=None, check=True):
+    """problems: list of dicts with dims, kappa, nrhs, gauge, b, x (buffers as
+    accepted by _p: host numpy arrays or device tensors).  Returns the status
+    and one info dict per right-hand side."""
+    n = len(problems)
+    arr = (wd_batch_problem * n)()
+    for j, pr in enumerate(problems):
+        arr[j].dims = (C.c_int * 4)(*[int(v) for v in pr["dims"]])
+        arr[j].kappa = float(pr["kappa"])
+        arr[j].nrhs = int(pr["nrhs"])
+        arr[j].gauge = _p(pr["gauge"])
+        arr[j].b = _p(pr["b"])
+        arr[j].x = _p(pr["x"])
+    nr = sum(int(pr["nrhs"]) for pr in problems)
+    infos = (wd_solve_info * max(nr, 1))()
+    p = params if params is not None else wd_solve_params_default()
+    rc = lib().wd_solve_batch(arr, n, C.byref(p), infos)
+    out = [infos[i].as_dict() for i in range(nr)]
+    if check:
+        _ck(rc, "wd_solve_batch")
+    return rc, out
 
 
 def wd_mhat(out, inp, gauge, tmp, kappa, dagger, dims, prec, recon=12):
