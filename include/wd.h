@@ -64,6 +64,12 @@ extern "C" {
 #endif
 
 enum { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2 };
+
+/* OR into a `recon` argument (12 | WD_TEMPORAL_GAUGE, ...) when the packed
+ * gauge field is in temporal gauge (see wd_gauge_fix_temporal): the hopping
+ * kernels then treat U_t(x) as the identity on every slice but t = L3-1 and
+ * neither load nor apply it. */
+enum { WD_TEMPORAL_GAUGE = 0x100 };
 enum { WD_EVEN = 0, WD_ODD = 1, WD_FULL = -1 };
 
 enum {
@@ -215,6 +221,25 @@ int wd_dslash_mrhs(void *out, const void *in, const void *gauge, int parity, int
                    double a, const void *x, double bx, int nrhs, double *norm2,
                    const int dims[4], int prec, int recon);
 
+/*
+ * Temporal gauge (paper, section "Performance": fixing the temporal links to
+ * the identity on all but one time slice saves their bandwidth, about 10 %).
+ * From the canonical FP64 gauge field U_in (device) compute, on the device,
+ *     omega(x, 0) = 1,  omega(x, t+1) = omega(x, t) U_t(x, t),
+ *     U_out_mu(x) = omega(x) U_mu(x) omega(x+mu)^+ ,
+ * so that U_out_t(x) = 1 exactly for t < L3-1.  omega_out: canonical
+ * [V][3][3].  Pack U_out and pass recon | WD_TEMPORAL_GAUGE to the hopping
+ * calls.  D[U_out] = omega D[U] omega^+ (gauge covariance).
+ * U_out must not alias U_in.
+ */
+int wd_gauge_fix_temporal(double *U_out, double *omega_out, const double *U_in,
+                          const int dims[4]);
+
+/* out(x) = omega(x) in(x) (dagger = 0) or omega(x)^+ in(x) (dagger = 1);
+ * canonical FP64 full spinors on the device; out may alias in. */
+int wd_rotate_spinor(double *out, const double *in, const double *omega, const int dims[4],
+                     int dagger);
+
 /* ------------------------------------------------------------------ */
 /* BLAS-like kernels and FP64 reductions (paper: dot product by        */
 /* parallel reduction in double precision; "BLAS-like" vector kernels) */
@@ -246,6 +271,7 @@ typedef struct {
     int use_graph;           /* capture check_interval iterations as a CUDA graph */
     int use_initial_guess;   /* x holds a starting guess (restart / resume) */
     double tol;              /* target ||b - D x|| / ||b|| (default 1e-10) */
+    int gauge_fix;           /* solve in temporal gauge (wd_gauge_fix_temporal) */
 } wd_solve_params;
 
 typedef struct {

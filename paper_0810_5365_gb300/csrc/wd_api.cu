@@ -150,6 +150,8 @@ int wd_convert_spinor(void* dst, int dst_prec, const void* src, int src_prec, co
 int wd_dslash_ex(void* out, const void* in, const void* gauge, int parity, int dagger, double a,
                  const void* x, double bx, const void* y, double cy, double* norm2,
                  const int dims[4], int prec, int recon) {
+  const int tg = (recon & WD_TEMPORAL_GAUGE_BIT) != 0;
+  recon &= ~WD_TEMPORAL_GAUGE_BIT;
   WD_TRY(check_dims(dims));
   WD_TRY(check_prec(prec));
   if (!out || !in || !gauge) return WD_ERR_NULL;
@@ -177,6 +179,7 @@ int wd_dslash_ex(void* out, const void* in, const void* gauge, int parity, int d
   d.rs = scratch();
   d.g = g;
   d.parity = parity;
+  d.tg = tg;
   return cuda_status(launch_dslash(prec, d, recon, dagger != 0, state().stream));
 }
 
@@ -252,6 +255,23 @@ int wd_solve_batch(const wd_batch_problem* problems, int nproblems, const wd_sol
   return solve_batch_impl(problems, nproblems, params, info);
 }
 
+int wd_gauge_fix_temporal(double* U_out, double* omega_out, const double* U_in,
+                          const int dims[4]) {
+  WD_TRY(check_dims(dims));
+  if (!U_out || !omega_out || !U_in) return WD_ERR_NULL;
+  if (!aligned(U_out) || !aligned(omega_out) || !aligned(U_in)) return WD_ERR_ALIGN;
+  if ((const void*)U_out == (const void*)U_in) return WD_ERR_ALIAS;
+  return cuda_status(gauge_fix_temporal(U_out, omega_out, U_in, make_geom(dims), state().stream));
+}
+
+int wd_rotate_spinor(double* out, const double* in, const double* omega, const int dims[4],
+                     int dagger) {
+  WD_TRY(check_dims(dims));
+  if (!out || !in || !omega) return WD_ERR_NULL;
+  if (!aligned(out) || !aligned(in) || !aligned(omega)) return WD_ERR_ALIGN;
+  return cuda_status(rotate_spinor(out, in, omega, make_geom(dims), dagger != 0, state().stream));
+}
+
 int wd_norm2(double* result, const void* x, const int dims[4], int parity, int prec) {
   WD_TRY(check_dims(dims));
   WD_TRY(check_prec(prec));
@@ -294,6 +314,7 @@ void wd_solve_params_default(wd_solve_params* p) {
   p->use_graph = 1;
   p->use_initial_guess = 0;
   p->tol = 1e-10;
+  p->gauge_fix = 0;
 }
 
 int wd_solve_ex(double* x, const double* b, const double* gauge, double kappa, const int dims[4],

@@ -115,9 +115,9 @@ __global__ void __launch_bounds__(MRHS_BS) batch_update_r(const BlasBatch bt, co
       for (int k = 0; k < 12; k++) {
         a[k].r = fma(-alpha, b[k].r, a[k].r);
         a[k].i = fma(-alpha, b[k].i, a[k].i);
-        t += (double)a[k].r * a[k].r + (double)a[k].i * a[k].i;
       }
       store_spinor<P, R>(fr, cb, VP, a);
+      t = site_norm2(a);
     }
     double v[1] = {t};
     block_sum<1, MRHS_BS>(v, red);

@@ -264,10 +264,7 @@ __global__ void __launch_bounds__(BS) norm2_kernel(double* res, const char* __re
     int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
     cx<R> s[12];
     load_spinor_rw<P, R>(s, x + h * hb, cb, g.Vh_pad);
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < 12; k++) t += (double)s[k].r * s[k].r + (double)s[k].i * s[k].i;
-    acc[0] += t;
+    acc[0] += site_norm2(s);
   }
   double tot[1];
   if (grid_reduce<1, BS>(acc, rs, tot) && threadIdx.x == 0) res[0] = tot[0];
@@ -285,14 +282,7 @@ __global__ void __launch_bounds__(BS) cdot_kernel(double* res, const char* __res
     cx<R> a[12], b[12];
     load_spinor_rw<P, R>(a, x + h * hb, cb, g.Vh_pad);
     load_spinor_rw<P, R>(b, y + h * hb, cb, g.Vh_pad);
-    double re = 0.0, im = 0.0;
-#pragma unroll
-    for (int k = 0; k < 12; k++) {
-      re += (double)a[k].r * b[k].r + (double)a[k].i * b[k].i;
-      im += (double)a[k].r * b[k].i - (double)a[k].i * b[k].r;
-    }
-    acc[0] += re;
-    acc[1] += im;
+    site_cdot(a, b, acc[0], acc[1]);
   }
   double tot[2];
   if (grid_reduce<2, BS>(acc, rs, tot) && threadIdx.x == 0) {

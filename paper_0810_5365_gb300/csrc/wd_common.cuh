@@ -144,6 +144,40 @@ __device__ __forceinline__ cx<R> conj_cross(cx<R> a, cx<R> b, cx<R> c, cx<R> d) 
 }
 
 // ---------------------------------------------------------------------------
+// per-site reductions: the 24 terms of one site are summed in the working
+// precision R; the sum over sites (the global sum) is FP64.  GB300 issues FP64
+// at 1/64 of its FP32 rate, so converting every element to double would cost
+// more than the memory traffic of the kernels that fuse these reductions.
+// ---------------------------------------------------------------------------
+
+template <typename R>
+__device__ __forceinline__ double site_norm2(const cx<R> (&v)[12]) {
+  R t = (R)0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    t = fma(v[k].r, v[k].r, t);
+    t = fma(v[k].i, v[k].i, t);
+  }
+  return (double)t;
+}
+
+// re + i im += sum_k conj(a_k) b_k
+template <typename R>
+__device__ __forceinline__ void site_cdot(const cx<R> (&a)[12], const cx<R> (&b)[12], double& re,
+                                          double& im) {
+  R r = (R)0, i = (R)0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    r = fma(a[k].r, b[k].r, r);
+    r = fma(a[k].i, b[k].i, r);
+    i = fma(a[k].r, b[k].i, i);
+    i = fma(-a[k].i, b[k].r, i);
+  }
+  re += (double)r;
+  im += (double)i;
+}
+
+// ---------------------------------------------------------------------------
 // packed spinor formats (per parity; Vh_pad sites)
 //   WD_F64: NC = 12 double2, group k = complex component k = spin*3 + colour
 //   WD_F32: NC =  6 float4,  group k = components 2k, 2k+1

@@ -161,28 +161,35 @@ __device__ __forceinline__ R load_project(cx<R> (&h)[6], const void* __restrict_
 // One hop: neighbour site nb (opposite parity), link in `region` at site lcb.
 // FWD: U h ; backward: U^+ h.  flip: the hop crosses the antiperiodic time
 // boundary (applied as a sign at accumulation).
+// unit: the link is the identity (temporal gauge, time hop off the boundary
+// slice): neither loaded nor multiplied.
 template <int P, int RC, int MU, int S, bool FWD, typename R>
 __device__ __forceinline__ void hop(cx<R> (&acc)[12], const void* __restrict__ in,
                                     const void* __restrict__ gauge, int nb, int region, int lcb,
-                                    bool flip, int Vh_pad) {
+                                    bool flip, int Vh_pad, bool unit = false) {
   cx<R> h[6];
   R sc = load_project<P, MU, S, R>(h, in, nb, Vh_pad);
-  cx<R> u[9];
-  load_link<P, RC, R>(u, gauge, region, lcb, Vh_pad);
   cx<R> t[6];
+  if (MU == 3 && unit) {
 #pragma unroll
-  for (int hs = 0; hs < 2; hs++) {
+    for (int k = 0; k < 6; k++) t[k] = h[k];
+  } else {
+    cx<R> u[9];
+    load_link<P, RC, R>(u, gauge, region, lcb, Vh_pad);
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      cx<R> v = mk<R>(0, 0);
+    for (int hs = 0; hs < 2; hs++) {
 #pragma unroll
-      for (int d = 0; d < 3; d++) {
-        if (FWD)
-          v = cmadd(u[c * 3 + d], h[hs * 3 + d], v);
-        else
-          v = cjmadd(u[d * 3 + c], h[hs * 3 + d], v);
+      for (int c = 0; c < 3; c++) {
+        cx<R> v = mk<R>(0, 0);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          if (FWD)
+            v = cmadd(u[c * 3 + d], h[hs * 3 + d], v);
+          else
+            v = cjmadd(u[d * 3 + c], h[hs * 3 + d], v);
+        }
+        t[hs * 3 + c] = v;
       }
-      t[hs * 3 + c] = v;
     }
   }
   if constexpr (P == WD_F16) {
@@ -211,19 +218,25 @@ struct RawF16 {
 
 __device__ __forceinline__ RawF16 fetch_f16(const void* __restrict__ in,
                                             const void* __restrict__ gauge, int nb, int region,
-                                            int lcb, int VP) {
+                                            int lcb, int VP, bool unit = false) {
   RawF16 r;
   const int4* p = (const int4*)in;
 #pragma unroll
   for (int k = 0; k < 3; k++) r.s[k] = __ldg(p + sbi(nb, k, 3));
   r.sc = __ldg((const float*)((const char*)in + (size_t)VP * 48) + nb);
-  r.la = __ldg((const int4*)gauge + (size_t)region * VP + lcb);
-  r.lb = __ldg((const int2*)((const char*)gauge + (size_t)8 * VP * 16) + (size_t)region * VP + lcb);
+  if (!unit) {
+    r.la = __ldg((const int4*)gauge + (size_t)region * VP + lcb);
+    r.lb = __ldg((const int2*)((const char*)gauge + (size_t)8 * VP * 16) + (size_t)region * VP + lcb);
+  } else {
+    r.la = make_int4(0, 0, 0, 0);
+    r.lb = make_int2(0, 0);
+  }
   return r;
 }
 
 template <int MU, int S, bool FWD>
-__device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& r, bool flip) {
+__device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& r, bool flip,
+                                            bool unit = false) {
   __half2 v[12];
 #pragma unroll
   for (int k = 0; k < 3; k++) {
@@ -239,34 +252,39 @@ __device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& 
     float2 f = __half22float2(hh[k]);
     h[k] = mk<float>(f.x, f.y);
   }
-  cx<float> u[9];
-  const __half2* ha = reinterpret_cast<const __half2*>(&r.la);
-  const __half2* hb = reinterpret_cast<const __half2*>(&r.lb);
-#pragma unroll
-  for (int j = 0; j < 4; j++) {
-    float2 f = __half22float2(ha[j]);
-    u[j] = mk<float>(f.x, f.y);
-  }
-#pragma unroll
-  for (int j = 0; j < 2; j++) {
-    float2 f = __half22float2(hb[j]);
-    u[4 + j] = mk<float>(f.x, f.y);
-  }
-  reconstruct_row2(u);
   cx<float> t[6];
+  if (MU == 3 && unit) {
 #pragma unroll
-  for (int hs = 0; hs < 2; hs++) {
+    for (int k = 0; k < 6; k++) t[k] = h[k];
+  } else {
+    cx<float> u[9];
+    const __half2* ha = reinterpret_cast<const __half2*>(&r.la);
+    const __half2* hb = reinterpret_cast<const __half2*>(&r.lb);
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      cx<float> w = mk<float>(0, 0);
+    for (int j = 0; j < 4; j++) {
+      float2 f = __half22float2(ha[j]);
+      u[j] = mk<float>(f.x, f.y);
+    }
 #pragma unroll
-      for (int d = 0; d < 3; d++) {
-        if (FWD)
-          w = cmadd(u[c * 3 + d], h[hs * 3 + d], w);
-        else
-          w = cjmadd(u[d * 3 + c], h[hs * 3 + d], w);
+    for (int j = 0; j < 2; j++) {
+      float2 f = __half22float2(hb[j]);
+      u[4 + j] = mk<float>(f.x, f.y);
+    }
+    reconstruct_row2(u);
+#pragma unroll
+    for (int hs = 0; hs < 2; hs++) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        cx<float> w = mk<float>(0, 0);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          if (FWD)
+            w = cmadd(u[c * 3 + d], h[hs * 3 + d], w);
+          else
+            w = cjmadd(u[d * 3 + c], h[hs * 3 + d], w);
+        }
+        t[hs * 3 + c] = w;
       }
-      t[hs * 3 + c] = w;
     }
   }
   const float sc = (MU == 3 && flip) ? -r.sc : r.sc;
@@ -299,6 +317,10 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_ke
     const int b3 = x3 == 0 ? cb + (g.L[3] - 1) * g.S3 : cb - g.S3;
     const bool fflip = x3 == g.L[3] - 1;
     const bool bflip = x3 == 0;
+    // temporal gauge: U_t(x) = 1 unless x3 = L3-1; the backward link
+    // U_t(x - t) is at x3 - 1, the identity unless x3 = 0
+    const bool funit = a.tg && !fflip;
+    const bool bunit = a.tg && !bflip;
 
     // forward hops use (1 - s gamma), backward (1 + s gamma)
     constexpr int SF = DAG ? -1 : 1;
@@ -324,12 +346,12 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_ke
       compute_f16<1, SF, true>(acc, r2, false);
       r1 = WD_F(b2, 4 + q, b2);
       compute_f16<1, SB_, false>(acc, r3, false);
-      r2 = WD_F(f3, 6 + p, cb);
+      r2 = fetch_f16(in, ga, f3, 6 + p, cb, VP, funit);
       compute_f16<2, SF, true>(acc, r0, false);
-      r3 = WD_F(b3, 6 + q, b3);
+      r3 = fetch_f16(in, ga, b3, 6 + q, b3, VP, bunit);
       compute_f16<2, SB_, false>(acc, r1, false);
-      compute_f16<3, SF, true>(acc, r2, fflip);
-      compute_f16<3, SB_, false>(acc, r3, bflip);
+      compute_f16<3, SF, true>(acc, r2, fflip, funit);
+      compute_f16<3, SB_, false>(acc, r3, bflip, bunit);
 #else
       RawF16 r0 = WD_F(f0, 0 + p, cb);
       RawF16 r1 = WD_F(b0, 0 + q, b0);
@@ -342,11 +364,11 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_ke
       compute_f16<1, SB_, false>(acc, r1, false);
       r1 = WD_F(b2, 4 + q, b2);
       compute_f16<2, SF, true>(acc, r0, false);
-      r0 = WD_F(f3, 6 + p, cb);
+      r0 = fetch_f16(in, ga, f3, 6 + p, cb, VP, funit);
       compute_f16<2, SB_, false>(acc, r1, false);
-      r1 = WD_F(b3, 6 + q, b3);
-      compute_f16<3, SF, true>(acc, r0, fflip);
-      compute_f16<3, SB_, false>(acc, r1, bflip);
+      r1 = fetch_f16(in, ga, b3, 6 + q, b3, VP, bunit);
+      compute_f16<3, SF, true>(acc, r0, fflip, funit);
+      compute_f16<3, SB_, false>(acc, r1, bflip, bunit);
 #endif
 #undef WD_F
     } else {
@@ -356,8 +378,8 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_ke
       hop<P, RC, 1, SB_, false>(acc, a.in, a.gauge, b1, 2 + q, b1, false, VP);
       hop<P, RC, 2, SF, true>(acc, a.in, a.gauge, f2, 4 + p, cb, false, VP);
       hop<P, RC, 2, SB_, false>(acc, a.in, a.gauge, b2, 4 + q, b2, false, VP);
-      hop<P, RC, 3, SF, true>(acc, a.in, a.gauge, f3, 6 + p, cb, fflip, VP);
-      hop<P, RC, 3, SB_, false>(acc, a.in, a.gauge, b3, 6 + q, b3, bflip, VP);
+      hop<P, RC, 3, SF, true>(acc, a.in, a.gauge, f3, 6 + p, cb, fflip, VP, funit);
+      hop<P, RC, 3, SB_, false>(acc, a.in, a.gauge, b3, 6 + q, b3, bflip, VP, bunit);
     }
 
     const R ca = (R)a.a;
@@ -389,11 +411,9 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_ke
         // the norm of what was stored (after rounding to half)
         cx<R> v[12];
         load_spinor_rw<P, R>(v, a.out, cb, VP);
-#pragma unroll
-        for (int k = 0; k < 12; k++) nrm += (double)v[k].r * v[k].r + (double)v[k].i * v[k].i;
+        nrm = site_norm2(v);
       } else {
-#pragma unroll
-        for (int k = 0; k < 12; k++) nrm += (double)acc[k].r * acc[k].r + (double)acc[k].i * acc[k].i;
+        nrm = site_norm2(acc);
       }
     }
   }

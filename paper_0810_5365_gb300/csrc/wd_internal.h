@@ -49,7 +49,13 @@ struct DslashArgs {
   RedScratch rs;
   Geom g;
   int parity;        // parity of the output sites
+  int tg = 0;        // links in temporal gauge: U_t = 1 off the last time slice
 };
+
+// bit OR-ed into a `recon` argument: the gauge field is in temporal gauge
+// (time links are the identity except on the slice t = L3-1), so the hopping
+// kernels skip those links' loads and mat-vecs
+constexpr int WD_TEMPORAL_GAUGE_BIT = 0x100;
 
 cudaError_t launch_dslash_f64(const DslashArgs& a, int recon, bool dagger, cudaStream_t st);
 cudaError_t launch_dslash_f32(const DslashArgs& a, int recon, bool dagger, cudaStream_t st);
@@ -108,5 +114,11 @@ cudaError_t cdot(double* res, const void* x, const void* y, const Geom& g, int p
                  cudaStream_t st);
 cudaError_t axpby(double a, const void* x, double b, void* y, const Geom& g, int prec, int nh,
                   cudaStream_t st);
+
+// temporal gauge (wd_gauge.cu): canonical FP64 fields on the device
+cudaError_t gauge_fix_temporal(double* Uout, double* omega, const double* Uin, const Geom& g,
+                               cudaStream_t st);
+cudaError_t rotate_spinor(double* out, const double* in, const double* omega, const Geom& g,
+                          int dagger, cudaStream_t st);
 
 }  // namespace wd

@@ -237,12 +237,9 @@ __global__ void __launch_bounds__(MRHS_BS) mrhs_dslash_kernel(const MrhsBatch bt
           if constexpr (P == WD_F16) {
             cx<R> v[12];
             load_spinor_rw<P, R>(v, out, cb, VP);
-#pragma unroll
-            for (int k = 0; k < 12; k++) nrm += (double)v[k].r * v[k].r + (double)v[k].i * v[k].i;
+            nrm = site_norm2(v);
           } else {
-#pragma unroll
-            for (int k = 0; k < 12; k++)
-              nrm += (double)acc[k].r * acc[k].r + (double)acc[k].i * acc[k].i;
+            nrm = site_norm2(acc);
           }
         }
       }

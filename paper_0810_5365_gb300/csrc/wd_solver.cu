@@ -47,15 +47,13 @@ __global__ void __launch_bounds__(BS) cg_update_r(char* r, const char* __restric
     cx<R> a[12], b[12];
     load_spinor_rw<P, R>(a, r, cb, g.Vh_pad);
     load_spinor_rw<P, R>(b, q, cb, g.Vh_pad);
-    double t = 0.0;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
       a[k].r = fma(-alpha, b[k].r, a[k].r);
       a[k].i = fma(-alpha, b[k].i, a[k].i);
-      t += (double)a[k].r * a[k].r + (double)a[k].i * a[k].i;
     }
     store_spinor<P, R>(r, cb, g.Vh_pad, a);
-    acc[0] += t;
+    acc[0] += site_norm2(a);
   }
   double tot[1];
   if (grid_reduce<1, BS>(acc, rs, tot) && threadIdx.x == 0) sc->rr = tot[0];
@@ -132,6 +130,9 @@ struct Workspace {
   void* xs = nullptr;    // sloppy solution accumulator (FP32 for FP16 inner)
   double* canon_spinor = nullptr;  // staging for host spinors
   double* canon_gauge = nullptr;   // staging for a host gauge field
+  double* gf_gauge = nullptr;      // temporal-gauge links (canonical)
+  double* gf_omega = nullptr;      // the gauge transformation (canonical)
+  double* gf_spinor = nullptr;     // rotated right-hand side (canonical)
   CgScalars* sc = nullptr;
   CgScalars* sc_host = nullptr;    // pinned
   cudaStream_t cap = nullptr;      // private capture stream
@@ -145,7 +146,8 @@ static Workspace& ws() {
 static void ws_free() {
   Workspace& w = ws();
   void* bufs[] = {w.g64, w.b64, w.x64, w.rf64, w.bhat, w.r64, w.t64, w.p, w.q, w.r,
-                  w.s, w.ts, w.xs, w.canon_spinor, w.canon_gauge, w.sc};
+                  w.s, w.ts, w.xs, w.canon_spinor, w.canon_gauge, w.sc,
+                  w.gf_gauge, w.gf_omega, w.gf_spinor};
   if (w.gs && w.gs != w.g64) cudaFree(w.gs);
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -228,6 +230,7 @@ struct Ctx {
   cudaStream_t st;
   double kappa;
   int sprec, srecon, orecon, xprec;
+  int tg = 0;
   double dslash_calls = 0;
 };
 
@@ -247,6 +250,7 @@ cudaError_t dsl(Ctx& c, int prec, int recon, const void* gauge, void* out, const
   d.rs = scratch();
   d.g = c.w->g;
   d.parity = parity;
+  d.tg = c.tg;
   c.dslash_calls += 1;
   return launch_dslash(prec, d, recon, dagger != 0, st);
 }
@@ -371,6 +375,17 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
                           cudaMemcpyHostToDevice, st));
     gdev = w.canon_gauge;
   }
+  if (P.gauge_fix) {
+    // solve D[U'] x' = omega b in temporal gauge, then x = omega^+ x'
+    if (!w.gf_gauge) WD_CK(cudaMalloc(&w.gf_gauge, 4 * V * 18 * sizeof(double)));
+    if (!w.gf_omega) WD_CK(cudaMalloc(&w.gf_omega, V * 18 * sizeof(double)));
+    if (!w.gf_spinor) WD_CK(cudaMalloc(&w.gf_spinor, V * 24 * sizeof(double)));
+    WD_CK(gauge_fix_temporal(w.gf_gauge, w.gf_omega, gdev, g, st));
+    WD_CK(rotate_spinor(w.gf_spinor, bdev, w.gf_omega, g, 0, st));
+    gdev = w.gf_gauge;
+    bdev = w.gf_spinor;
+    c.tg = 1;
+  }
   WD_CK(pack_gauge(w.g64, gdev, g, WD_F64, P.outer_recon, st));
   if (w.gs != w.g64) WD_CK(pack_gauge(w.gs, gdev, g, P.inner_prec, P.inner_recon, st));
   WD_CK(pack_spinor(w.b64, bdev, g, WD_FULL, WD_F64, st));
@@ -382,6 +397,10 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
       if (!w.canon_spinor) WD_CK(cudaMalloc(&w.canon_spinor, V * 24 * sizeof(double)));
       WD_CK(cudaMemcpyAsync(w.canon_spinor, x, V * 24 * sizeof(double), cudaMemcpyHostToDevice, st));
       xdev = w.canon_spinor;
+    }
+    if (P.gauge_fix) {
+      WD_CK(rotate_spinor(w.gf_spinor, xdev, w.gf_omega, g, 0, st));
+      xdev = w.gf_spinor;
     }
     WD_CK(pack_spinor(w.x64, xdev, g, WD_FULL, WD_F64, st));
   } else {
@@ -503,6 +522,7 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
   if (!x_dev && !w.canon_spinor) WD_CK(cudaMalloc(&w.canon_spinor, V * 24 * sizeof(double)));
   xdev = x_dev ? x : w.canon_spinor;
   WD_CK(unpack_spinor(xdev, w.x64, g, WD_FULL, WD_F64, st));
+  if (P.gauge_fix) WD_CK(rotate_spinor(xdev, xdev, w.gf_omega, g, 1, st));
   if (!x_dev)
     WD_CK(cudaMemcpyAsync(x, xdev, V * 24 * sizeof(double), cudaMemcpyDeviceToHost, st));
   WD_CK(read_scalars(c));

@@ -14,6 +14,7 @@ import os
 from .build import LIB
 
 WD_F64, WD_F32, WD_F16 = 0, 1, 2
+WD_TEMPORAL_GAUGE = 0x100
 WD_EVEN, WD_ODD, WD_FULL = 0, 1, -1
 
 WD_OK = 0
@@ -36,7 +37,8 @@ EXPORTS = [
     "wd_spinor_bytes", "wd_gauge_bytes", "wd_pack_gauge", "wd_pack_spinor", "wd_unpack_spinor",
     "wd_convert_spinor", "wd_dslash", "wd_dslash_dag", "wd_dslash_ex", "wd_mhat", "wd_norm2",
     "wd_cdot", "wd_axpby", "wd_solve_params_default", "wd_solve", "wd_solve_ex",
-    "wd_dslash_ex_noalloc", "wd_dslash_mrhs", "wd_solve_batch",
+    "wd_dslash_ex_noalloc", "wd_dslash_mrhs", "wd_solve_batch", "wd_gauge_fix_temporal",
+    "wd_rotate_spinor",
 ]
 
 
@@ -53,7 +55,7 @@ class wd_solve_params(C.Structure):
     _fields_ = [("inner_prec", C.c_int), ("inner_recon", C.c_int), ("outer_recon", C.c_int),
                 ("reliable_interval", C.c_int), ("check_interval", C.c_int),
                 ("maxiter", C.c_int), ("use_graph", C.c_int), ("use_initial_guess", C.c_int),
-                ("tol", C.c_double)]
+                ("tol", C.c_double), ("gauge_fix", C.c_int)]
 
 
 class wd_batch_problem(C.Structure):
@@ -106,6 +108,8 @@ def lib():
                                            C.c_double, vp, C.c_double, dp, i4, C.c_int,
                                            C.c_int]),
         "wd_mhat": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_int, i4, C.c_int, C.c_int]),
+        "wd_gauge_fix_temporal": (C.c_int, [dp, dp, dp, i4]),
+        "wd_rotate_spinor": (C.c_int, [dp, dp, dp, i4, C.c_int]),
         "wd_dslash_mrhs": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
                                      C.c_int, dp, i4, C.c_int, C.c_int]),
         "wd_solve_batch": (C.c_int, [C.POINTER(wd_batch_problem), C.c_int,
@@ -257,6 +261,16 @@ def wd_solve_batch(problems, params=None, check=True):
     if check:
         _ck(rc, "wd_solve_batch")
     return rc, out
+
+
+def wd_gauge_fix_temporal(U_out, omega_out, U_in, dims):
+    _ck(lib().wd_gauge_fix_temporal(_p(U_out), _p(omega_out), _p(U_in), _d(dims)),
+        "wd_gauge_fix_temporal")
+
+
+def wd_rotate_spinor(out, inp, omega, dims, dagger=0):
+    _ck(lib().wd_rotate_spinor(_p(out), _p(inp), _p(omega), _d(dims), int(dagger)),
+        "wd_rotate_spinor")
 
 
 def wd_mhat(out, inp, gauge, tmp, kappa, dagger, dims, prec, recon=12):

@@ -8,6 +8,12 @@ import paper_0810_5365_gb300 as W
 PREC_TOL = {W.WD_F64: 1e-13, W.WD_F32: 1e-6, W.WD_F16: 5e-3}
 PREC_NAME = {W.WD_F64: "f64", W.WD_F32: "f32", W.WD_F16: "f16"}
 
+# Relative bound on a reported norm or dot product against numpy's FP64 sum of
+# the stored values.  Each site's 24 terms are summed in the working precision
+# (FP32 for the FP32/FP16 fields): 24 positive terms in float carry at most
+# 24 * 2^-24 = 1.4e-6 relative error; the sum over sites is FP64.
+NORM_TOL = {W.WD_F64: 1e-12, W.WD_F32: 2e-6, W.WD_F16: 2e-6}
+
 
 def dev(a):
     """complex128 numpy array -> contiguous float64 CUDA tensor (same bytes)."""

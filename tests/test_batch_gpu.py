@@ -15,7 +15,7 @@ import torch
 import oracle
 import paper_0810_5365_gb300 as W
 from synth import fields
-from tests._wdutil import PREC_TOL, dev, pack_gauge, rel_l2, rel_max, unpack_spinor
+from tests._wdutil import NORM_TOL, PREC_TOL, dev, pack_gauge, rel_l2, rel_max, unpack_spinor
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,7 @@ def test_mrhs_dslash_matches_oracle(dims, prec, recon, dagger):
         assert rel_l2(got, want) <= tol, (r, rel_l2(got, want))
         assert rel_max(got, want) <= 4 * tol
         n2 = np.vdot(got, got).real
-        assert abs(nrm[r].item() - n2) <= 1e-12 * n2
+        assert abs(nrm[r].item() - n2) <= NORM_TOL[prec] * n2
 
 
 def test_mrhs_agrees_with_single_rhs_kernel():
