@@ -287,11 +287,14 @@ def solve_section(W, torch, reps=3):
     xh = np.zeros_like(b)
     out = {}
     Vh = int(np.prod(dims)) // 2
-    for name, inner, gf in (("f16", W.WD_F16, 0), ("f32", W.WD_F32, 0), ("f64", W.WD_F64, 0),
-                            ("f16_gauge_fixed", W.WD_F16, 1)):
+    for name, inner, gf, sv in (("f16", W.WD_F16, 0, 0), ("f32", W.WD_F32, 0, 0),
+                                ("f64", W.WD_F64, 0, 0), ("f16_gauge_fixed", W.WD_F16, 1, 0),
+                                ("f16_bicgstab", W.WD_F16, 0, 1), ("f32_bicgstab", W.WD_F32, 0, 1),
+                                ("f16_bicgstab_gauge_fixed", W.WD_F16, 1, 1)):
         p = W.wd_solve_params_default()
         p.inner_prec = inner
         p.gauge_fix = gf
+        p.solver = sv
         p.maxiter = 100000
         runs = []
         for r in range(reps + 1):
@@ -321,8 +324,9 @@ def solve_section(W, torch, reps=3):
             "host_buffers_wall_s": host_wall, "host_buffers_status": ih["status"],
             "all_wall_s": [d["wall_s"] for d in runs],
         }
-    for name in ("f16", "f32", "f16_gauge_fixed"):
-        out[name]["speedup_vs_f64"] = out["f64"]["wall_s"] / out[name]["wall_s"]
+    for name in out:
+        if name != "f64":
+            out[name]["speedup_vs_f64"] = out["f64"]["wall_s"] / out[name]["wall_s"]
     out["config"] = {"dims": list(dims), "kappa": SOLVE_KAPPA, "tol": 1e-10,
                      "rhs": "complex Gaussian (seed 2025)", "links": "eps=0.3, seed 1234",
                      "reliable_interval": 50, "timing": f"median of {reps} after 1 warm-up"}

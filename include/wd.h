@@ -258,6 +258,21 @@ int wd_axpby(double a, const void *x, double b, void *y, const int dims[4],
              int parity, int prec);
 
 /* ------------------------------------------------------------------ */
+/* tensor cores                                                        */
+/* ------------------------------------------------------------------ */
+
+/*
+ * D = A B on the 5th-generation tensor cores (tcgen05.mma, BF16 operands,
+ * FP32 accumulation in tensor memory): A [M][K] and B [K][N] row-major BF16,
+ * D [M][N] row-major FP32, all device memory.  M % 128 == 0, K % 16 == 0 with
+ * K <= 256, N % 16 == 0 with 16 <= N <= 256 (else WD_ERR_ARG).  The paper has
+ * no tensor cores; this is the contraction core of the learned preconditioner
+ * below, exposed so it can be checked on its own.  Synchronous: returns
+ * WD_ERR_TIMEOUT if a bounded device wait gave up.
+ */
+int wd_tc_gemm_bf16(float *D, const void *A, const void *B, int M, int K, int N);
+
+/* ------------------------------------------------------------------ */
 /* solver (paper: even-odd preconditioned CG; Fig. 2)                  */
 /* ------------------------------------------------------------------ */
 
@@ -272,7 +287,12 @@ typedef struct {
     int use_initial_guess;   /* x holds a starting guess (restart / resume) */
     double tol;              /* target ||b - D x|| / ||b|| (default 1e-10) */
     int gauge_fix;           /* solve in temporal gauge (wd_gauge_fix_temporal) */
+    int solver;              /* WD_SOLVER_CG (CG on the normal equations, default)
+                                or WD_SOLVER_BICGSTAB (BiCGstab on the Schur
+                                operator itself; the paper's second inverter) */
 } wd_solve_params;
+
+enum { WD_SOLVER_CG = 0, WD_SOLVER_BICGSTAB = 1 };
 
 typedef struct {
     int iters;               /* inner iterations */
@@ -316,7 +336,8 @@ int wd_solve_ex(double *x, const double *b, const double *gauge, double kappa,
  * convergence; each iteration step is one launch over all problems and
  * right-hand sides (links reused across right-hand sides), and
  * check_interval iterations are one captured CUDA graph.
- * Limits: 1 <= nproblems <= 16, 1 <= nrhs <= 32 per problem.
+ * Limits: 1 <= nproblems <= 16, 1 <= nrhs <= 32 per problem; params->solver
+ * must be WD_SOLVER_CG and params->gauge_fix 0 (else WD_ERR_ARG).
  * info (optional): one wd_solve_info per right-hand side, in problem order.
  * Returns WD_OK if every right-hand side converged, else the first failing
  * status (the per-right-hand-side statuses are in info).

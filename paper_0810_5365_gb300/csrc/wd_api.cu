@@ -88,8 +88,10 @@ void wd_finalize(void) {
   State& s = state();
   if (s.partials) cudaFree(s.partials);
   if (s.counter) cudaFree(s.counter);
+  if (s.dev_flag) cudaFree(s.dev_flag);
   s.partials = nullptr;
   s.counter = nullptr;
+  s.dev_flag = nullptr;
   s.partials_cap = 0;
 }
 
@@ -272,6 +274,21 @@ int wd_rotate_spinor(double* out, const double* in, const double* omega, const i
   return cuda_status(rotate_spinor(out, in, omega, make_geom(dims), dagger != 0, state().stream));
 }
 
+int wd_tc_gemm_bf16(float* D, const void* A, const void* B, int M, int K, int N) {
+  if (!D || !A || !B) return WD_ERR_NULL;
+  if (!aligned(D) || !aligned(A) || !aligned(B)) return WD_ERR_ALIGN;
+  if (M < 128 || M % 128 || K < 16 || K % 16 || K > 256 || N < 16 || N % 16 || N > 256)
+    return WD_ERR_ARG;
+  cudaStream_t st = state().stream;
+  int* flag = nullptr;
+  WD_TRY(cuda_status(device_flag(&flag, st)));
+  WD_TRY(cuda_status(tc_gemm_bf16(A, B, D, M, K, N, flag, st)));
+  int h = 0;
+  WD_TRY(cuda_status(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st)));
+  WD_TRY(cuda_status(cudaStreamSynchronize(st)));
+  return h ? WD_ERR_TIMEOUT : WD_OK;
+}
+
 int wd_norm2(double* result, const void* x, const int dims[4], int parity, int prec) {
   WD_TRY(check_dims(dims));
   WD_TRY(check_prec(prec));
@@ -315,6 +332,7 @@ void wd_solve_params_default(wd_solve_params* p) {
   p->use_initial_guess = 0;
   p->tol = 1e-10;
   p->gauge_fix = 0;
+  p->solver = WD_SOLVER_CG;
 }
 
 int wd_solve_ex(double* x, const double* b, const double* gauge, double kappa, const int dims[4],

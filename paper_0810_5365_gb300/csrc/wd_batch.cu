@@ -470,6 +470,7 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
   if (link_bytes(P.inner_prec, P.inner_recon) == 0 || link_bytes(WD_F64, P.outer_recon) == 0)
     return WD_ERR_PREC;
   if (!(P.tol > 0) || P.maxiter < 0 || P.reliable_interval < 1) return WD_ERR_ARG;
+  if (P.solver != WD_SOLVER_CG || P.gauge_fix) return WD_ERR_ARG;  // batched CG only
   const int chunk = P.check_interval < 2 ? 2 : (P.check_interval & ~1);
   cudaStream_t st = state().stream;
 

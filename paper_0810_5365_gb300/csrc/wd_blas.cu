@@ -58,6 +58,16 @@ cudaError_t ensure_scratch(size_t doubles) {
   return cudaSuccess;
 }
 
+cudaError_t device_flag(int** flag, cudaStream_t st) {
+  State& s = state();
+  if (!s.dev_flag) {
+    cudaError_t e = cudaMalloc(&s.dev_flag, 256);
+    if (e != cudaSuccess) return e;
+  }
+  *flag = s.dev_flag;
+  return cudaMemsetAsync(s.dev_flag, 0, sizeof(int), st);
+}
+
 RedScratch scratch() {
   RedScratch r;
   r.partials = state().partials;

@@ -295,12 +295,18 @@ __device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& 
 #define WD_F16_PREFETCH 2
 #endif
 
-template <int P, int RC, bool DAG, bool NORM, int BS>
-__global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_kernel(const DslashArgs a) {
+// TG: links in temporal gauge (compile-time, so that the ordinary kernel keeps
+// its register budget)
+template <int P, int RC, bool DAG, int RED, bool TG, int BS>
+__global__ void __launch_bounds__(BS, DslashMinBlocks<P, RED != RED_NONE>::value)
+    dslash_kernel(const DslashArgs a) {
+  constexpr int NRED = RED == RED_NONE ? 1 : RED == RED_NORM ? 1 : RED == RED_NORM_DOTX ? 3 : 2;
   using R = typename std::conditional<P == WD_F64, double, float>::type;
   const Geom& g = a.g;
   const int cb = blockIdx.x * BS + threadIdx.x;
-  double nrm = 0.0;
+  double red[NRED];
+#pragma unroll
+  for (int j = 0; j < NRED; j++) red[j] = 0.0;
   if (cb < g.Vh) {
     const int p = a.parity;
     int x0, x1, x2, x3;
@@ -319,8 +325,8 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_ke
     const bool bflip = x3 == 0;
     // temporal gauge: U_t(x) = 1 unless x3 = L3-1; the backward link
     // U_t(x - t) is at x3 - 1, the identity unless x3 = 0
-    const bool funit = a.tg && !fflip;
-    const bool bunit = a.tg && !bflip;
+    const bool funit = TG && !fflip;
+    const bool bunit = TG && !bflip;
 
     // forward hops use (1 - s gamma), backward (1 + s gamma)
     constexpr int SF = DAG ? -1 : 1;
@@ -406,22 +412,66 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, NORM>::value) dslash_ke
       }
     }
     store_spinor<P, R>(a.out, cb, VP, acc);
-    if constexpr (NORM) {
+    if constexpr (RED != RED_NONE) {
       if constexpr (P == WD_F16) {
-        // the norm of what was stored (after rounding to half)
+        // reduce what was stored (after rounding to half)
+        load_spinor_rw<P, R>(acc, a.out, cb, VP);
+      }
+      if constexpr (RED == RED_NORM || RED == RED_NORM_DOTX) red[0] = site_norm2(acc);
+      if constexpr (RED == RED_NORM_DOTX) {
         cx<R> v[12];
-        load_spinor_rw<P, R>(v, a.out, cb, VP);
-        nrm = site_norm2(v);
-      } else {
-        nrm = site_norm2(acc);
+        load_spinor_rw<P, R>(v, a.x, cb, VP);
+        site_cdot(acc, v, red[1], red[2]);
+      }
+      if constexpr (RED == RED_DOTZ) {
+        cx<R> v[12];
+        load_spinor_rw<P, R>(v, a.z, cb, VP);
+        site_cdot(v, acc, red[0], red[1]);
       }
     }
   }
-  if constexpr (NORM) {
-    double v[1] = {nrm};
-    double tot[1];
-    if (grid_reduce<1, BS>(v, a.rs, tot) && threadIdx.x == 0) *a.norm_out = tot[0];
+  if constexpr (RED != RED_NONE) {
+    double tot[NRED];
+    if (grid_reduce<NRED, BS>(red, a.rs, tot) && threadIdx.x == 0) {
+#pragma unroll
+      for (int j = 0; j < NRED; j++) a.norm_out[j] = tot[j];
+    }
   }
+}
+
+template <int P, int RC, bool DG, bool TG>
+cudaError_t launch_dslash_red_tg(const DslashArgs& a, dim3 grid, dim3 block, cudaStream_t st) {
+  const int mode = a.norm_out ? a.red_mode : RED_NONE;
+  switch (mode) {
+    case RED_NONE:
+      dslash_kernel<P, RC, DG, RED_NONE, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
+      break;
+    case RED_NORM:
+      dslash_kernel<P, RC, DG, RED_NORM, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
+      break;
+    case RED_NORM_DOTX:
+    case RED_DOTZ:
+      // the dot-product epilogues serve BiCGstab, which never applies H^+
+      if constexpr (!DG) {
+        if (mode == RED_NORM_DOTX) {
+          if (!a.x) return cudaErrorInvalidValue;
+          dslash_kernel<P, RC, DG, RED_NORM_DOTX, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
+        } else {
+          if (!a.z) return cudaErrorInvalidValue;
+          dslash_kernel<P, RC, DG, RED_DOTZ, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
+        }
+        break;
+      }
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int P, int RC, bool DG>
+cudaError_t launch_dslash_red(const DslashArgs& a, dim3 grid, dim3 block, cudaStream_t st) {
+  return a.tg ? launch_dslash_red_tg<P, RC, DG, true>(a, grid, block, st)
+              : launch_dslash_red_tg<P, RC, DG, false>(a, grid, block, st);
 }
 
 // Launch one instance; the .cu file of each precision instantiates it.
@@ -429,23 +479,15 @@ template <int P>
 cudaError_t launch_dslash_prec(const DslashArgs& a, int recon, bool dagger, cudaStream_t st) {
   const int BS = DSLASH_BS;
   dim3 grid((a.g.Vh + BS - 1) / BS), block(BS);
-  const bool norm = a.norm_out != nullptr;
-#define WD_LAUNCH(RC, DG, NM) dslash_kernel<P, RC, DG, NM, DSLASH_BS><<<grid, block, 0, st>>>(a)
-  if constexpr (P == WD_F16) {
-    if (recon != 12) return cudaErrorInvalidValue;
-    if (dagger) { if (norm) WD_LAUNCH(12, true, true); else WD_LAUNCH(12, true, false); }
-    else        { if (norm) WD_LAUNCH(12, false, true); else WD_LAUNCH(12, false, false); }
-  } else {
-    if (recon == 12) {
-      if (dagger) { if (norm) WD_LAUNCH(12, true, true); else WD_LAUNCH(12, true, false); }
-      else        { if (norm) WD_LAUNCH(12, false, true); else WD_LAUNCH(12, false, false); }
-    } else {
-      if (dagger) { if (norm) WD_LAUNCH(18, true, true); else WD_LAUNCH(18, true, false); }
-      else        { if (norm) WD_LAUNCH(18, false, true); else WD_LAUNCH(18, false, false); }
-    }
+  if (recon == 12)
+    return dagger ? launch_dslash_red<P, 12, true>(a, grid, block, st)
+                  : launch_dslash_red<P, 12, false>(a, grid, block, st);
+  if constexpr (P != WD_F16) {
+    if (recon == 18)
+      return dagger ? launch_dslash_red<P, 18, true>(a, grid, block, st)
+                    : launch_dslash_red<P, 18, false>(a, grid, block, st);
   }
-#undef WD_LAUNCH
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace wd

@@ -32,6 +32,7 @@ constexpr int DSLASH_BS = WD_DSLASH_BS;
 // (the fused-norm FP32 variant needs 80 registers to stay free of spills)
 template <int P, bool NORM>
 struct DslashMinBlocks {
+  // (one fewer block for FP32 kernels that reduce, see the sweep above)
   static constexpr int value =
       P == WD_F64   ? WD_DSLASH_MINB_F64
       : P == WD_F32 ? (NORM ? WD_DSLASH_MINB_F32_NORM : WD_DSLASH_MINB_F32)
@@ -50,7 +51,15 @@ struct DslashArgs {
   Geom g;
   int parity;        // parity of the output sites
   int tg = 0;        // links in temporal gauge: U_t = 1 off the last time slice
+  // reduction fused into the epilogue when norm_out != nullptr:
+  //   RED_NORM       norm_out[0]    = ||out||^2
+  //   RED_NORM_DOTX  norm_out[0..2] = ||out||^2, <out, x> (re, im)
+  //   RED_DOTZ       norm_out[0..1] = <z, out>   (re, im),  <a, b> = sum conj(a) b
+  int red_mode = 1;
+  const void* z = nullptr;
 };
+
+enum { RED_NONE = 0, RED_NORM = 1, RED_NORM_DOTX = 2, RED_DOTZ = 3 };
 
 // bit OR-ed into a `recon` argument: the gauge field is in temporal gauge
 // (time links are the identity except on the slice t = L3-1), so the hopping
@@ -84,6 +93,7 @@ struct State {
   unsigned* counter = nullptr;
   size_t partials_cap = 0;  // doubles
   int num_sms = 0;
+  int* dev_flag = nullptr;  // device int: set by kernels whose bounded waits gave up
 };
 
 State& state();
@@ -114,6 +124,13 @@ cudaError_t cdot(double* res, const void* x, const void* y, const Geom& g, int p
                  cudaStream_t st);
 cudaError_t axpby(double a, const void* x, double b, void* y, const Geom& g, int prec, int nh,
                   cudaStream_t st);
+
+// zeroed device flag for bounded device-side waits (allocated on first use)
+cudaError_t device_flag(int** flag, cudaStream_t st);
+
+// tensor-core GEMM (wd_tcgemm.cu)
+cudaError_t tc_gemm_bf16(const void* A, const void* B, float* D, int M, int K, int N, int* err,
+                         cudaStream_t st);
 
 // temporal gauge (wd_gauge.cu): canonical FP64 fields on the device
 cudaError_t gauge_fix_temporal(double* Uout, double* omega, const double* Uin, const Geom& g,

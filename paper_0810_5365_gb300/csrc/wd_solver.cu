@@ -34,7 +34,18 @@ struct CgScalars {
   double r64;       // ||bhat - Mhat x64||^2 (FP64)
   double bnorm2;    // ||b||^2 of the full right-hand side
   double res_e, res_o;  // ||b - D x||^2 on even / odd sites
+  // BiCGstab (complex scalars as (re, im), ping-pong between iterations)
+  double rho[2][2];  // <r0, r>
+  double rv[2][2];   // <r0, v>
+  double tts[2][3];  // ||t||^2, <t, s>
 };
+
+__host__ __device__ __forceinline__ void zdiv(double ar, double ai, double br, double bi,
+                                              double& cr, double& ci) {
+  const double d = br * br + bi * bi;
+  cr = (ar * br + ai * bi) / d;
+  ci = (ai * br - ar * bi) / d;
+}
 
 // r -= alpha q ; rr = ||r||^2 ; alpha = gamma[kp] / qq
 template <int P, int BS>
@@ -107,6 +118,126 @@ __global__ void __launch_bounds__(BS) ru_accumulate(char* x64, char* xs, Geom g)
 }
 
 // ---------------------------------------------------------------------------
+// BiCGstab updates (van der Vorst, SIAM J. Sci. Stat. Comput. 13, 1992) on
+// the Schur operator; the paper reports a BiCGstab inverter beside its CG
+// (section "Performance").  Scalars are recomputed by every thread from the
+// reductions in CgScalars; kp selects the current slot.
+// ---------------------------------------------------------------------------
+
+// p = r + beta (p - omega_old v),  beta = (rho_new / rho_old) (alpha_old / omega_old)
+template <int P, int BS>
+__global__ void __launch_bounds__(BS) bicg_update_p(char* p, const char* __restrict__ r,
+                                                    const char* __restrict__ v,
+                                                    const CgScalars* sc, int kp, Geom g) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  const int kq = 1 - kp;
+  double ar, ai, wr, wi, t1r, t1i, t2r, t2i, br, bi;
+  zdiv(sc->rho[kq][0], sc->rho[kq][1], sc->rv[kq][0], sc->rv[kq][1], ar, ai);   // alpha_old
+  zdiv(sc->tts[kq][1], sc->tts[kq][2], sc->tts[kq][0], 0.0, wr, wi);          // omega_old
+  zdiv(sc->rho[kp][0], sc->rho[kp][1], sc->rho[kq][0], sc->rho[kq][1], t1r, t1i);
+  zdiv(ar, ai, wr, wi, t2r, t2i);
+  br = t1r * t2r - t1i * t2i;
+  bi = t1r * t2i + t1i * t2r;
+  const R Br = (R)br, Bi = (R)bi, Wr = (R)wr, Wi = (R)wi;
+  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+    cx<R> pv[12], rv_[12], vv[12];
+    load_spinor_rw<P, R>(pv, p, cb, g.Vh_pad);
+    load_spinor_rw<P, R>(rv_, r, cb, g.Vh_pad);
+    load_spinor_rw<P, R>(vv, v, cb, g.Vh_pad);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      // u = p - omega v
+      const R ur = pv[k].r - (Wr * vv[k].r - Wi * vv[k].i);
+      const R ui = pv[k].i - (Wr * vv[k].i + Wi * vv[k].r);
+      pv[k].r = rv_[k].r + (Br * ur - Bi * ui);
+      pv[k].i = rv_[k].i + (Br * ui + Bi * ur);
+    }
+    store_spinor<P, R>(p, cb, g.Vh_pad, pv);
+  }
+}
+
+// s = r - alpha v,  alpha = rho / <r0, v>
+template <int P, int BS>
+__global__ void __launch_bounds__(BS) bicg_update_s(char* s, const char* __restrict__ r,
+                                                    const char* __restrict__ v,
+                                                    const CgScalars* sc, int kp, Geom g) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  double ar, ai;
+  zdiv(sc->rho[kp][0], sc->rho[kp][1], sc->rv[kp][0], sc->rv[kp][1], ar, ai);
+  const R Ar = (R)ar, Ai = (R)ai;
+  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+    cx<R> rv_[12], vv[12];
+    load_spinor_rw<P, R>(rv_, r, cb, g.Vh_pad);
+    load_spinor_rw<P, R>(vv, v, cb, g.Vh_pad);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      rv_[k].r -= Ar * vv[k].r - Ai * vv[k].i;
+      rv_[k].i -= Ar * vv[k].i + Ai * vv[k].r;
+    }
+    store_spinor<P, R>(s, cb, g.Vh_pad, rv_);
+  }
+}
+
+// x += alpha p + omega s ; r = s - omega t ; rho_next = <r0, r> ; rr = ||r||^2
+template <int P, int PX, int BS>
+__global__ void __launch_bounds__(BS) bicg_update_xr(char* x, char* r, const char* __restrict__ p,
+                                                     const char* __restrict__ s,
+                                                     const char* __restrict__ t,
+                                                     const char* __restrict__ r0, CgScalars* sc,
+                                                     int kp, Geom g, RedScratch rs) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  using RX = typename std::conditional<PX == WD_F64, double, float>::type;
+  double ar, ai, wr, wi;
+  zdiv(sc->rho[kp][0], sc->rho[kp][1], sc->rv[kp][0], sc->rv[kp][1], ar, ai);
+  zdiv(sc->tts[kp][1], sc->tts[kp][2], sc->tts[kp][0], 0.0, wr, wi);
+  const RX Ar = (RX)ar, Ai = (RX)ai, Wxr = (RX)wr, Wxi = (RX)wi;
+  const R Wr = (R)wr, Wi = (R)wi;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+    cx<R> pv[12], sv[12], tv[12], zv[12];
+    cx<RX> xv[12];
+    load_spinor_rw<P, R>(pv, p, cb, g.Vh_pad);
+    load_spinor_rw<P, R>(sv, s, cb, g.Vh_pad);
+    load_spinor_rw<P, R>(tv, t, cb, g.Vh_pad);
+    load_spinor_rw<PX, RX>(xv, x, cb, g.Vh_pad);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const RX pr = (RX)pv[k].r, pi = (RX)pv[k].i, sr = (RX)sv[k].r, si = (RX)sv[k].i;
+      xv[k].r += Ar * pr - Ai * pi + Wxr * sr - Wxi * si;
+      xv[k].i += Ar * pi + Ai * pr + Wxr * si + Wxi * sr;
+      sv[k].r -= Wr * tv[k].r - Wi * tv[k].i;
+      sv[k].i -= Wr * tv[k].i + Wi * tv[k].r;
+    }
+    store_spinor<PX, RX>(x, cb, g.Vh_pad, xv);
+    store_spinor<P, R>(r, cb, g.Vh_pad, sv);
+    if constexpr (P == WD_F16) load_spinor_rw<P, R>(sv, r, cb, g.Vh_pad);  // what was stored
+    load_spinor_rw<P, R>(zv, r0, cb, g.Vh_pad);
+    site_cdot(zv, sv, acc[0], acc[1]);
+    acc[2] += site_norm2(sv);
+  }
+  double tot[3];
+  if (grid_reduce<3, BS>(acc, rs, tot) && threadIdx.x == 0) {
+    sc->rho[1 - kp][0] = tot[0];
+    sc->rho[1 - kp][1] = tot[1];
+    sc->rr = tot[2];
+  }
+}
+
+// restart: rho[0] = ||r||^2 (r0 = r), and the "previous" slot set so that the
+// first p-update gives p = r (p = v = 0 beforehand)
+__global__ void bicg_restart_scalars(CgScalars* sc) {
+  sc->rho[0][0] = sc->rr;
+  sc->rho[0][1] = 0.0;
+  sc->rho[1][0] = 1.0;
+  sc->rho[1][1] = 0.0;
+  sc->rv[1][0] = 1.0;
+  sc->rv[1][1] = 0.0;
+  sc->tts[1][0] = 1.0;
+  sc->tts[1][1] = 1.0;
+  sc->tts[1][2] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
 // workspace
 // ---------------------------------------------------------------------------
 
@@ -127,6 +258,8 @@ struct Workspace {
   void* r = nullptr;
   void* s = nullptr;
   void* ts = nullptr;    // sloppy odd temporary
+  void* t = nullptr;     // sloppy even (BiCGstab: t = A s)
+  void* r0 = nullptr;    // sloppy even (BiCGstab shadow residual)
   void* xs = nullptr;    // sloppy solution accumulator (FP32 for FP16 inner)
   double* canon_spinor = nullptr;  // staging for host spinors
   double* canon_gauge = nullptr;   // staging for a host gauge field
@@ -146,7 +279,7 @@ static Workspace& ws() {
 static void ws_free() {
   Workspace& w = ws();
   void* bufs[] = {w.g64, w.b64, w.x64, w.rf64, w.bhat, w.r64, w.t64, w.p, w.q, w.r,
-                  w.s, w.ts, w.xs, w.canon_spinor, w.canon_gauge, w.sc,
+                  w.s, w.ts, w.t, w.r0, w.xs, w.canon_spinor, w.canon_gauge, w.sc,
                   w.gf_gauge, w.gf_omega, w.gf_spinor};
   if (w.gs && w.gs != w.g64) cudaFree(w.gs);
   for (void* b : bufs)
@@ -200,6 +333,8 @@ static int ws_ensure(const int dims[4], int sprec, int srecon, int orecon) {
   WD_CK(cudaMalloc(&w.r, hs));
   WD_CK(cudaMalloc(&w.s, hs));
   WD_CK(cudaMalloc(&w.ts, hs));
+  WD_CK(cudaMalloc(&w.t, hs));
+  WD_CK(cudaMalloc(&w.r0, hs));
   WD_CK(cudaMalloc(&w.xs, hx));
   WD_CK(cudaMalloc(&w.sc, sizeof(CgScalars)));
   WD_CK(cudaMemset(w.sc, 0, sizeof(CgScalars)));
@@ -231,12 +366,14 @@ struct Ctx {
   double kappa;
   int sprec, srecon, orecon, xprec;
   int tg = 0;
+  int bicg = 0;
   double dslash_calls = 0;
 };
 
 cudaError_t dsl(Ctx& c, int prec, int recon, const void* gauge, void* out, const void* in,
                 int parity, int dagger, double a, const void* x, double bx, const void* y,
-                double cy, double* norm, cudaStream_t st) {
+                double cy, double* norm, cudaStream_t st, int red_mode = RED_NORM,
+                const void* z = nullptr) {
   DslashArgs d;
   d.out = out;
   d.in = in;
@@ -251,6 +388,8 @@ cudaError_t dsl(Ctx& c, int prec, int recon, const void* gauge, void* out, const
   d.g = c.w->g;
   d.parity = parity;
   d.tg = c.tg;
+  d.red_mode = red_mode;
+  d.z = z;
   c.dslash_calls += 1;
   return launch_dslash(prec, d, recon, dagger != 0, st);
 }
@@ -282,7 +421,49 @@ cudaError_t iteration_t(Ctx& c, int kp, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// one BiCGstab iteration on A = Mhat (sloppy)
+template <int P, int PX>
+cudaError_t iteration_bicg_t(Ctx& c, int kp, cudaStream_t st) {
+  Workspace& w = *c.w;
+  const Geom& g = w.g;
+  const double k2 = c.kappa * c.kappa;
+  const int grid = blas_grid(g.Vh, 256);
+  cudaError_t e;
+  bicg_update_p<P, 256><<<grid, 256, 0, st>>>((char*)w.p, (const char*)w.r, (const char*)w.q,
+                                               w.sc, kp, g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // v = A p with <r0, v>
+  if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.ts, w.p, WD_ODD, 0, 1.0, nullptr, 0, nullptr, 0,
+               nullptr, st)))
+    return e;
+  if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.q, w.ts, WD_EVEN, 0, -k2, w.p, 1.0, nullptr, 0,
+               &w.sc->rv[kp][0], st, RED_DOTZ, w.r0)))
+    return e;
+  bicg_update_s<P, 256><<<grid, 256, 0, st>>>((char*)w.s, (const char*)w.r, (const char*)w.q,
+                                               w.sc, kp, g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // t = A s with ||t||^2, <t, s>
+  if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.ts, w.s, WD_ODD, 0, 1.0, nullptr, 0, nullptr, 0,
+               nullptr, st)))
+    return e;
+  if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.t, w.ts, WD_EVEN, 0, -k2, w.s, 1.0, nullptr, 0,
+               &w.sc->tts[kp][0], st, RED_NORM_DOTX)))
+    return e;
+  bicg_update_xr<P, PX, 256><<<grid, 256, 0, st>>>((char*)w.xs, (char*)w.r, (const char*)w.p,
+                                                   (const char*)w.s, (const char*)w.t,
+                                                   (const char*)w.r0, w.sc, kp, g, scratch());
+  return cudaGetLastError();
+}
+
 cudaError_t iteration(Ctx& c, int kp, cudaStream_t st) {
+  if (c.bicg) {
+    switch (c.sprec) {
+      case WD_F64: return iteration_bicg_t<WD_F64, WD_F64>(c, kp, st);
+      case WD_F32: return iteration_bicg_t<WD_F32, WD_F32>(c, kp, st);
+      case WD_F16: return iteration_bicg_t<WD_F16, WD_F32>(c, kp, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (c.sprec) {
     case WD_F64: return iteration_t<WD_F64, WD_F64>(c, kp, st);
     case WD_F32: return iteration_t<WD_F32, WD_F32>(c, kp, st);
@@ -313,6 +494,16 @@ cudaError_t reliable_update(Ctx& c, bool accumulate, cudaStream_t st) {
           w.bhat, 1.0, &w.sc->r64, st);
   if (e != cudaSuccess) return e;
   if ((e = convert_spinor(w.r, c.sprec, w.r64, WD_F64, g, 1, st)) != cudaSuccess) return e;
+  if (c.bicg) {
+    // restart BiCGstab: r0 = r, p = v = 0, rho = ||r||^2
+    const size_t hs = spinor_half_bytes(g, c.sprec);
+    if ((e = convert_spinor(w.r0, c.sprec, w.r, c.sprec, g, 1, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.p, 0, hs, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.q, 0, hs, st)) != cudaSuccess) return e;
+    if ((e = norm2(&w.sc->rr, w.r, g, c.sprec, 1, st)) != cudaSuccess) return e;
+    bicg_restart_scalars<<<1, 1, 0, st>>>(w.sc);
+    return cudaGetLastError();
+  }
   e = mhat_sloppy(c, w.s, w.r, 1, &w.sc->gamma[0], st);
   if (e != cudaSuccess) return e;
   return convert_spinor(w.p, c.sprec, w.s, c.sprec, g, 1, st);
@@ -353,6 +544,7 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
   c.srecon = P.inner_recon;
   c.orecon = P.outer_recon;
   c.xprec = sloppy_x_prec(P.inner_prec);
+  c.bicg = P.solver == WD_SOLVER_BICGSTAB;
   cudaStream_t st = c.st;
   const size_t V = 2 * (size_t)g.Vh;
   const size_t h64 = spinor_half_bytes(g, WD_F64);
@@ -455,13 +647,15 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
   double t_ru = 0.0;
   double r64 = std::sqrt(w.sc_host->r64);
   bool converged = !(bnorm > 0) || r64 <= target;
+  int bicg_restarts = 0;
   while (!converged) {
-    if (!std::isfinite(w.sc_host->r64) || !std::isfinite(w.sc_host->gamma[0])) {
+    const double g0 = c.bicg ? w.sc_host->rr : w.sc_host->gamma[0];
+    if (!std::isfinite(w.sc_host->r64) || !std::isfinite(g0)) {
       status = WD_ERR_NONFINITE;
       break;
     }
     if (iters >= P.maxiter) break;
-    if (!(w.sc_host->gamma[0] > 0)) {
+    if (!(g0 > 0)) {
       status = WD_ERR_BREAKDOWN;
       break;
     }
@@ -478,13 +672,34 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
     iters += chunk;
     if (read_scalars(c) != cudaSuccess) { status = WD_ERR_CUDA; break; }
     const double rr = w.sc_host->rr;
-    if (!std::isfinite(rr) || !std::isfinite(w.sc_host->gamma[0])) {
-      status = WD_ERR_NONFINITE;
-      break;
-    }
-    if (!(w.sc_host->qq > 0)) {
-      status = WD_ERR_BREAKDOWN;
-      break;
+    if (c.bicg) {
+      // a BiCGstab breakdown (<r0, v> or ||t|| vanishing) shows up as a
+      // non-finite scalar: drop the sloppy progress since the last reliable
+      // update and restart from x64; give up after three restarts in a row
+      const bool bad = !std::isfinite(rr) || !std::isfinite(w.sc_host->rho[0][0]) ||
+                       !std::isfinite(w.sc_host->rho[1][0]);
+      if (bad) {
+        if (++bicg_restarts > 3) {
+          status = WD_ERR_BREAKDOWN;
+          break;
+        }
+        cudaError_t e = cudaMemsetAsync(w.xs, 0, spinor_half_bytes(g, c.xprec), st);
+        if (e == cudaSuccess) e = reliable_update(c, false, st);
+        if (e == cudaSuccess) e = read_scalars(c);
+        if (e != cudaSuccess) { state().last_cuda_error = (int)e; status = WD_ERR_CUDA; break; }
+        last_ru = iters;
+        continue;
+      }
+      bicg_restarts = 0;
+    } else {
+      if (!std::isfinite(rr) || !std::isfinite(w.sc_host->gamma[0])) {
+        status = WD_ERR_NONFINITE;
+        break;
+      }
+      if (!(w.sc_host->qq > 0)) {
+        status = WD_ERR_BREAKDOWN;
+        break;
+      }
     }
     const bool looks_done = std::sqrt(rr) <= target;
     if (looks_done || iters - last_ru >= reliable_interval || iters >= P.maxiter) {

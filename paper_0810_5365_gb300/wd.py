@@ -15,6 +15,7 @@ from .build import LIB
 
 WD_F64, WD_F32, WD_F16 = 0, 1, 2
 WD_TEMPORAL_GAUGE = 0x100
+WD_SOLVER_CG, WD_SOLVER_BICGSTAB = 0, 1
 WD_EVEN, WD_ODD, WD_FULL = 0, 1, -1
 
 WD_OK = 0
@@ -38,7 +39,7 @@ EXPORTS = [
     "wd_convert_spinor", "wd_dslash", "wd_dslash_dag", "wd_dslash_ex", "wd_mhat", "wd_norm2",
     "wd_cdot", "wd_axpby", "wd_solve_params_default", "wd_solve", "wd_solve_ex",
     "wd_dslash_ex_noalloc", "wd_dslash_mrhs", "wd_solve_batch", "wd_gauge_fix_temporal",
-    "wd_rotate_spinor",
+    "wd_rotate_spinor", "wd_tc_gemm_bf16",
 ]
 
 
@@ -55,7 +56,7 @@ class wd_solve_params(C.Structure):
     _fields_ = [("inner_prec", C.c_int), ("inner_recon", C.c_int), ("outer_recon", C.c_int),
                 ("reliable_interval", C.c_int), ("check_interval", C.c_int),
                 ("maxiter", C.c_int), ("use_graph", C.c_int), ("use_initial_guess", C.c_int),
-                ("tol", C.c_double), ("gauge_fix", C.c_int)]
+                ("tol", C.c_double), ("gauge_fix", C.c_int), ("solver", C.c_int)]
 
 
 class wd_batch_problem(C.Structure):
@@ -109,6 +110,7 @@ def lib():
                                            C.c_int]),
         "wd_mhat": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_int, i4, C.c_int, C.c_int]),
         "wd_gauge_fix_temporal": (C.c_int, [dp, dp, dp, i4]),
+        "wd_tc_gemm_bf16": (C.c_int, [dp, vp, vp, C.c_int, C.c_int, C.c_int]),
         "wd_rotate_spinor": (C.c_int, [dp, dp, dp, i4, C.c_int]),
         "wd_dslash_mrhs": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
                                      C.c_int, dp, i4, C.c_int, C.c_int]),
@@ -261,6 +263,10 @@ def wd_solve_batch(problems, params=None, check=True):
     if check:
         _ck(rc, "wd_solve_batch")
     return rc, out
+
+
+def wd_tc_gemm_bf16(D, A, B, M, K, N):
+    _ck(lib().wd_tc_gemm_bf16(_p(D), _p(A), _p(B), int(M), int(K), int(N)), "wd_tc_gemm_bf16")
 
 
 def wd_gauge_fix_temporal(U_out, omega_out, U_in, dims):

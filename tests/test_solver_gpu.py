@@ -117,3 +117,39 @@ def test_bad_solver_params():
     assert info["status"] == W.WD_ERR_PREC
     info = W.wd_solve_ex(np.zeros_like(b), b, U, 0.12, dims, params(tol=-1.0), check=False)
     assert info["status"] == W.WD_ERR_ARG
+
+
+@pytest.mark.parametrize("dims,kappa", [((4, 4, 4, 4), 0.12), ((4, 4, 4, 8), 0.137),
+                                        ((6, 6, 6, 6), 0.135), ((8, 8, 8, 8), 0.137)])
+@pytest.mark.parametrize("inner", [W.WD_F64, W.WD_F32, W.WD_F16])
+def test_bicgstab_reaches_tolerance(dims, kappa, inner):
+    """BiCGstab on the Schur operator (the paper's second inverter), with the
+    same FP64 reliable updates; judged by the oracle's true residual."""
+    U = fields.su3_links(dims, workers=1)
+    b = fields.gaussian_spinor(dims, seed=2024)
+    x = np.zeros_like(b)
+    info = W.wd_solve_ex(x, b, U, kappa, dims, params(inner_prec=inner,
+                                                      solver=W.WD_SOLVER_BICGSTAB))
+    assert info["status"] == W.WD_OK
+    assert true_residual(x, b, U, dims, kappa) <= 1.05e-10
+
+
+def test_bicgstab_in_temporal_gauge_and_plain_launches():
+    dims, kappa = (4, 6, 8, 10), 0.13
+    U = fields.su3_links(dims, workers=1)
+    b = fields.gaussian_spinor(dims, seed=31)
+    for gf, graph in ((1, 1), (0, 0)):
+        x = np.zeros_like(b)
+        W.wd_solve_ex(x, b, U, kappa, dims, params(solver=W.WD_SOLVER_BICGSTAB, gauge_fix=gf,
+                                                   use_graph=graph))
+        assert true_residual(x, b, U, dims, kappa) <= 1.05e-10
+
+
+def test_batch_rejects_bicgstab():
+    dims = (4, 4, 4, 4)
+    U = fields.su3_links(dims, workers=1)
+    b = fields.gaussian_spinor(dims)[None]
+    rc, _ = W.wd_solve_batch([{"dims": dims, "kappa": 0.12, "nrhs": 1, "gauge": U, "b": b,
+                               "x": np.zeros_like(b)}], params(solver=W.WD_SOLVER_BICGSTAB),
+                             check=False)
+    assert rc == W.WD_ERR_ARG
