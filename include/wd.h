@@ -354,6 +354,90 @@ typedef struct {
 int wd_solve_batch(const wd_batch_problem *problems, int nproblems,
                    const wd_solve_params *params, wd_solve_info *info);
 
+/* ------------------------------------------------------------------ */
+/* learned preconditioner (not in the paper)                           */
+/* ------------------------------------------------------------------ */
+
+/*
+ * A three-layer gauge-covariant nearest-neighbour network N, linear in its
+ * input: layer l maps C_l -> C_{l+1} spin-like channels per colour
+ * (4 -> 8 -> 8 -> 4, i.e. 12 -> 24 -> 24 -> 12 complex channels per site) as
+ *     y(x)[o][a] = sum_{d=0..8} sum_i W_d[o][i] (T_d phi)(x)[i][a],
+ * T_0 = identity, T_{1+2mu} phi(x) = U_mu(x) phi(x+mu),
+ * T_{2+2mu} phi(x) = U_mu(x-mu)^+ phi(x-mu) (antiperiodic time sign as in D).
+ * Weights: WD_NN_PARAMS floats, layers back to back, each [9][C_out][C_in]
+ * complex (re, im), device memory.  The contraction runs on the tensor cores
+ * (BF16 operands, FP32 accumulation); activations are FP32.
+ */
+enum { WD_NN_PARAMS = 2304 };
+
+typedef struct {
+    int samples;             /* training pairs (b = D x, x), x complex Gaussian (4096) */
+    int batch;               /* pairs per Adam step (16) */
+    int epochs;              /* passes over the samples (1) */
+    float lr;                /* Adam learning rate (2e-3) */
+    unsigned long long seed; /* seed of the on-device sample generator (4242) */
+    int init;                /* 1: start from the hopping series (wd_nn_init) */
+} wd_nn_train_params;
+
+typedef struct {
+    int steps;
+    double loss_first;       /* ||N(b) - x||^2 / ||x||^2 of the first step's last pair */
+    double loss_last;        /* same for the last step */
+    double seconds;
+} wd_nn_train_info;
+
+void wd_nn_train_params_default(wd_nn_train_params *p);
+
+/* weights <- the truncated hopping series of D^-1:
+ * N = (1 + kH)(1 + i kH)(1 - i kH) = 1 + kH + k^2 H^2 + k^3 H^3. */
+int wd_nn_init(float *weights, double kappa);
+
+/* One layer: out (cout channels) = sum_d W_d T_d in (cin channels),
+ * cin, cout in {4, 8}; weights [9][cout][cin] complex (device).  Fields use
+ * the packed FP32 full layout widened to C channels: per parity, blocks of
+ * 32 sites holding 3C/2 16-byte groups per site (complex index c*3 + colour),
+ * each half rounded up to 256 bytes; C = 4 is the packed FP32 spinor.
+ * Synchronous. */
+int wd_nn_layer(void *out, const void *in, const float *weights, int cin, int cout,
+                const void *gauge, const int dims[4]);
+
+/* Weight gradient of one layer (backpropagation):
+ *     grad_d[o][i] = sum_{x, colour a} delta(x)[o][a] conj((T_d in)(x)[i][a])
+ * in: cin channels, delta: cout channels (packed FP32 full layout as above);
+ * grad: [9][cout][cin] complex FP32 (device).  Synchronous. */
+int wd_nn_wgrad(float *grad, const void *in, const void *delta, int cin, int cout,
+                const void *gauge, const int dims[4]);
+
+/* Complex Gaussian spinor field written in the packed FP32 full layout:
+ * component k of lexicographic site i is the complex normal number
+ * first + 12 i + k of stream (seed, stream) of the counter-based SplitMix64 /
+ * Box-Muller generator (Re, Im ~ N(0, 1/2)).  The training samples of
+ * wd_nn_train are drawn this way. */
+int wd_gaussian_spinor(void *out, unsigned long long seed, unsigned long long stream,
+                       unsigned long long first, const int dims[4]);
+
+/* out = N(in): packed FP32 full spinors (WD_FULL layout); gauge packed
+ * WD_F32 with recon 12.  Synchronous. */
+int wd_nn_apply(void *out, const void *in, const float *weights, const void *gauge,
+                const int dims[4]);
+
+/* Train N on pairs (D x, x) generated on the GPU (Adam, loss ||N(Dx) - x||^2).
+ * gauge: canonical FP64 (host or device).  weights: device, in/out. */
+int wd_nn_train(float *weights, const double *gauge, double kappa, const int dims[4],
+                const wd_nn_train_params *params, wd_nn_train_info *info);
+
+/*
+ * Flexible GCR(m) on the full operator D x = b (restart length m <= 16),
+ * right-preconditioned by N (weights may be NULL: plain GCR), FP32 inner
+ * vectors with FP64 restarts: x accumulated and r = b - D x recomputed in FP64
+ * at every restart; stops on ||b - D x|| / ||b|| <= params->tol.  x, b, gauge
+ * canonical FP64, host or device.  info->reliable_updates counts restarts.
+ */
+int wd_solve_fgcr(double *x, const double *b, const double *gauge, double kappa,
+                  const int dims[4], const float *weights, int m,
+                  const wd_solve_params *params, wd_solve_info *info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,19 @@
 #include "wd_internal.h"
 
 namespace wd {
+int nn_apply_impl(void* out, const void* in, const float* w, const void* gauge, const int dims[4]);
+int nn_init_impl(float* w_dev, double kappa);
+int nn_layer_impl(void* out, const void* in, const float* w, int cin, int cout, const void* gauge,
+                  const int dims[4]);
+int gaussian_spinor_impl(void* out, unsigned long long seed, unsigned long long stream,
+                         unsigned long long first, const int dims[4]);
+int nn_wgrad_impl(float* grad, const void* in, const void* delta, int cin, int cout,
+                  const void* gauge, const int dims[4]);
+int nn_train_impl(float* w, const double* gauge, double kappa, const int dims[4],
+                  const wd_nn_train_params* prm, wd_nn_train_info* info);
+int fgcr_impl(double* x, const double* bsrc, const double* gauge, double kappa,
+              const int dims[4], const float* wts, const wd_solve_params* prm,
+              wd_solve_info* info, int m);
 int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_params* prm,
                      wd_solve_info* infos);
 cudaError_t dslash_mrhs(void* out, const void* in, const void* gauge, int parity, int dagger,
@@ -287,6 +300,82 @@ int wd_tc_gemm_bf16(float* D, const void* A, const void* B, int M, int K, int N)
   WD_TRY(cuda_status(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st)));
   WD_TRY(cuda_status(cudaStreamSynchronize(st)));
   return h ? WD_ERR_TIMEOUT : WD_OK;
+}
+
+void wd_nn_train_params_default(wd_nn_train_params* p) {
+  if (!p) return;
+  p->samples = 4096;
+  p->batch = 16;
+  p->epochs = 1;
+  p->lr = 2e-3f;
+  p->seed = 4242ull;
+  p->init = 1;
+}
+
+int wd_nn_layer(void* out, const void* in, const float* weights, int cin, int cout,
+                const void* gauge, const int dims[4]) {
+  WD_TRY(check_dims(dims));
+  if (!out || !in || !weights || !gauge) return WD_ERR_NULL;
+  if (!aligned(out) || !aligned(in) || !aligned(weights) || !aligned(gauge)) return WD_ERR_ALIGN;
+  if ((cin != 4 && cin != 8) || (cout != 4 && cout != 8)) return WD_ERR_ARG;
+  if (out == in) return WD_ERR_ALIAS;
+  return nn_layer_impl(out, in, weights, cin, cout, gauge, dims);
+}
+
+int wd_nn_wgrad(float* grad, const void* in, const void* delta, int cin, int cout,
+                const void* gauge, const int dims[4]) {
+  WD_TRY(check_dims(dims));
+  if (!grad || !in || !delta || !gauge) return WD_ERR_NULL;
+  if (!aligned(grad) || !aligned(in) || !aligned(delta) || !aligned(gauge)) return WD_ERR_ALIGN;
+  if ((cin != 4 && cin != 8) || (cout != 4 && cout != 8) || (cin == 4 && cout == 4))
+    return WD_ERR_ARG;
+  return nn_wgrad_impl(grad, in, delta, cin, cout, gauge, dims);
+}
+
+int wd_gaussian_spinor(void* out, unsigned long long seed, unsigned long long stream,
+                       unsigned long long first, const int dims[4]) {
+  WD_TRY(check_dims(dims));
+  if (!out) return WD_ERR_NULL;
+  if (!aligned(out)) return WD_ERR_ALIGN;
+  return gaussian_spinor_impl(out, seed, stream, first, dims);
+}
+
+int wd_nn_init(float* weights, double kappa) {
+  if (!weights) return WD_ERR_NULL;
+  if (!aligned(weights)) return WD_ERR_ALIGN;
+  return nn_init_impl(weights, kappa);
+}
+
+int wd_nn_apply(void* out, const void* in, const float* weights, const void* gauge,
+                const int dims[4]) {
+  WD_TRY(check_dims(dims));
+  if (!out || !in || !weights || !gauge) return WD_ERR_NULL;
+  if (!aligned(out) || !aligned(in) || !aligned(weights) || !aligned(gauge)) return WD_ERR_ALIGN;
+  if (out == in) return WD_ERR_ALIAS;
+  return nn_apply_impl(out, in, weights, gauge, dims);
+}
+
+int wd_nn_train(float* weights, const double* gauge, double kappa, const int dims[4],
+                const wd_nn_train_params* params, wd_nn_train_info* info) {
+  WD_TRY(check_dims(dims));
+  if (!weights || !gauge) return WD_ERR_NULL;
+  if (!aligned(weights) || !aligned(gauge)) return WD_ERR_ALIGN;
+  wd_nn_train_params p;
+  wd_nn_train_params_default(&p);
+  if (params) p = *params;
+  return nn_train_impl(weights, gauge, kappa, dims, &p, info);
+}
+
+int wd_solve_fgcr(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
+                  const float* weights, int m, const wd_solve_params* params,
+                  wd_solve_info* info) {
+  WD_TRY(check_dims(dims));
+  if (!x || !b || !gauge) return WD_ERR_NULL;
+  if (!aligned(x) || !aligned(b) || !aligned(gauge) || (weights && !aligned(weights)))
+    return WD_ERR_ALIGN;
+  if (x == b) return WD_ERR_ALIAS;
+  if (m < 1 || m > 16) return WD_ERR_ARG;
+  return fgcr_impl(x, b, gauge, kappa, dims, weights, params, info, m);
 }
 
 int wd_norm2(double* result, const void* x, const int dims[4], int parity, int prec) {

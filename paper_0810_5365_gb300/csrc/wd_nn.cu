@@ -1,0 +1,846 @@
+// Learned gauge-covariant preconditioner: a three-layer linear network of the
+// nearest-neighbour layers of wd_nn.cuh (4 -> 8 -> 8 -> 4 spin-like channels
+// per colour, i.e. 12 -> 24 -> 24 -> 12 complex channels per site), trained
+// on pairs (b = D x, x) drawn on the GPU to minimise ||N(b) - x||^2, and used
+// as the preconditioner of flexible GCR.  None of this is in the paper; it
+// sits on top of the paper's operator and kernels.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "wd_nn.cuh"
+
+namespace wd {
+
+// parameter layout: layer l has 9 x COUT_l x CIN_l complex weights, stored
+// [d][o][i][re, im], layers back to back
+constexpr int NN_C[4] = {4, 8, 8, 4};
+constexpr int nn_layer_floats(int l) { return 9 * NN_C[l + 1] * NN_C[l] * 2; }
+constexpr int nn_layer_offset(int l) {
+  return l == 0 ? 0 : nn_layer_offset(l - 1) + nn_layer_floats(l - 1);
+}
+constexpr int NN_PARAMS = nn_layer_offset(3);  // 2304 floats
+
+// ---------------------------------------------------------------------------
+// layer launch
+// ---------------------------------------------------------------------------
+
+static cudaError_t nn_layer(int cin, int cout, const Geom& g, const void* gauge, const void* in,
+                            void* out, const float* w, int* err, cudaStream_t st) {
+  NnLayerArgs A;
+  A.g = g;
+  A.gauge = gauge;
+  A.in = (const char*)in;
+  A.out = (char*)out;
+  A.in_half = nn_half_bytes(g.Vh_pad, cin);
+  A.out_half = nn_half_bytes(g.Vh_pad, cout);
+  A.w = w;
+  A.err = err;
+  const int grid = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  if (cin == 4 && cout == 8) nn_layer_kernel<4, 8><<<grid, NN_TILE, 0, st>>>(A);
+  else if (cin == 8 && cout == 8) nn_layer_kernel<8, 8><<<grid, NN_TILE, 0, st>>>(A);
+  else if (cin == 8 && cout == 4) nn_layer_kernel<8, 4><<<grid, NN_TILE, 0, st>>>(A);
+  else if (cin == 4 && cout == 4) nn_layer_kernel<4, 4><<<grid, NN_TILE, 0, st>>>(A);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: G_d[o][i] = sum_{x, a} delta(x)[o][a] conj((T_d phi)(x)[i][a])
+// per-tile partials (fixed order) and a fixed-order sum over tiles
+// ---------------------------------------------------------------------------
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NN_TILE) nn_wgrad_kernel(const NnLayerArgs A,
+                                                           const char* __restrict__ delta,
+                                                           size_t delta_half, float* partials) {
+  constexpr int NV = COUT * CIN * 2;
+  __shared__ float red[4][NV];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Geom& g = A.g;
+  const int tpp = (g.Vh + NN_TILE - 1) / NN_TILE;
+  const int p = blockIdx.x / tpp;
+  const int cb = (blockIdx.x - p * tpp) * NN_TILE + tid;
+  const bool valid = cb < g.Vh;
+  cx<float> dl[COUT * 3];
+  NnNeighbours nbs;
+  if (valid) {
+    nn_neighbours(nbs, cb, p, g);
+    nn_load<COUT>(dl, delta + p * delta_half, cb, g.Vh_pad);
+  } else {
+#pragma unroll
+    for (int k = 0; k < COUT * 3; k++) dl[k] = mk<float>(0.f, 0.f);
+  }
+  for (int d = 0; d < NN_NDIR; d++) {
+    cx<float> t[CIN * 3];
+    if (valid) {
+      nn_transport<CIN>(t, A, nbs, d, p);
+    } else {
+#pragma unroll
+      for (int k = 0; k < CIN * 3; k++) t[k] = mk<float>(0.f, 0.f);
+    }
+#pragma unroll
+    for (int o = 0; o < COUT; o++) {
+#pragma unroll
+      for (int i = 0; i < CIN; i++) {
+        // sum_a delta[o][a] * conj(t[i][a])
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const cx<float> x = dl[o * 3 + a], y = t[i * 3 + a];
+          re = fmaf(x.r, y.r, re);
+          re = fmaf(x.i, y.i, re);
+          im = fmaf(x.i, y.r, im);
+          im = fmaf(-x.r, y.i, im);
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+          re += __shfl_xor_sync(0xffffffffu, re, s);
+          im += __shfl_xor_sync(0xffffffffu, im, s);
+        }
+        if (lane == 0) {
+          red[warp][(o * CIN + i) * 2] = re;
+          red[warp][(o * CIN + i) * 2 + 1] = im;
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = tid; j < NV; j += NN_TILE)
+      partials[((size_t)blockIdx.x * NN_NDIR + d) * NV + j] =
+          red[0][j] + red[1][j] + red[2][j] + red[3][j];
+    __syncthreads();
+  }
+}
+
+// out[j] (+)= sum_t partials[t][j], t in order
+__global__ void nn_sum_tiles(const float* __restrict__ partials, int ntiles, int n, float* out,
+                             int accumulate) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int t = 0; t < ntiles; t++) s += (double)partials[(size_t)t * n + j];
+  out[j] = accumulate ? out[j] + (float)s : (float)s;
+}
+
+static cudaError_t nn_wgrad(int cin, int cout, const Geom& g, const void* gauge, const void* in,
+                            const void* delta, float* partials, float* grad_out, int accumulate,
+                            cudaStream_t st) {
+  NnLayerArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.g = g;
+  A.gauge = gauge;
+  A.in = (const char*)in;
+  A.in_half = nn_half_bytes(g.Vh_pad, cin);
+  const size_t dh = nn_half_bytes(g.Vh_pad, cout);
+  const int grid = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  if (cin == 4 && cout == 8)
+    nn_wgrad_kernel<4, 8><<<grid, NN_TILE, 0, st>>>(A, (const char*)delta, dh, partials);
+  else if (cin == 8 && cout == 8)
+    nn_wgrad_kernel<8, 8><<<grid, NN_TILE, 0, st>>>(A, (const char*)delta, dh, partials);
+  else if (cin == 8 && cout == 4)
+    nn_wgrad_kernel<8, 4><<<grid, NN_TILE, 0, st>>>(A, (const char*)delta, dh, partials);
+  else
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n = NN_NDIR * cout * cin * 2;
+  nn_sum_tiles<<<(n + 127) / 128, 128, 0, st>>>(partials, grid, n, grad_out, accumulate);
+  return cudaGetLastError();
+}
+
+// adjoint weights: W'_e[i][o] = conj(W_{opp(e)}[o][i]); opp swaps +mu and -mu
+__global__ void nn_adjoint_weights(const float* w, float* wa, int cin, int cout) {
+  const int n = NN_NDIR * cout * cin;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int e = t / (cin * cout), rem = t - e * cin * cout;
+    const int i = rem / cout, o = rem - i * cout;   // wa layout [e][i][o]
+    const int d = e == 0 ? 0 : ((e & 1) ? e + 1 : e - 1);
+    wa[t * 2] = w[((d * cout + o) * cin + i) * 2];
+    wa[t * 2 + 1] = -w[((d * cout + o) * cin + i) * 2 + 1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// training data: complex Gaussian spinors from counter-based SplitMix64 +
+// Box-Muller (the same published definitions as the host-side generator:
+// draw j of stream `key` is finalise(key + (j+1) * GAMMA); complex number j
+// uses uniforms 2j and 2j+1), written straight into the packed FP32 layout
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long sm64_finalise(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double sm64_uniform(unsigned long long key, unsigned long long ctr) {
+  const unsigned long long z = sm64_finalise(key + (ctr + 1ull) * 0x9E3779B97F4A7C15ull);
+  return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+unsigned long long sm64_stream_key(unsigned long long seed, unsigned long long stream) {
+  if (stream == 0) return seed;
+  unsigned long long z = (seed ^ (stream * 0xD1B54A32D192ED03ull)) + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// field sample `sample` (counter offset sample * V * 12) of stream key
+__global__ void gaussian_spinor_kernel(char* out, unsigned long long key, unsigned long long first,
+                                       Geom g, size_t half) {
+  const long long V = 2LL * g.Vh;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x[4];
+    long long r = i;
+    for (int m = 0; m < 4; m++) {
+      x[m] = (int)(r % g.L[m]);
+      r /= g.L[m];
+    }
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const int cb = (int)(i >> 1);
+    cx<float> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const unsigned long long j = first + (unsigned long long)i * 12 + k;
+      // FP32 transcendental functions (GB300 runs FP64 at 1/64 rate)
+      const float u1 = (float)sm64_uniform(key, 2 * j), u2 = (float)sm64_uniform(key, 2 * j + 1);
+      const float rad = sqrtf(-logf(u1));
+      float sn, cs;
+      sincosf(6.2831853071795865f * u2, &sn, &cs);
+      v[k] = mk<float>(rad * cs, rad * sn);
+    }
+    store_spinor<WD_F32, float>(out + par * half, cb, g.Vh_pad, v);
+  }
+}
+
+// Adam on the real and imaginary parts (Kingma and Ba, ICLR 2015)
+__global__ void nn_adam(float* w, const float* grad, float* m, float* v, int n, float lr,
+                        float b1, float b2, float eps, int step, float gscale) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const float gj = grad[j] * gscale;
+  const float mj = b1 * m[j] + (1.f - b1) * gj;
+  const float vj = b2 * v[j] + (1.f - b2) * gj * gj;
+  m[j] = mj;
+  v[j] = vj;
+  const float mh = mj / (1.f - powf(b1, (float)step));
+  const float vh = vj / (1.f - powf(b2, (float)step));
+  w[j] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// network application
+// ---------------------------------------------------------------------------
+
+struct NnBuffers {
+  void* h1 = nullptr;  // 8 channels
+  void* h2 = nullptr;  // 8 channels
+  size_t bytes8 = 0;
+};
+
+static cudaError_t nn_forward(const Geom& g, const void* gauge, const float* w, const void* in,
+                              void* out, NnBuffers& B, int* err, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = nn_layer(4, 8, g, gauge, in, B.h1, w + nn_layer_offset(0), err, st))) return e;
+  if ((e = nn_layer(8, 8, g, gauge, B.h1, B.h2, w + nn_layer_offset(1), err, st))) return e;
+  return nn_layer(8, 4, g, gauge, B.h2, out, w + nn_layer_offset(2), err, st);
+}
+
+// (1 + c kappa H) on the first four channels of a layer; identity on the rest
+static void init_hopping_layer(float* w, int cin, int cout, double cr, double ci, double kappa) {
+  // chiral basis: gamma_mu = [[0, A_mu], [A_mu^+, 0]], A = -i sigma_{1,2,3}, A_t = 1
+  const double SX[2][2][2] = {{{0, 0}, {1, 0}}, {{1, 0}, {0, 0}}};
+  const double SY[2][2][2] = {{{0, 0}, {0, -1}}, {{0, 1}, {0, 0}}};
+  const double SZ[2][2][2] = {{{1, 0}, {0, 0}}, {{0, 0}, {-1, 0}}};
+  double gam[4][4][4][2];
+  std::memset(gam, 0, sizeof(gam));
+  const double(*S[3])[2][2] = {SX, SY, SZ};
+  for (int mu = 0; mu < 4; mu++)
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++) {
+        double re, im;  // A_mu[a][b]
+        if (mu < 3) {   // -i sigma
+          re = S[mu][a][b][1];
+          im = -S[mu][a][b][0];
+        } else {
+          re = a == b ? 1.0 : 0.0;
+          im = 0.0;
+        }
+        gam[mu][a][b + 2][0] = re;       // upper right: A
+        gam[mu][a][b + 2][1] = im;
+        gam[mu][b + 2][a][0] = re;       // lower left: A^+ (conjugate transpose)
+        gam[mu][b + 2][a][1] = -im;
+      }
+  std::memset(w, 0, sizeof(float) * 9 * cout * cin * 2);
+  auto W = [&](int d, int o, int i) -> float* { return w + ((d * cout + o) * cin + i) * 2; };
+  for (int o = 0; o < cout && o < cin; o++) W(0, o, o)[0] = 1.f;
+  for (int mu = 0; mu < 4; mu++)
+    for (int fb = 0; fb < 2; fb++) {
+      const int d = 1 + 2 * mu + fb;
+      const double sgn = fb == 0 ? -1.0 : 1.0;  // (1 - gamma) forward, (1 + gamma) backward
+      for (int o = 0; o < 4; o++)
+        for (int i = 0; i < 4; i++) {
+          double pr = (o == i ? 1.0 : 0.0) + sgn * gam[mu][o][i][0];
+          double pi = sgn * gam[mu][o][i][1];
+          // times c kappa
+          const double vr = kappa * (cr * pr - ci * pi), vi = kappa * (cr * pi + ci * pr);
+          W(d, o, i)[0] = (float)vr;
+          W(d, o, i)[1] = (float)vi;
+        }
+    }
+}
+
+void nn_init_hopping_series(float* w_host, double kappa) {
+  // (1 + k H)(1 + i k H)(1 - i k H) = 1 + kH + k^2 H^2 + k^3 H^3
+  init_hopping_layer(w_host + nn_layer_offset(0), 4, 8, 1.0, 0.0, kappa);
+  init_hopping_layer(w_host + nn_layer_offset(1), 8, 8, 0.0, 1.0, kappa);
+  init_hopping_layer(w_host + nn_layer_offset(2), 8, 4, 0.0, -1.0, kappa);
+}
+
+
+// ---------------------------------------------------------------------------
+// flexible GCR kernels (classical Gram-Schmidt in one pass each)
+// ---------------------------------------------------------------------------
+
+constexpr int GCR_MAXK = 16;
+
+struct PtrList {
+  const char* p[GCR_MAXK];
+};
+
+// res[j] = <v_j, w> (complex), j < k; packed FP32 full fields
+__global__ void __launch_bounds__(256) multi_cdot_kernel(const PtrList vs, int k, const char* w,
+                                                         Geom g, size_t half, RedScratch rs,
+                                                         double* res) {
+  double acc[2 * GCR_MAXK];
+#pragma unroll
+  for (int j = 0; j < 2 * GCR_MAXK; j++) acc[j] = 0.0;
+  const long long n = 2LL * g.Vh;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
+    cx<float> a[12];
+    load_spinor_rw<WD_F32, float>(a, w + h * half, cb, g.Vh_pad);
+#pragma unroll
+    for (int j = 0; j < GCR_MAXK; j++) {
+      if (j < k) {
+        cx<float> b[12];
+        load_spinor_rw<WD_F32, float>(b, vs.p[j] + h * half, cb, g.Vh_pad);
+        site_cdot(b, a, acc[2 * j], acc[2 * j + 1]);
+      }
+    }
+  }
+  double tot[2 * GCR_MAXK];
+  if (grid_reduce<2 * GCR_MAXK, 256>(acc, rs, tot) && threadIdx.x == 0) {
+    for (int j = 0; j < 2 * k; j++) res[j] = tot[j];
+  }
+}
+
+// w -= sum_j beta_j W_j ; z -= sum_j beta_j Z_j ; beta_j = dots[j] / nrm[j]
+__global__ void __launch_bounds__(256) multi_axpy_kernel(const PtrList Ws, const PtrList Zs, int k,
+                                                         char* w, char* z, const double* dots,
+                                                         const double* nrm, Geom g, size_t half) {
+  float br[GCR_MAXK], bi[GCR_MAXK];
+#pragma unroll
+  for (int j = 0; j < GCR_MAXK; j++) {
+    br[j] = j < k ? (float)(dots[2 * j] / nrm[j]) : 0.f;
+    bi[j] = j < k ? (float)(dots[2 * j + 1] / nrm[j]) : 0.f;
+  }
+  const long long n = 2LL * g.Vh;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
+    cx<float> a[12], c[12];
+    load_spinor_rw<WD_F32, float>(a, w + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(c, z + h * half, cb, g.Vh_pad);
+#pragma unroll
+    for (int j = 0; j < GCR_MAXK; j++) {
+      if (j < k) {
+        cx<float> u[12], v[12];
+        load_spinor_rw<WD_F32, float>(u, Ws.p[j] + h * half, cb, g.Vh_pad);
+        load_spinor_rw<WD_F32, float>(v, Zs.p[j] + h * half, cb, g.Vh_pad);
+#pragma unroll
+        for (int q = 0; q < 12; q++) {
+          a[q].r -= br[j] * u[q].r - bi[j] * u[q].i;
+          a[q].i -= br[j] * u[q].i + bi[j] * u[q].r;
+          c[q].r -= br[j] * v[q].r - bi[j] * v[q].i;
+          c[q].i -= br[j] * v[q].i + bi[j] * v[q].r;
+        }
+      }
+    }
+    store_spinor<WD_F32, float>(w + h * half, cb, g.Vh_pad, a);
+    store_spinor<WD_F32, float>(z + h * half, cb, g.Vh_pad, c);
+  }
+}
+
+// out[0] = ||w||^2, out[1..2] = <w, r>
+__global__ void __launch_bounds__(256) norm_cdot_kernel(const char* w, const char* r, Geom g,
+                                                        size_t half, RedScratch rs, double* out) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  const long long n = 2LL * g.Vh;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
+    cx<float> a[12], b[12];
+    load_spinor_rw<WD_F32, float>(a, w + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(b, r + h * half, cb, g.Vh_pad);
+    acc[0] += site_norm2(a);
+    site_cdot(a, b, acc[1], acc[2]);
+  }
+  double tot[3];
+  if (grid_reduce<3, 256>(acc, rs, tot) && threadIdx.x == 0) {
+    out[0] = tot[0];
+    out[1] = tot[1];
+    out[2] = tot[2];
+  }
+}
+
+// x += alpha z ; r -= alpha w ; out = ||r||^2 ; alpha = wr / ww
+__global__ void __launch_bounds__(256) gcr_update_kernel(char* x, char* r, const char* z,
+                                                         const char* w, const double* nc, Geom g,
+                                                         size_t half, RedScratch rs, double* out) {
+  const float ar = (float)(nc[1] / nc[0]), ai = (float)(nc[2] / nc[0]);
+  double acc[1] = {0.0};
+  const long long n = 2LL * g.Vh;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
+    cx<float> xv[12], rv[12], zv[12], wv[12];
+    load_spinor_rw<WD_F32, float>(xv, x + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(rv, r + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(zv, z + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(wv, w + h * half, cb, g.Vh_pad);
+#pragma unroll
+    for (int q = 0; q < 12; q++) {
+      xv[q].r += ar * zv[q].r - ai * zv[q].i;
+      xv[q].i += ar * zv[q].i + ai * zv[q].r;
+      rv[q].r -= ar * wv[q].r - ai * wv[q].i;
+      rv[q].i -= ar * wv[q].i + ai * wv[q].r;
+    }
+    store_spinor<WD_F32, float>(x + h * half, cb, g.Vh_pad, xv);
+    store_spinor<WD_F32, float>(r + h * half, cb, g.Vh_pad, rv);
+    acc[0] += site_norm2(rv);
+  }
+  double tot[1];
+  if (grid_reduce<1, 256>(acc, rs, tot) && threadIdx.x == 0) out[0] = tot[0];
+}
+
+// x64 += xs (F32 -> F64, full fields); xs = 0
+__global__ void accumulate_full_kernel(char* x64, char* xs, Geom g, size_t h64, size_t h32) {
+  const long long n = 2LL * g.Vh;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
+    cx<double> a[12];
+    cx<float> b[12];
+    load_spinor_rw<WD_F64, double>(a, x64 + h * h64, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(b, xs + h * h32, cb, g.Vh_pad);
+#pragma unroll
+    for (int q = 0; q < 12; q++) {
+      a[q].r += (double)b[q].r;
+      a[q].i += (double)b[q].i;
+      b[q] = mk<float>(0.f, 0.f);
+    }
+    store_spinor<WD_F64, double>(x64 + h * h64, cb, g.Vh_pad, a);
+    store_spinor<WD_F32, float>(xs + h * h32, cb, g.Vh_pad, b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Alloc {
+  std::vector<void*> ptrs;
+  cudaError_t get(void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  ~Alloc() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// out = in - kappa H in on packed full fields (a = -kappa) or the variant
+// out = in - D in ... through the single-field kernel
+cudaError_t full_op(int prec, int recon, const void* gauge, void* out, const void* in,
+                    double kappa, const Geom& g, cudaStream_t st, const void* bfield = nullptr) {
+  const size_t h = spinor_half_bytes(g, prec);
+  for (int p = 0; p < 2; p++) {
+    DslashArgs d;
+    d.out = (char*)out + p * h;
+    d.in = (const char*)in + (1 - p) * h;
+    d.gauge = gauge;
+    if (bfield) {
+      // out = b - D in = b - in + kappa H in
+      d.a = kappa;
+      d.x = (const char*)bfield + p * h;
+      d.bx = 1.0;
+      d.y = (const char*)in + p * h;
+      d.cy = -1.0;
+    } else {
+      d.a = -kappa;
+      d.x = (const char*)in + p * h;
+      d.bx = 1.0;
+      d.y = nullptr;
+      d.cy = 0.0;
+    }
+    d.norm_out = nullptr;
+    d.rs = scratch();
+    d.g = g;
+    d.parity = p;
+    cudaError_t e = launch_dslash(prec, d, recon, false, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+#define NCK(call)                                 \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) {                      \
+      state().last_cuda_error = (int)e_;          \
+      return WD_ERR_CUDA;                         \
+    }                                             \
+  } while (0)
+
+}  // namespace
+
+int nn_apply_impl(void* out, const void* in, const float* w, const void* gauge, const int dims[4]) {
+  const Geom g = make_geom(dims);
+  cudaStream_t st = state().stream;
+  Alloc al;
+  NnBuffers B;
+  B.bytes8 = 2 * nn_half_bytes(g.Vh_pad, 8);
+  NCK(al.get(&B.h1, B.bytes8));
+  NCK(al.get(&B.h2, B.bytes8));
+  int* flag = nullptr;
+  NCK(device_flag(&flag, st));
+  NCK(nn_forward(g, gauge, w, in, out, B, flag, st));
+  int hflag = 0;
+  NCK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NCK(cudaStreamSynchronize(st));
+  return hflag ? WD_ERR_TIMEOUT : WD_OK;
+}
+
+int nn_layer_impl(void* out, const void* in, const float* w, int cin, int cout, const void* gauge,
+                  const int dims[4]) {
+  const Geom g = make_geom(dims);
+  cudaStream_t st = state().stream;
+  int* flag = nullptr;
+  NCK(device_flag(&flag, st));
+  NCK(nn_layer(cin, cout, g, gauge, in, out, w, flag, st));
+  int hflag = 0;
+  NCK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NCK(cudaStreamSynchronize(st));
+  return hflag ? WD_ERR_TIMEOUT : WD_OK;
+}
+
+int nn_wgrad_impl(float* grad, const void* in, const void* delta, int cin, int cout,
+                  const void* gauge, const int dims[4]) {
+  const Geom g = make_geom(dims);
+  cudaStream_t st = state().stream;
+  Alloc al;
+  void* part;
+  const int ntile = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  NCK(al.get(&part, (size_t)ntile * NN_NDIR * cout * cin * 2 * sizeof(float)));
+  NCK(nn_wgrad(cin, cout, g, gauge, in, delta, (float*)part, grad, 0, st));
+  NCK(cudaStreamSynchronize(st));
+  return WD_OK;
+}
+
+int gaussian_spinor_impl(void* out, unsigned long long seed, unsigned long long stream,
+                         unsigned long long first, const int dims[4]) {
+  const Geom g = make_geom(dims);
+  cudaStream_t st = state().stream;
+  gaussian_spinor_kernel<<<blas_grid(2LL * g.Vh, 256), 256, 0, st>>>(
+      (char*)out, sm64_stream_key(seed, stream), first, g, spinor_half_bytes(g, WD_F32));
+  NCK(cudaGetLastError());
+  return WD_OK;
+}
+
+int nn_init_impl(float* w_dev, double kappa) {
+  std::vector<float> h(NN_PARAMS);
+  nn_init_hopping_series(h.data(), kappa);
+  NCK(cudaMemcpy(w_dev, h.data(), NN_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
+  return WD_OK;
+}
+
+int nn_train_impl(float* w, const double* gauge, double kappa, const int dims[4],
+                  const wd_nn_train_params* prm, wd_nn_train_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  wd_nn_train_params P = *prm;
+  if (P.samples < 1 || P.batch < 1 || P.epochs < 1 || !(P.lr > 0)) return WD_ERR_ARG;
+  const Geom g = make_geom(dims);
+  cudaStream_t st = state().stream;
+  Alloc al;
+  const size_t V = 2 * (size_t)g.Vh;
+  const size_t h32 = spinor_half_bytes(g, WD_F32);
+  // packed FP32 links (network transport and the operator that draws b)
+  void* gp;
+  NCK(al.get(&gp, gauge_bytes(g, WD_F32, 12)));
+  const double* gd = gauge;
+  if (!on_device(gauge)) {
+    void* v;
+    NCK(al.get(&v, 4 * V * 18 * sizeof(double)));
+    NCK(cudaMemcpyAsync(v, gauge, 4 * V * 18 * sizeof(double), cudaMemcpyHostToDevice, st));
+    gd = (const double*)v;
+  }
+  NCK(pack_gauge(gp, gd, g, WD_F32, 12, st));
+  if (P.init) NCK((cudaError_t)(nn_init_impl(w, kappa) == WD_OK ? cudaSuccess : cudaErrorUnknown));
+  void *x, *b, *y, *dl, *wa, *grad, *m, *v2, *part, *losses;
+  NnBuffers B;
+  B.bytes8 = 2 * nn_half_bytes(g.Vh_pad, 8);
+  void *d1, *d2;
+  NCK(al.get(&x, 2 * h32));
+  NCK(al.get(&b, 2 * h32));
+  NCK(al.get(&y, 2 * h32));
+  NCK(al.get(&dl, 2 * h32));
+  NCK(al.get(&B.h1, B.bytes8));
+  NCK(al.get(&B.h2, B.bytes8));
+  NCK(al.get(&d1, B.bytes8));
+  NCK(al.get(&d2, B.bytes8));
+  NCK(al.get(&wa, NN_PARAMS * sizeof(float)));
+  NCK(al.get(&grad, NN_PARAMS * sizeof(float)));
+  NCK(al.get(&m, NN_PARAMS * sizeof(float)));
+  NCK(al.get(&v2, NN_PARAMS * sizeof(float)));
+  const int ntile = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  NCK(al.get(&part, (size_t)ntile * NN_NDIR * 8 * 8 * 2 * sizeof(float)));
+  const int steps_per_epoch = (P.samples + P.batch - 1) / P.batch;
+  const int nsteps = steps_per_epoch * P.epochs;
+  NCK(al.get(&losses, (size_t)nsteps * 2 * sizeof(double)));
+  NCK(cudaMemsetAsync(m, 0, NN_PARAMS * sizeof(float), st));
+  NCK(cudaMemsetAsync(v2, 0, NN_PARAMS * sizeof(float), st));
+  NCK(cudaMemsetAsync(losses, 0, (size_t)nsteps * 2 * sizeof(double), st));
+  int* flag = nullptr;
+  NCK(device_flag(&flag, st));
+  NCK(ensure_scratch(4096));
+  const unsigned long long key = sm64_stream_key(P.seed, 7);
+  float* W = w;
+  float* WA = (float*)wa;
+  const int grid = blas_grid(V, 256);
+  for (int step = 0; step < nsteps; step++) {
+    // adjoint weights of layers 2 and 3 (for the input gradients)
+    nn_adjoint_weights<<<8, 256, 0, st>>>(W + nn_layer_offset(1), WA + nn_layer_offset(1), 8, 8);
+    nn_adjoint_weights<<<8, 256, 0, st>>>(W + nn_layer_offset(2), WA + nn_layer_offset(2), 8, 4);
+    NCK(cudaGetLastError());
+    for (int sbt = 0; sbt < P.batch; sbt++) {
+      const long long sample = ((long long)step * P.batch + sbt) % P.samples;
+      gaussian_spinor_kernel<<<grid, 256, 0, st>>>((char*)x, key,
+                                                   (unsigned long long)sample * V * 12, g, h32);
+      NCK(cudaGetLastError());
+      NCK(full_op(WD_F32, 12, gp, b, x, kappa, g, st));                    // b = D x
+      NCK(nn_forward(g, gp, W, b, y, B, flag, st));                        // y = N(b)
+      NCK(axpby(1.0, y, 0.0, dl, g, WD_F32, 2, st));                       // dl = y
+      NCK(axpby(-1.0, x, 1.0, dl, g, WD_F32, 2, st));                      // dl = y - x
+      // the loss of the batch's last sample: ||y - x||^2 and ||x||^2
+      double* L = (double*)losses + 2 * step;
+      NCK(norm2(L + 0, dl, g, WD_F32, 2, st));
+      NCK(norm2(L + 1, x, g, WD_F32, 2, st));
+      // backward: G3 (h2 -> y), delta2 = L3^+ dl, G2, delta1 = L2^+ delta2, G1
+      const int acc = sbt > 0;
+      NCK(nn_wgrad(8, 4, g, gp, B.h2, dl, (float*)part, (float*)grad + nn_layer_offset(2), acc, st));
+      NCK(nn_layer(4, 8, g, gp, dl, d2, WA + nn_layer_offset(2), flag, st));
+      NCK(nn_wgrad(8, 8, g, gp, B.h1, d2, (float*)part, (float*)grad + nn_layer_offset(1), acc, st));
+      NCK(nn_layer(8, 8, g, gp, d2, d1, WA + nn_layer_offset(1), flag, st));
+      NCK(nn_wgrad(4, 8, g, gp, b, d1, (float*)part, (float*)grad + nn_layer_offset(0), acc, st));
+    }
+    const float gscale = (float)(1.0 / ((double)P.batch * 12.0 * (double)V));
+    nn_adam<<<(NN_PARAMS + 255) / 256, 256, 0, st>>>(W, (const float*)grad, (float*)m, (float*)v2,
+                                                    NN_PARAMS, P.lr, 0.9f, 0.999f, 1e-8f, step + 1,
+                                                    gscale);
+    NCK(cudaGetLastError());
+  }
+  std::vector<double> hl((size_t)nsteps * 2);
+  NCK(cudaMemcpyAsync(hl.data(), losses, hl.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  int hflag = 0;
+  NCK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NCK(cudaStreamSynchronize(st));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->steps = nsteps;
+    info->loss_first = hl[1] > 0 ? hl[0] / hl[1] : 0.0;
+    info->loss_last = hl[2 * nsteps - 1] > 0 ? hl[2 * nsteps - 2] / hl[2 * nsteps - 1] : 0.0;
+    info->seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return hflag ? WD_ERR_TIMEOUT : WD_OK;
+}
+
+// flexible GCR(m) on the full operator D, preconditioned by the network
+// (w == nullptr: no preconditioner), FP32 inner vectors, FP64 restarts
+int fgcr_impl(double* x, const double* bsrc, const double* gauge, double kappa,
+              const int dims[4], const float* wts, const wd_solve_params* prm,
+              wd_solve_info* info, int m) {
+  const auto t0 = std::chrono::steady_clock::now();
+  wd_solve_params P;
+  wd_solve_params_default(&P);
+  if (prm) P = *prm;
+  if (m < 1 || m > GCR_MAXK) return WD_ERR_ARG;
+  const Geom g = make_geom(dims);
+  cudaStream_t st = state().stream;
+  Alloc al;
+  const size_t V = 2 * (size_t)g.Vh;
+  const size_t h32 = spinor_half_bytes(g, WD_F32), h64 = spinor_half_bytes(g, WD_F64);
+  void *g32, *g64;
+  NCK(al.get(&g32, gauge_bytes(g, WD_F32, 12)));
+  NCK(al.get(&g64, gauge_bytes(g, WD_F64, 18)));
+  const double* gd = gauge;
+  if (!on_device(gauge)) {
+    void* v;
+    NCK(al.get(&v, 4 * V * 18 * sizeof(double)));
+    NCK(cudaMemcpyAsync(v, gauge, 4 * V * 18 * sizeof(double), cudaMemcpyHostToDevice, st));
+    gd = (const double*)v;
+  }
+  NCK(pack_gauge(g32, gd, g, WD_F32, 12, st));
+  NCK(pack_gauge(g64, gd, g, WD_F64, 18, st));
+  const double* bd = bsrc;
+  double* canon = nullptr;
+  {
+    void* v;
+    NCK(al.get(&v, V * 24 * sizeof(double)));
+    canon = (double*)v;
+  }
+  if (!on_device(bsrc)) {
+    NCK(cudaMemcpyAsync(canon, bsrc, V * 24 * sizeof(double), cudaMemcpyHostToDevice, st));
+    bd = canon;
+  }
+  void *b64, *x64, *r64, *r, *xs, *zs, *ws, *scal;
+  NCK(al.get(&b64, 2 * h64));
+  NCK(al.get(&x64, 2 * h64));
+  NCK(al.get(&r64, 2 * h64));
+  NCK(al.get(&r, 2 * h32));
+  NCK(al.get(&xs, 2 * h32));
+  NCK(al.get(&zs, (size_t)m * 2 * h32));
+  NCK(al.get(&ws, (size_t)m * 2 * h32));
+  NCK(al.get(&scal, (size_t)(4 * GCR_MAXK + 16) * sizeof(double)));
+  double* S = (double*)scal;
+  double* dots = S;                       // 2 * GCR_MAXK
+  double* nrm = S + 2 * GCR_MAXK;          // GCR_MAXK
+  double* nc = S + 3 * GCR_MAXK;           // 3
+  double* rr = nc + 3;                     // 1
+  double* r64n = rr + 1;                   // 1
+  double* bn = r64n + 1;                   // 1
+  constexpr int I_RR = 3 * GCR_MAXK + 3, I_R64 = 3 * GCR_MAXK + 4, I_BN = 3 * GCR_MAXK + 5;
+  NnBuffers B;
+  B.bytes8 = 2 * nn_half_bytes(g.Vh_pad, 8);
+  if (wts) {
+    NCK(al.get(&B.h1, B.bytes8));
+    NCK(al.get(&B.h2, B.bytes8));
+  }
+  int* flag = nullptr;
+  NCK(device_flag(&flag, st));
+  NCK(ensure_scratch((size_t)num_sms() * 8 * 2 * GCR_MAXK + 1024));
+  NCK(pack_spinor(b64, bd, g, WD_FULL, WD_F64, st));
+  NCK(norm2(bn, b64, g, WD_F64, 2, st));
+  NCK(cudaMemsetAsync(x64, 0, 2 * h64, st));
+  NCK(cudaMemsetAsync(xs, 0, 2 * h32, st));
+  const int grid = blas_grid(V, 256);
+  RedScratch rs = scratch();
+  double hs[4 * GCR_MAXK + 16];
+  auto rd = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(hs, S, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+  };
+  // r64 = b - D x64 ; r = r64
+  auto restart = [&]() -> cudaError_t {
+    cudaError_t e = full_op(WD_F64, 18, g64, r64, x64, kappa, g, st, b64);
+    if (e == cudaSuccess) e = norm2(r64n, r64, g, WD_F64, 2, st);
+    if (e == cudaSuccess) e = convert_spinor(r, WD_F32, r64, WD_F64, g, 2, st);
+    return e;
+  };
+  NCK(restart());
+  NCK(rd());
+  const double bnorm = std::sqrt(hs[I_BN]);
+  const double target = P.tol * bnorm * 0.9;
+  int iters = 0, status = WD_ERR_NOCONV, restarts = 0;
+  double rel = bnorm > 0 ? std::sqrt(hs[I_R64]) / bnorm : 0.0;
+  bool done = !(bnorm > 0) || std::sqrt(hs[I_R64]) <= target;
+  while (!done && iters < P.maxiter) {
+    int k = 0;
+    for (; k < m && iters < P.maxiter; k++, iters++) {
+      char* zk = (char*)zs + (size_t)k * 2 * h32;
+      char* wk = (char*)ws + (size_t)k * 2 * h32;
+      if (wts)
+        NCK(nn_forward(g, g32, wts, r, zk, B, flag, st));
+      else
+        NCK(convert_spinor(zk, WD_F32, r, WD_F32, g, 2, st));
+      NCK(full_op(WD_F32, 12, g32, wk, zk, kappa, g, st));
+      if (k > 0) {
+        PtrList Wl, Zl;
+        for (int j = 0; j < GCR_MAXK; j++) {
+          Wl.p[j] = (const char*)ws + (size_t)(j < k ? j : 0) * 2 * h32;
+          Zl.p[j] = (const char*)zs + (size_t)(j < k ? j : 0) * 2 * h32;
+        }
+        multi_cdot_kernel<<<grid, 256, 0, st>>>(Wl, k, wk, g, h32, rs, dots);
+        NCK(cudaGetLastError());
+        multi_axpy_kernel<<<grid, 256, 0, st>>>(Wl, Zl, k, wk, zk, dots, nrm, g, h32);
+        NCK(cudaGetLastError());
+      }
+      norm_cdot_kernel<<<grid, 256, 0, st>>>(wk, (const char*)r, g, h32, rs, nc);
+      NCK(cudaGetLastError());
+      NCK(cudaMemcpyAsync(nrm + k, nc, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      gcr_update_kernel<<<grid, 256, 0, st>>>((char*)xs, (char*)r, zk, wk, nc, g, h32, rs, rr);
+      NCK(cudaGetLastError());
+      NCK(rd());
+      const double rn = std::sqrt(hs[I_RR]);
+      if (!std::isfinite(rn)) {
+        status = WD_ERR_NONFINITE;
+        done = true;
+        break;
+      }
+      if (rn <= target) {
+        k++;
+        iters++;
+        break;
+      }
+    }
+    if (status == WD_ERR_NONFINITE) break;
+    accumulate_full_kernel<<<grid, 256, 0, st>>>((char*)x64, (char*)xs, g, h64, h32);
+    NCK(cudaGetLastError());
+    NCK(restart());
+    NCK(rd());
+    restarts++;
+    const double r64v = std::sqrt(hs[I_R64]);
+    rel = r64v / bnorm;
+    if (!std::isfinite(r64v)) {
+      status = WD_ERR_NONFINITE;
+      break;
+    }
+    if (r64v <= target) done = true;
+  }
+  if (done && status != WD_ERR_NONFINITE) status = WD_OK;
+  // unpack
+  const bool xdev = on_device(x);
+  double* xd = xdev ? x : canon;
+  NCK(unpack_spinor(xd, x64, g, WD_FULL, WD_F64, st));
+  if (!xdev) NCK(cudaMemcpyAsync(x, xd, V * 24 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  int hflag = 0;
+  NCK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NCK(cudaStreamSynchronize(st));
+  if (hflag) status = WD_ERR_TIMEOUT;
+  if (status == WD_OK && !(rel <= P.tol)) status = WD_ERR_NOCONV;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = iters;
+    info->reliable_updates = restarts;
+    info->status = status;
+    info->true_residual = rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+}  // namespace wd

@@ -1,0 +1,262 @@
+// A gauge-covariant nearest-neighbour convolution layer (the learned
+// preconditioner; the paper has no such component):
+//
+//   y(x)[o][a] = sum_{d=0..8} sum_i W_d[o][i] (T_d phi)(x)[i][a]
+//
+// T_0 phi(x) = phi(x); T_{1+2mu} phi(x) = U_mu(x) phi(x+mu);
+// T_{2+2mu} phi(x) = U_mu(x-mu)^+ phi(x-mu), with the antiperiodic time sign
+// of the Wilson operator.  W_d acts on the channel index only (a = colour),
+// so the layer commutes with gauge transformations.  Complex weights, FP32
+// activations, BF16 tensor-core contraction with FP32 accumulation.
+//
+// Activation layout: the site-blocked layout of the spinor fields with C
+// channels x 3 colours per site (complex index c*3 + a, two complexes per
+// 16-byte group, NG = 3C/2 groups); a full field is the even half followed by
+// the odd half.  With C = 4 this is exactly the packed FP32 spinor.
+//
+// Per 128-site tile the nine directions are gathered in chunks of K = 16 real
+// columns (one direction for 8 input channels, two for 4): each thread
+// transports its site's neighbour channels on the CUDA cores and writes them
+// as BF16 rows of three shared-memory A tiles (one per colour, K-major, no
+// swizzle); one thread then issues three tcgen05.mma (128 x 16 x 16) that
+// accumulate into three TMEM accumulators.  Two A buffers alternate, each
+// guarded by an mbarrier that the MMA completion arrives on.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "wd_internal.h"
+#include "wd_tc.cuh"
+
+namespace wd {
+
+constexpr int NN_TILE = 128;
+constexpr int NN_NDIR = 9;
+constexpr long NN_SPIN_LIMIT = 1L << 22;
+
+struct NnLayerArgs {
+  Geom g;
+  const void* gauge;       // packed FP32, 12 reals
+  const char* in;          // CIN channels, full field
+  char* out;               // COUT channels, full field
+  size_t in_half, out_half;  // bytes per parity half
+  const float* w;          // [9][COUT][CIN] complex (re, im)
+  int* err;
+};
+
+__host__ __device__ constexpr size_t nn_half_bytes(const int vh_pad, int C) {
+  return ((size_t)vh_pad * C * 24 + 255) / 256 * 256;
+}
+
+// the 9 directions: neighbour site (other parity for d > 0), link, sign
+struct NnNeighbours {
+  int nb[9];
+  int lreg[9];
+  int lcb[9];
+  bool flip[9];
+};
+
+__device__ __forceinline__ void nn_neighbours(NnNeighbours& n, int cb, int p, const Geom& g) {
+  int x0, x1, x2, x3;
+  cb_coords(cb, p, g, x0, x1, x2, x3);
+  const int row = cb - (x0 >> 1);
+  const int q = 1 - p;
+  n.nb[0] = cb;
+  n.lreg[0] = -1;
+  n.lcb[0] = 0;
+  n.flip[0] = false;
+  const int f0 = row + ((x0 + 1 == g.L[0] ? 0 : x0 + 1) >> 1);
+  const int b0 = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
+  const int f1 = x1 == g.L[1] - 1 ? cb - (g.L[1] - 1) * g.S1 : cb + g.S1;
+  const int b1 = x1 == 0 ? cb + (g.L[1] - 1) * g.S1 : cb - g.S1;
+  const int f2 = x2 == g.L[2] - 1 ? cb - (g.L[2] - 1) * g.S2 : cb + g.S2;
+  const int b2 = x2 == 0 ? cb + (g.L[2] - 1) * g.S2 : cb - g.S2;
+  const int f3 = x3 == g.L[3] - 1 ? cb - (g.L[3] - 1) * g.S3 : cb + g.S3;
+  const int b3 = x3 == 0 ? cb + (g.L[3] - 1) * g.S3 : cb - g.S3;
+  const int fw[4] = {f0, f1, f2, f3}, bw[4] = {b0, b1, b2, b3};
+#pragma unroll
+  for (int mu = 0; mu < 4; mu++) {
+    n.nb[1 + 2 * mu] = fw[mu];
+    n.lreg[1 + 2 * mu] = 2 * mu + p;
+    n.lcb[1 + 2 * mu] = cb;
+    n.flip[1 + 2 * mu] = mu == 3 && x3 == g.L[3] - 1;
+    n.nb[2 + 2 * mu] = bw[mu];
+    n.lreg[2 + 2 * mu] = 2 * mu + q;
+    n.lcb[2 + 2 * mu] = bw[mu];
+    n.flip[2 + 2 * mu] = mu == 3 && x3 == 0;
+  }
+}
+
+// load C channels x 3 colours of site cb of a packed activation half
+template <int C>
+__device__ __forceinline__ void nn_load(cx<float> (&v)[C * 3], const char* half, int cb, int vh_pad) {
+  constexpr int NG = 3 * C / 2;
+  const float4* p = (const float4*)half;
+#pragma unroll
+  for (int k = 0; k < NG; k++) {
+    float4 q = __ldg(p + sbi(cb, k, NG));
+    v[2 * k] = mk<float>(q.x, q.y);
+    v[2 * k + 1] = mk<float>(q.z, q.w);
+  }
+}
+
+template <int C>
+__device__ __forceinline__ void nn_store(char* half, int cb, int vh_pad, const cx<float> (&v)[C * 3]) {
+  constexpr int NG = 3 * C / 2;
+  float4* p = (float4*)half;
+#pragma unroll
+  for (int k = 0; k < NG; k++)
+    p[sbi(cb, k, NG)] = make_float4(v[2 * k].r, v[2 * k].i, v[2 * k + 1].r, v[2 * k + 1].i);
+}
+
+// the transported input channels of direction d at this site
+template <int C>
+__device__ __forceinline__ void nn_transport(cx<float> (&t)[C * 3], const NnLayerArgs& A,
+                                             const NnNeighbours& n, int d, int p) {
+  const int src_par = d == 0 ? p : 1 - p;
+  cx<float> v[C * 3];
+  nn_load<C>(v, A.in + src_par * A.in_half, n.nb[d], A.g.Vh_pad);
+  if (d == 0) {
+#pragma unroll
+    for (int k = 0; k < C * 3; k++) t[k] = v[k];
+    return;
+  }
+  cx<float> u[9];
+  load_link<WD_F32, 12, float>(u, A.gauge, n.lreg[d], n.lcb[d], A.g.Vh_pad);
+  const float s = n.flip[d] ? -1.f : 1.f;
+  const bool fwd = (d & 1) != 0;
+#pragma unroll
+  for (int c = 0; c < C; c++) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<float> w = mk<float>(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        if (fwd)
+          w = cmadd(u[a * 3 + b], v[c * 3 + b], w);
+        else
+          w = cjmadd(u[b * 3 + a], v[c * 3 + b], w);
+      }
+      t[c * 3 + a] = s * w;
+    }
+  }
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NN_TILE) nn_layer_kernel(const NnLayerArgs A) {
+  static_assert(CIN == 4 || CIN == 8, "4 or 8 input channels");
+  static_assert(COUT == 4 || COUT == 8, "4 or 8 output channels");
+  constexpr int DPC = 16 / (2 * CIN);                  // directions per K = 16 chunk
+  constexpr int NCHUNK = (NN_NDIR + DPC - 1) / DPC;
+  constexpr int NPAD = 16;                             // N of the MMA (2 COUT <= 16)
+  constexpr uint32_t ABUF = NN_TILE * 16 * 2;          // one colour's A chunk, bytes
+  __shared__ __align__(128) unsigned char sA[2][3][ABUF];
+  __shared__ __align__(128) unsigned char sB[NCHUNK][NPAD * 16 * 2];
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t tmem_base;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Geom& g = A.g;
+  const int tpp = (g.Vh + NN_TILE - 1) / NN_TILE;
+  const int p = blockIdx.x / tpp;
+  const int cb = (blockIdx.x - p * tpp) * NN_TILE + tid;
+  const bool valid = cb < g.Vh;
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 64);
+    tmem_relinquish();
+  }
+  // weights -> BF16 B^T chunks (real form of the complex product)
+  for (int e = tid; e < NCHUNK * NPAD * 16; e += NN_TILE) {
+    const int c = e / (NPAD * 16), rem = e - c * NPAD * 16;
+    const int n = rem / 16, k = rem - n * 16;
+    const int j = k / (2 * CIN), i = (k / 2) % CIN, ri = k & 1;
+    const int o = n >> 1, ro = n & 1;
+    const int d = c * DPC + j;
+    float val = 0.f;
+    if (d < NN_NDIR && o < COUT) {
+      const float wr = A.w[((d * COUT + o) * CIN + i) * 2];
+      const float wi = A.w[((d * COUT + o) * CIN + i) * 2 + 1];
+      // Y.re = Xr Wr - Xi Wi ; Y.im = Xr Wi + Xi Wr
+      val = ro == 0 ? (ri == 0 ? wr : -wi) : (ri == 0 ? wi : wr);
+    }
+    *(__nv_bfloat16*)(sB[c] + kmajor_offset(n, k, 16)) = __float2bfloat16_rn(val);
+  }
+  NnNeighbours nbs;
+  if (valid) nn_neighbours(nbs, cb, p, g);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t idesc = make_idesc_bf16(NN_TILE, NPAD);
+  bool ok = true;
+
+  for (int c = 0; c < NCHUNK; c++) {
+    const int buf = c & 1;
+    if (c >= 2) ok = mbar_wait_bounded(&bar[buf], ((c - 2) >> 1) & 1, NN_SPIN_LIMIT) && ok;
+#pragma unroll
+    for (int j = 0; j < DPC; j++) {
+      const int d = c * DPC + j;
+      cx<float> t[CIN * 3];
+      if (valid && d < NN_NDIR) {
+        nn_transport<CIN>(t, A, nbs, d, p);
+      } else {
+#pragma unroll
+        for (int k = 0; k < CIN * 3; k++) t[k] = mk<float>(0.f, 0.f);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+#pragma unroll
+        for (int i = 0; i < CIN; i++) {
+          const int k = 2 * (j * CIN + i);
+          __nv_bfloat162 h = __floats2bfloat162_rn(t[i * 3 + a].r, t[i * 3 + a].i);
+          *(__nv_bfloat162*)(sA[buf][a] + kmajor_offset(tid, k, 16)) = h;
+        }
+      }
+    }
+    fence_smem_to_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint64_t bd = make_smem_desc(smem_u32(sB[c]), 128, 256);
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const uint64_t ad = make_smem_desc(smem_u32(sA[buf][a]), 128, 256);
+        tc_mma_bf16(tbase + (uint32_t)(a * NPAD), ad, bd, idesc, c > 0 ? 1u : 0u);
+      }
+      tc_commit(&bar[buf]);
+    }
+  }
+  // the last commit covers every MMA issued before it
+  {
+    const int c = NCHUNK - 1;
+    ok = mbar_wait_bounded(&bar[c & 1], (c >> 1) & 1, NN_SPIN_LIMIT) && ok;
+  }
+  // tcgen05.ld is warp-collective: decide once for the whole CTA
+  ok = __syncthreads_and(ok) != 0;
+  tc_fence_after();
+  if (!ok) {
+    if (tid == 0) atomicExch(A.err, 1);
+  } else {
+    cx<float> y[COUT * 3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * NPAD), v);
+#pragma unroll
+      for (int o = 0; o < COUT; o++) y[o * 3 + a] = mk<float>(v[2 * o], v[2 * o + 1]);
+    }
+    if (valid) nn_store<COUT>(A.out + p * A.out_half, cb, g.Vh_pad, y);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 64);
+}
+
+}  // namespace wd

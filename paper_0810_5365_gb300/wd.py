@@ -39,8 +39,12 @@ EXPORTS = [
     "wd_convert_spinor", "wd_dslash", "wd_dslash_dag", "wd_dslash_ex", "wd_mhat", "wd_norm2",
     "wd_cdot", "wd_axpby", "wd_solve_params_default", "wd_solve", "wd_solve_ex",
     "wd_dslash_ex_noalloc", "wd_dslash_mrhs", "wd_solve_batch", "wd_gauge_fix_temporal",
-    "wd_rotate_spinor", "wd_tc_gemm_bf16",
+    "wd_rotate_spinor", "wd_tc_gemm_bf16", "wd_nn_train_params_default", "wd_nn_init",
+    "wd_nn_apply", "wd_nn_train", "wd_solve_fgcr", "wd_nn_layer", "wd_gaussian_spinor",
+    "wd_nn_wgrad",
 ]
+
+WD_NN_PARAMS = 2304
 
 
 class WdError(RuntimeError):
@@ -62,6 +66,19 @@ class wd_solve_params(C.Structure):
 class wd_batch_problem(C.Structure):
     _fields_ = [("dims", C.c_int * 4), ("kappa", C.c_double), ("nrhs", C.c_int),
                 ("gauge", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p)]
+
+
+class wd_nn_train_params(C.Structure):
+    _fields_ = [("samples", C.c_int), ("batch", C.c_int), ("epochs", C.c_int),
+                ("lr", C.c_float), ("seed", C.c_ulonglong), ("init", C.c_int)]
+
+
+class wd_nn_train_info(C.Structure):
+    _fields_ = [("steps", C.c_int), ("loss_first", C.c_double), ("loss_last", C.c_double),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class wd_solve_info(C.Structure):
@@ -111,6 +128,16 @@ def lib():
         "wd_mhat": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_int, i4, C.c_int, C.c_int]),
         "wd_gauge_fix_temporal": (C.c_int, [dp, dp, dp, i4]),
         "wd_tc_gemm_bf16": (C.c_int, [dp, vp, vp, C.c_int, C.c_int, C.c_int]),
+        "wd_nn_train_params_default": (None, [C.POINTER(wd_nn_train_params)]),
+        "wd_nn_init": (C.c_int, [dp, C.c_double]),
+        "wd_nn_layer": (C.c_int, [vp, vp, dp, C.c_int, C.c_int, vp, i4]),
+        "wd_nn_wgrad": (C.c_int, [dp, vp, vp, C.c_int, C.c_int, vp, i4]),
+        "wd_gaussian_spinor": (C.c_int, [vp, C.c_ulonglong, C.c_ulonglong, C.c_ulonglong, i4]),
+        "wd_nn_apply": (C.c_int, [vp, vp, dp, vp, i4]),
+        "wd_nn_train": (C.c_int, [dp, dp, C.c_double, i4, C.POINTER(wd_nn_train_params),
+                                  C.POINTER(wd_nn_train_info)]),
+        "wd_solve_fgcr": (C.c_int, [dp, dp, dp, C.c_double, i4, dp, C.c_int,
+                                    C.POINTER(wd_solve_params), C.POINTER(wd_solve_info)]),
         "wd_rotate_spinor": (C.c_int, [dp, dp, dp, i4, C.c_int]),
         "wd_dslash_mrhs": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
                                      C.c_int, dp, i4, C.c_int, C.c_int]),
@@ -267,6 +294,62 @@ def wd_solve_batch(problems, params=None, check=True):
 
 def wd_tc_gemm_bf16(D, A, B, M, K, N):
     _ck(lib().wd_tc_gemm_bf16(_p(D), _p(A), _p(B), int(M), int(K), int(N)), "wd_tc_gemm_bf16")
+
+
+def wd_nn_train_params_default():
+    p = wd_nn_train_params()
+    lib().wd_nn_train_params_default(C.byref(p))
+    return p
+
+
+def wd_nn_layer(out, inp, weights, cin, cout, gauge, dims):
+    _ck(lib().wd_nn_layer(_p(out), _p(inp), _p(weights), int(cin), int(cout), _p(gauge), _d(dims)),
+        "wd_nn_layer")
+
+
+def wd_nn_wgrad(grad, inp, delta, cin, cout, gauge, dims):
+    _ck(lib().wd_nn_wgrad(_p(grad), _p(inp), _p(delta), int(cin), int(cout), _p(gauge), _d(dims)),
+        "wd_nn_wgrad")
+
+
+def wd_gaussian_spinor(out, seed, stream, first, dims):
+    _ck(lib().wd_gaussian_spinor(_p(out), int(seed), int(stream), int(first), _d(dims)),
+        "wd_gaussian_spinor")
+
+
+def nn_field_bytes(dims, channels):
+    """Bytes of a packed FP32 full field with `channels` channels per colour."""
+    vh = int(dims[0]) * int(dims[1]) * int(dims[2]) * int(dims[3]) // 2
+    vh_pad = (vh + 31) // 32 * 32
+    return 2 * ((vh_pad * channels * 24 + 255) // 256 * 256)
+
+
+def wd_nn_init(weights, kappa):
+    _ck(lib().wd_nn_init(_p(weights), float(kappa)), "wd_nn_init")
+
+
+def wd_nn_apply(out, inp, weights, gauge, dims):
+    _ck(lib().wd_nn_apply(_p(out), _p(inp), _p(weights), _p(gauge), _d(dims)), "wd_nn_apply")
+
+
+def wd_nn_train(weights, gauge, kappa, dims, params=None):
+    p = params if params is not None else wd_nn_train_params_default()
+    info = wd_nn_train_info()
+    _ck(lib().wd_nn_train(_p(weights), _p(gauge), float(kappa), _d(dims), C.byref(p),
+                          C.byref(info)), "wd_nn_train")
+    return info.as_dict()
+
+
+def wd_solve_fgcr(x, b, gauge, kappa, dims, weights=None, m=10, params=None, check=True):
+    info = wd_solve_info()
+    p = params if params is not None else wd_solve_params_default()
+    rc = lib().wd_solve_fgcr(_p(x), _p(b), _p(gauge), float(kappa), _d(dims), _p(weights), int(m),
+                             C.byref(p), C.byref(info))
+    out = info.as_dict()
+    out["status"] = rc
+    if check:
+        _ck(rc, "wd_solve_fgcr")
+    return out
 
 
 def wd_gauge_fix_temporal(U_out, omega_out, U_in, dims):
