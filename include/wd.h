@@ -253,7 +253,8 @@ int wd_cdot(double *result, const void *x, const void *y, const int dims[4],
             int parity, int prec);
 
 /* y = a x + b y (real a, b), elementwise in the storage precision's
- * arithmetic (FP32 for WD_F16). */
+ * arithmetic (FP32 for WD_F16).  With b == 0, y is output only and is not
+ * read (BLAS convention), so it may be uninitialised. */
 int wd_axpby(double a, const void *x, double b, void *y, const int dims[4],
              int parity, int prec);
 

@@ -29,7 +29,9 @@ cudaError_t launch_mrhs_f16(const MrhsBatch& bt, int recon, bool dagger, const i
 
 static cudaError_t launch_mrhs(int prec, const MrhsBatch& bt, int recon, bool dagger,
                                const int* active, RedScratch rs, double* norm_out, cudaStream_t st) {
-  int grid = bt.ntiles < num_sms() * 4 ? bt.ntiles : num_sms() * 4;
+  // one CTA per 32-site sub-tile (4 per tile), grid-stride beyond ~16 per SM
+  const int nsub = bt.ntiles * (MRHS_BS / MRHS_SUB);
+  int grid = nsub < num_sms() * 16 ? nsub : num_sms() * 16;
   if (grid < 1) grid = 1;
   switch (prec) {
     case WD_F64: return launch_mrhs_f64(bt, recon, dagger, active, rs, norm_out, grid, st);
@@ -94,7 +96,7 @@ __device__ __forceinline__ void batch_finalize(const BlasBatch& bt, const int* a
 
 // r -= alpha q (f0 = r, f1 = q); rr = ||r||^2 ; alpha = gk / qq per rhs
 template <int P>
-__global__ void __launch_bounds__(MRHS_BS) batch_update_r(const BlasBatch bt, const int* active,
+__global__ void __launch_bounds__(MRHS_BS) batch_update_r(const __grid_constant__ BlasBatch bt, const int* active,
                                                           const double* gk, const double* qq,
                                                           RedScratch rs, double* rr) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(MRHS_BS) batch_update_r(const BlasBatch bt, co
 
 // x += alpha p ; p = s + beta p   (f0 = x [PX], f1 = p, f2 = s)
 template <int P, int PX>
-__global__ void __launch_bounds__(MRHS_BS) batch_update_xp(const BlasBatch bt, const int* active,
+__global__ void __launch_bounds__(MRHS_BS) batch_update_xp(const __grid_constant__ BlasBatch bt, const int* active,
                                                            const double* gk, const double* gk1,
                                                            const double* qq) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(MRHS_BS) batch_update_xp(const BlasBatch bt, c
 
 // x64 += xs ; xs = 0   (f0 = x64 even half, f1 = xs [PX])
 template <int PX>
-__global__ void __launch_bounds__(MRHS_BS) batch_ru_accumulate(const BlasBatch bt,
+__global__ void __launch_bounds__(MRHS_BS) batch_ru_accumulate(const __grid_constant__ BlasBatch bt,
                                                                const int* active) {
   using RX = typename std::conditional<PX == WD_F64, double, float>::type;
   WD_TILE_LOOP
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(MRHS_BS) batch_ru_accumulate(const BlasBatch b
 
 // dst = src (f0 = dst [PD], f1 = src [PS])
 template <int PD, int PS>
-__global__ void __launch_bounds__(MRHS_BS) batch_convert(const BlasBatch bt, const int* active) {
+__global__ void __launch_bounds__(MRHS_BS) batch_convert(const __grid_constant__ BlasBatch bt, const int* active) {
   using R = typename std::conditional<PD == WD_F64 || PS == WD_F64, double, float>::type;
   WD_TILE_LOOP
   if (!valid) continue;
@@ -532,7 +534,7 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
     c.sc.r64 = s + 4 * nr; c.sc.bnorm2 = s + 5 * nr; c.sc.res_e = s + 6 * nr;
     c.sc.res_o = s + 7 * nr;
     WD_BCK(cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking));
-    WD_BCK(ensure_scratch((size_t)tile0 * MRHS_MAX + 4096));
+    WD_BCK(ensure_scratch((size_t)tile0 * (MRHS_BS / MRHS_SUB) * MRHS_MAX + 4096));
   }
   for (int g = 0; g < nr; g++) c.active_h[g] = 1;
   WD_BCK(cudaMemcpyAsync(c.active, c.active_h, nr * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -787,7 +789,7 @@ cudaError_t dslash_mrhs(void* out, const void* in, const void* gauge, int parity
   m.x = x;
   m.s_out = m.s_in = m.s_x = h;
   if (norms) {
-    cudaError_t e = ensure_scratch((size_t)bt.ntiles * MRHS_MAX + 1024);
+    cudaError_t e = ensure_scratch((size_t)bt.ntiles * (MRHS_BS / MRHS_SUB) * MRHS_MAX + 1024);
     if (e != cudaSuccess) return e;
   }
   return launch_mrhs(prec, bt, recon, dagger != 0, nullptr, scratch(), norms, st);

@@ -311,11 +311,18 @@ __global__ void axpby_kernel(double a, const char* __restrict__ x, double b, cha
     int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
     cx<R> u[12], v[12];
     load_spinor_rw<P, R>(u, x + h * hb, cb, g.Vh_pad);
-    load_spinor_rw<P, R>(v, y + h * hb, cb, g.Vh_pad);
+    if (b != 0.0) {
+      load_spinor_rw<P, R>(v, y + h * hb, cb, g.Vh_pad);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      v[k].r = (R)a * u[k].r + (R)b * v[k].r;
-      v[k].i = (R)a * u[k].i + (R)b * v[k].i;
+      for (int k = 0; k < 12; k++) {
+        v[k].r = (R)a * u[k].r + (R)b * v[k].r;
+        v[k].i = (R)a * u[k].i + (R)b * v[k].i;
+      }
+    } else {
+      // b = 0: y is output only and never read (BLAS convention), so an
+      // uninitialised y cannot leak NaN or Inf through 0 * y
+#pragma unroll
+      for (int k = 0; k < 12; k++) v[k] = mk<R>((R)a * u[k].r, (R)a * u[k].i);
     }
     store_spinor<P, R>(y + h * hb, cb, g.Vh_pad, v);
   }

@@ -388,9 +388,12 @@ struct RedScratch {
   unsigned* counter;   // zero between kernels; reset by the last block
 };
 
+// Sum over the BS threads of a block (1-, 2- or 3-dimensional; warps are
+// taken in linear thread order).  The total is in every thread of warp 0.
 template <int N, int BS>
 __device__ __forceinline__ void block_sum(double (&v)[N], double* smem /* N * BS/32 */) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int j = 0; j < N; j++) {
     double t = v[j];

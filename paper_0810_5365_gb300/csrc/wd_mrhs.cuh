@@ -3,11 +3,10 @@
 // A batch is a list of problems (lattice geometry, gauge field, nrhs fields);
 // the problems may have different lattice sizes.  Their sites of one parity
 // are cut into tiles of MRHS_BS checkerboard sites and all tiles of all
-// problems form one launch.  A CTA takes a tile, stages the eight links of
-// each of its sites in shared memory once (12-real FP32 / FP16 formats), and
-// then applies the hopping term to every active right-hand side of the
-// problem, so each link crosses HBM once per site instead of once per site
-// and right-hand side.  Per right-hand side the epilogue is the one of the
+// problems form one launch.  The four warps of a CTA apply the hopping term to
+// different right-hand sides of the same 32 sites at the same time, so each
+// link crosses HBM once per site instead of once per site and right-hand side
+// (the repeats are served by L1/L2).  Per right-hand side the epilogue is the one of the
 // single-field kernel (out = a H in + bx x + cy y), optionally with ||out||^2
 // reduced deterministically per right-hand side.
 #pragma once
@@ -44,59 +43,6 @@ struct MrhsBatch {
   MrhsProblem p[MRHS_MAX_PROBLEMS];
 };
 
-// link slots staged per thread and hop (128-bit vectors)
-template <int P, int RC>
-struct MrhsStage {
-  static constexpr bool on = (P == WD_F32 || P == WD_F16) && RC == 12;
-  static constexpr int vec16 = P == WD_F32 ? 3 : 2;  // F16: int4 + int2 (padded to 16 B)
-  static constexpr size_t bytes_per_thread = on ? 8 * vec16 * 16 : 0;
-};
-
-template <int P, int RC>
-__device__ __forceinline__ void stage_link(int4* sm, int hop, int tid, const void* gauge,
-                                           int region, int lcb, int VP) {
-  if constexpr (P == WD_F32) {
-    const int4* p = (const int4*)gauge + (size_t)region * VP * 3;
-#pragma unroll
-    for (int k = 0; k < 3; k++) sm[(hop * 3 + k) * MRHS_BS + tid] = __ldg(p + sbi(lcb, k, 3));
-  } else {
-    const int4* pa = (const int4*)gauge + (size_t)region * VP;
-    const int2* pb = (const int2*)((const char*)gauge + (size_t)8 * VP * 16) + (size_t)region * VP;
-    int2 b = __ldg(pb + lcb);
-    sm[(hop * 2 + 0) * MRHS_BS + tid] = __ldg(pa + lcb);
-    sm[(hop * 2 + 1) * MRHS_BS + tid] = make_int4(b.x, b.y, 0, 0);
-  }
-}
-
-template <int P, typename R>
-__device__ __forceinline__ void unstage_link(cx<R> (&u)[9], const int4* sm, int hop, int tid) {
-  if constexpr (P == WD_F32) {
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      int4 w = sm[(hop * 3 + k) * MRHS_BS + tid];
-      float4 v = *reinterpret_cast<const float4*>(&w);
-      u[2 * k] = mk<R>(v.x, v.y);
-      u[2 * k + 1] = mk<R>(v.z, v.w);
-    }
-  } else {
-    int4 a = sm[(hop * 2 + 0) * MRHS_BS + tid];
-    int4 b = sm[(hop * 2 + 1) * MRHS_BS + tid];
-    const __half2* ha = reinterpret_cast<const __half2*>(&a);
-    const __half2* hb = reinterpret_cast<const __half2*>(&b);
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      float2 f = __half22float2(ha[j]);
-      u[j] = mk<R>(f.x, f.y);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; j++) {
-      float2 f = __half22float2(hb[j]);
-      u[4 + j] = mk<R>(f.x, f.y);
-    }
-  }
-  reconstruct_row2(u);
-}
-
 // one hop with a link already in registers
 template <int P, int MU, int S, bool FWD, typename R>
 __device__ __forceinline__ void hop_with_link(cx<R> (&acc)[12], const void* __restrict__ in, int nb,
@@ -129,131 +75,104 @@ __device__ __forceinline__ void hop_with_link(cx<R> (&acc)[12], const void* __re
   }
 }
 
-template <int P, int RC, int MU, int S, bool FWD, typename R>
-__device__ __forceinline__ void hop_mrhs(cx<R> (&acc)[12], const void* __restrict__ in, int nb,
-                                         const int4* sm, int hop, int tid, const void* gauge,
-                                         int region, int lcb, bool flip, int VP) {
-  cx<R> u[9];
-  if constexpr (MrhsStage<P, RC>::on)
-    unstage_link<P, R>(u, sm, hop, tid);
-  else
-    load_link<P, RC, R>(u, gauge, region, lcb, VP);
-  hop_with_link<P, MU, S, FWD, R>(acc, in, nb, u, flip, VP);
-}
+// One CTA = 32 sites x 4 right-hand-side lanes (one warp per right-hand
+// side).  Block b covers sub-tile b / G and right-hand sides 4 (b % G) .. +3,
+// G = ceil(max nrhs / 4): the G blocks of a sub-tile are adjacent in launch
+// order, run together, and read the same links, which L1/L2 then return once
+// per site for all right-hand sides.  Each thread computes one right-hand
+// side of one site, so the kernel keeps the registers (and occupancy) of the
+// single-field kernel.
+constexpr int MRHS_LANES = 4;   // right-hand-side lanes (warps) per CTA
+constexpr int MRHS_SUB = 32;    // sites per CTA
 
 template <int P, int RC, bool DAG, bool NORM>
-__global__ void __launch_bounds__(MRHS_BS) mrhs_dslash_kernel(const MrhsBatch bt,
-                                                              const int* __restrict__ active,
-                                                              RedScratch rs, double* norm_out) {
+__global__ void __launch_bounds__(MRHS_SUB* MRHS_LANES, DslashMinBlocks<P, NORM>::value)
+    mrhs_dslash_kernel(const __grid_constant__ MrhsBatch bt, int groups,
+                       const int* __restrict__ active, RedScratch rs, double* norm_out) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
-  extern __shared__ int4 smem4[];
-  __shared__ double red[MRHS_BS / 32];
-  const int tid = threadIdx.x;
+  __shared__ double red[MRHS_LANES];
+  const int tx = threadIdx.x, ry = threadIdx.y;
   constexpr int SF = DAG ? -1 : 1;
   constexpr int SB_ = -SF;
-
-  const int nprob = bt.nprob, ntiles = bt.ntiles;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int j = 0;
-    while (j + 1 < nprob && tile >= bt.p[j + 1].tile0) j++;
-    const MrhsProblem& pr = bt.p[j];
-    const Geom g = pr.g;
-    const int cb = (tile - pr.tile0) * MRHS_BS + tid;
-    const bool valid = cb < g.Vh;
-    const int p = pr.parity, q = 1 - p, VP = g.Vh_pad;
-    int f[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
-    bool fflip = false, bflip = false;
-    if (valid) {
-      int x0, x1, x2, x3;
-      cb_coords(cb, p, g, x0, x1, x2, x3);
-      const int row = cb - (x0 >> 1);
-      f[0] = row + ((x0 + 1 == g.L[0] ? 0 : x0 + 1) >> 1);
-      b[0] = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
-      f[1] = x1 == g.L[1] - 1 ? cb - (g.L[1] - 1) * g.S1 : cb + g.S1;
-      b[1] = x1 == 0 ? cb + (g.L[1] - 1) * g.S1 : cb - g.S1;
-      f[2] = x2 == g.L[2] - 1 ? cb - (g.L[2] - 1) * g.S2 : cb + g.S2;
-      b[2] = x2 == 0 ? cb + (g.L[2] - 1) * g.S2 : cb - g.S2;
-      f[3] = x3 == g.L[3] - 1 ? cb - (g.L[3] - 1) * g.S3 : cb + g.S3;
-      b[3] = x3 == 0 ? cb + (g.L[3] - 1) * g.S3 : cb - g.S3;
-      fflip = x3 == g.L[3] - 1;
-      bflip = x3 == 0;
-    }
-    __syncthreads();  // the previous tile's staged links are no longer read
-    if constexpr (MrhsStage<P, RC>::on) {
-      if (valid) {
+  constexpr int SUBS = MRHS_BS / MRHS_SUB;  // sub-tiles per tile
+  const int nprob = bt.nprob;
+  const int sub = blockIdx.x / groups;
+  const int r = (blockIdx.x - sub * groups) * MRHS_LANES + ry;
+  const int tile = sub / SUBS, q = sub - tile * SUBS;
+  int j = 0;
+  while (j + 1 < nprob && tile >= bt.p[j + 1].tile0) j++;
+  const MrhsProblem& pr = bt.p[j];
+  const int cb = (tile - pr.tile0) * MRHS_BS + q * MRHS_SUB + tx;
+  const bool act = r < pr.nrhs && (active == nullptr || active[pr.rhs0 + r] != 0);
+  double nrm = 0.0;
+  if (act && cb < pr.g.Vh) {
+    const Geom& g = pr.g;
+    const int p = pr.parity, qq = 1 - p, VP = g.Vh_pad;
+    int x0, x1, x2, x3;
+    cb_coords(cb, p, g, x0, x1, x2, x3);
+    const int row = cb - (x0 >> 1);
+    const int f0 = row + ((x0 + 1 == g.L[0] ? 0 : x0 + 1) >> 1);
+    const int b0 = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
+    const int f1 = x1 == g.L[1] - 1 ? cb - (g.L[1] - 1) * g.S1 : cb + g.S1;
+    const int b1 = x1 == 0 ? cb + (g.L[1] - 1) * g.S1 : cb - g.S1;
+    const int f2 = x2 == g.L[2] - 1 ? cb - (g.L[2] - 1) * g.S2 : cb + g.S2;
+    const int b2 = x2 == 0 ? cb + (g.L[2] - 1) * g.S2 : cb - g.S2;
+    const int f3 = x3 == g.L[3] - 1 ? cb - (g.L[3] - 1) * g.S3 : cb + g.S3;
+    const int b3 = x3 == 0 ? cb + (g.L[3] - 1) * g.S3 : cb - g.S3;
+    const bool fflip = x3 == g.L[3] - 1;
+    const bool bflip = x3 == 0;
+    const void* in = (const char*)pr.in + (size_t)r * pr.s_in;
+    const void* ga = pr.gauge;
+    cx<R> acc[12];
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-          stage_link<P, RC>(smem4, 2 * mu, tid, pr.gauge, 2 * mu + p, cb, VP);
-          stage_link<P, RC>(smem4, 2 * mu + 1, tid, pr.gauge, 2 * mu + q, b[mu], VP);
-        }
+    for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
+    hop<P, RC, 0, SF, true>(acc, in, ga, f0, 0 + p, cb, false, VP);
+    hop<P, RC, 0, SB_, false>(acc, in, ga, b0, 0 + qq, b0, false, VP);
+    hop<P, RC, 1, SF, true>(acc, in, ga, f1, 2 + p, cb, false, VP);
+    hop<P, RC, 1, SB_, false>(acc, in, ga, b1, 2 + qq, b1, false, VP);
+    hop<P, RC, 2, SF, true>(acc, in, ga, f2, 4 + p, cb, false, VP);
+    hop<P, RC, 2, SB_, false>(acc, in, ga, b2, 4 + qq, b2, false, VP);
+    hop<P, RC, 3, SF, true>(acc, in, ga, f3, 6 + p, cb, fflip, VP);
+    hop<P, RC, 3, SB_, false>(acc, in, ga, b3, 6 + qq, b3, bflip, VP);
+    const R ca = (R)pr.a;
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
+    if (pr.x) {
+      cx<R> v[12];
+      load_spinor_rw<P, R>(v, (const char*)pr.x + (size_t)r * pr.s_x, cb, VP);
+      const R cbx = (R)pr.bx;
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        acc[k].r = fma(cbx, v[k].r, acc[k].r);
+        acc[k].i = fma(cbx, v[k].i, acc[k].i);
       }
     }
-    // each thread reads back only the slots it wrote: no barrier needed here
-
-    for (int r = 0; r < pr.nrhs; r++) {
-      const bool act = active == nullptr || active[pr.rhs0 + r] != 0;
-      if (!act) continue;  // uniform over the CTA
-      double nrm = 0.0;
-      if (valid) {
-        const void* in = (const char*)pr.in + (size_t)r * pr.s_in;
-        cx<R> acc[12];
+    if (pr.y) {
+      cx<R> v[12];
+      load_spinor_rw<P, R>(v, (const char*)pr.y + (size_t)r * pr.s_y, cb, VP);
+      const R ccy = (R)pr.cy;
 #pragma unroll
-        for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
-        const void* ga = pr.gauge;
-        hop_mrhs<P, RC, 0, SF, true>(acc, in, f[0], smem4, 0, tid, ga, 0 + p, cb, false, VP);
-        hop_mrhs<P, RC, 0, SB_, false>(acc, in, b[0], smem4, 1, tid, ga, 0 + q, b[0], false, VP);
-        hop_mrhs<P, RC, 1, SF, true>(acc, in, f[1], smem4, 2, tid, ga, 2 + p, cb, false, VP);
-        hop_mrhs<P, RC, 1, SB_, false>(acc, in, b[1], smem4, 3, tid, ga, 2 + q, b[1], false, VP);
-        hop_mrhs<P, RC, 2, SF, true>(acc, in, f[2], smem4, 4, tid, ga, 4 + p, cb, false, VP);
-        hop_mrhs<P, RC, 2, SB_, false>(acc, in, b[2], smem4, 5, tid, ga, 4 + q, b[2], false, VP);
-        hop_mrhs<P, RC, 3, SF, true>(acc, in, f[3], smem4, 6, tid, ga, 6 + p, cb, fflip, VP);
-        hop_mrhs<P, RC, 3, SB_, false>(acc, in, b[3], smem4, 7, tid, ga, 6 + q, b[3], bflip, VP);
-        const R ca = (R)pr.a;
-#pragma unroll
-        for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
-        if (pr.x) {
-          cx<R> v[12];
-          load_spinor_rw<P, R>(v, (const char*)pr.x + (size_t)r * pr.s_x, cb, VP);
-          const R cbx = (R)pr.bx;
-#pragma unroll
-          for (int k = 0; k < 12; k++) {
-            acc[k].r = fma(cbx, v[k].r, acc[k].r);
-            acc[k].i = fma(cbx, v[k].i, acc[k].i);
-          }
-        }
-        if (pr.y) {
-          cx<R> v[12];
-          load_spinor_rw<P, R>(v, (const char*)pr.y + (size_t)r * pr.s_y, cb, VP);
-          const R ccy = (R)pr.cy;
-#pragma unroll
-          for (int k = 0; k < 12; k++) {
-            acc[k].r = fma(ccy, v[k].r, acc[k].r);
-            acc[k].i = fma(ccy, v[k].i, acc[k].i);
-          }
-        }
-        void* out = (char*)pr.out + (size_t)r * pr.s_out;
-        store_spinor<P, R>(out, cb, VP, acc);
-        if constexpr (NORM) {
-          if constexpr (P == WD_F16) {
-            cx<R> v[12];
-            load_spinor_rw<P, R>(v, out, cb, VP);
-            nrm = site_norm2(v);
-          } else {
-            nrm = site_norm2(acc);
-          }
-        }
+      for (int k = 0; k < 12; k++) {
+        acc[k].r = fma(ccy, v[k].r, acc[k].r);
+        acc[k].i = fma(ccy, v[k].i, acc[k].i);
       }
-      if constexpr (NORM) {
-        double v[1] = {nrm};
-        block_sum<1, MRHS_BS>(v, red);
-        if (tid == 0) rs.partials[(size_t)tile * MRHS_MAX + r] = v[0];
-      }
+    }
+    void* out = (char*)pr.out + (size_t)r * pr.s_out;
+    store_spinor<P, R>(out, cb, VP, acc);
+    if constexpr (NORM) {
+      if constexpr (P == WD_F16) load_spinor_rw<P, R>(acc, out, cb, VP);
+      nrm = site_norm2(acc);
     }
   }
-
   if constexpr (NORM) {
-    // the last CTA to finish sums each right-hand side's tiles in tile order
+    // one warp = one right-hand side of these 32 sites
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if (tx == 0 && act) rs.partials[(size_t)sub * MRHS_MAX + r] = nrm;
+
+    // the last CTA to finish sums each right-hand side's sub-tiles in order
     __shared__ bool last;
+    const int tid = ry * MRHS_SUB + tx;
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -264,14 +183,15 @@ __global__ void __launch_bounds__(MRHS_BS) mrhs_dslash_kernel(const MrhsBatch bt
     if (!last) return;
     __threadfence();
     for (int jj = 0; jj < nprob; jj++) {
-      const MrhsProblem& pr = bt.p[jj];
-      for (int r = 0; r < pr.nrhs; r++) {
-        if (active != nullptr && active[pr.rhs0 + r] == 0) continue;
+      const MrhsProblem& pj = bt.p[jj];
+      for (int rr = 0; rr < pj.nrhs; rr++) {
+        if (active != nullptr && active[pj.rhs0 + rr] == 0) continue;
         double v[1] = {0.0};
-        for (int t = tid; t < pr.ntiles; t += MRHS_BS)
-          v[0] += __ldcg(rs.partials + (size_t)(pr.tile0 + t) * MRHS_MAX + r);
-        block_sum<1, MRHS_BS>(v, red);
-        if (tid == 0) norm_out[pr.rhs0 + r] = v[0];
+        const int s0 = pj.tile0 * SUBS, ns = pj.ntiles * SUBS;
+        for (int t = tid; t < ns; t += MRHS_SUB * MRHS_LANES)
+          v[0] += __ldcg(rs.partials + (size_t)(s0 + t) * MRHS_MAX + rr);
+        block_sum<1, MRHS_SUB * MRHS_LANES>(v, red);
+        if (tid == 0) norm_out[pj.rhs0 + rr] = v[0];
       }
     }
     if (tid == 0) *rs.counter = 0u;
@@ -281,15 +201,13 @@ __global__ void __launch_bounds__(MRHS_BS) mrhs_dslash_kernel(const MrhsBatch bt
 template <int P, int RC, bool DG, bool NM>
 cudaError_t launch_mrhs_one(const MrhsBatch& bt, const int* active, RedScratch rs,
                             double* norm_out, int grid, cudaStream_t st) {
-  constexpr size_t smem = (size_t)MRHS_BS * MrhsStage<P, RC>::bytes_per_thread;
-  static bool attr = false;  // raise the dynamic shared-memory limit once
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mrhs_dslash_kernel<P, RC, DG, NM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  mrhs_dslash_kernel<P, RC, DG, NM><<<grid, MRHS_BS, smem, st>>>(bt, active, rs, norm_out);
+  int maxr = 1;
+  for (int j = 0; j < bt.nprob; j++) maxr = bt.p[j].nrhs > maxr ? bt.p[j].nrhs : maxr;
+  const int groups = (maxr + MRHS_LANES - 1) / MRHS_LANES;
+  const long long nblk = (long long)bt.ntiles * (MRHS_BS / MRHS_SUB) * groups;
+  (void)grid;
+  mrhs_dslash_kernel<P, RC, DG, NM><<<(unsigned)nblk, dim3(MRHS_SUB, MRHS_LANES), 0, st>>>(
+      bt, groups, active, rs, norm_out);
   return cudaGetLastError();
 }
 

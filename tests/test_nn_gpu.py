@@ -108,7 +108,7 @@ def test_layer_within_bf16_bound(dims, cin, cout):
     bound = np.zeros_like(want.real)
     for d in range(9):
         t = np.abs(nn.transport(phi32, U32, dims, d, tr))
-        bound += np.einsum("oi,xia->xoa", np.abs(Wc), t)
+        bound += np.einsum("oi,xia->xoa", np.abs(Wc[d]), t)
     err = np.abs(got - want)
     assert np.all(err <= 2 * 2.0 ** -8 * np.sqrt(2) * bound + 1e-5)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 5e-3
