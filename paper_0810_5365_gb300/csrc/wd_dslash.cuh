@@ -234,6 +234,66 @@ __device__ __forceinline__ RawF16 fetch_f16(const void* __restrict__ in,
   return r;
 }
 
+#ifndef WD_F16_HMATH
+#define WD_F16_HMATH 1
+#endif
+
+// Packed half2 complex arithmetic for the FP16 link product.  With
+// hx = (-h.i, h.r) = i h:  u h = u.r h + u.i hx, and with hx = (h.i, -h.r) =
+// -i h:  conj(u) h = u.r h + u.i hx, so one routine serves U h and U^+ h.
+__device__ __forceinline__ __half2 h2_cmac(__half2 u, __half2 h, __half2 hx, __half2 w) {
+  w = __hfma2(__low2half2(u), h, w);
+  return __hfma2(__high2half2(u), hx, w);
+}
+
+// conj(a b - c d) on half2 (the SU(3) third row from the first two)
+__device__ __forceinline__ __half2 h2_conj_cross(__half2 a, __half2 b, __half2 c, __half2 d) {
+  const __half2 pm = __floats2half2_rn(-1.f, 1.f);
+  const __half2 bx = __hmul2(__lowhigh2highlow(b), pm);  // i b
+  const __half2 dx = __hmul2(__lowhigh2highlow(d), pm);  // i d
+  __half2 x = __hmul2(__low2half2(a), b);
+  x = __hfma2(__high2half2(a), bx, x);
+  x = __hfma2(__hneg2(__low2half2(c)), d, x);
+  x = __hfma2(__hneg2(__high2half2(c)), dx, x);
+  return __hmul2(x, __floats2half2_rn(1.f, -1.f));
+}
+
+// The transported half spinor t = U h (FWD) or U^+ h in half2 arithmetic:
+// the stored spinor is scaled to |v| <= 1 and |U_ij| <= 1, so every partial
+// sum stays below 6 in magnitude and each rounding is relative 2^-11, the
+// same order as the storage rounding of the FP16 format itself.
+template <bool FWD>
+__device__ __forceinline__ void transport_h2(const RawF16& r, const __half2 (&h)[6],
+                                             __half2 (&t)[6]) {
+  __half2 u[9];
+  const __half2* ha = reinterpret_cast<const __half2*>(&r.la);
+  const __half2* hb = reinterpret_cast<const __half2*>(&r.lb);
+#pragma unroll
+  for (int j = 0; j < 4; j++) u[j] = ha[j];
+  u[4] = hb[0];
+  u[5] = hb[1];
+  u[6] = h2_conj_cross(u[1], u[5], u[2], u[4]);
+  u[7] = h2_conj_cross(u[2], u[3], u[0], u[5]);
+  u[8] = h2_conj_cross(u[0], u[4], u[1], u[3]);
+  const __half2 sx = FWD ? __floats2half2_rn(-1.f, 1.f) : __floats2half2_rn(1.f, -1.f);
+  __half2 hx[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) hx[k] = __hmul2(__lowhigh2highlow(h[k]), sx);
+#pragma unroll
+  for (int hs = 0; hs < 2; hs++) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      __half2 w = __float2half2_rn(0.f);
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        const __half2 e = FWD ? u[c * 3 + d] : u[d * 3 + c];
+        w = h2_cmac(e, h[hs * 3 + d], hx[hs * 3 + d], w);
+      }
+      t[hs * 3 + c] = w;
+    }
+  }
+}
+
 template <int MU, int S, bool FWD>
 __device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& r, bool flip,
                                             bool unit = false) {
@@ -246,6 +306,26 @@ __device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& 
   }
   __half2 hh[6];
   project_h2<MU, S>(v, hh);
+#if WD_F16_HMATH
+  {
+    __half2 t2[6];
+    if (MU == 3 && unit) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) t2[k] = hh[k];
+    } else {
+      transport_h2<FWD>(r, hh, t2);
+    }
+    cx<float> t[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const float2 f = __half22float2(t2[k]);
+      t[k] = mk<float>(f.x, f.y);
+    }
+    const float sc = (MU == 3 && flip) ? -r.sc : r.sc;
+    expand_add<MU, S, false>(acc, t, sc);
+    return;
+  }
+#endif
   cx<float> h[6];
 #pragma unroll
   for (int k = 0; k < 6; k++) {

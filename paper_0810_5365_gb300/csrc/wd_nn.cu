@@ -26,6 +26,24 @@ constexpr int NN_PARAMS = nn_layer_offset(3);  // 2304 floats
 // layer launch
 // ---------------------------------------------------------------------------
 
+// persistent grid: as many CTAs as fit on the SMs at once (at most 8 per SM,
+// the 512 TMEM columns / 64 per CTA), never more than there are tiles
+template <int CIN, int COUT>
+static cudaError_t launch_layer(const NnLayerArgs& A, int ntiles, cudaStream_t st) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, nn_layer_kernel<CIN, COUT>, NN_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+  }
+  const int cap = num_sms() * per_sm;
+  const int grid = ntiles < cap ? ntiles : cap;
+  nn_layer_kernel<CIN, COUT><<<grid, NN_THREADS, 0, st>>>(A, ntiles);
+  return cudaGetLastError();
+}
+
 static cudaError_t nn_layer(int cin, int cout, const Geom& g, const void* gauge, const void* in,
                             void* out, const float* w, int* err, cudaStream_t st) {
   NnLayerArgs A;
@@ -37,13 +55,12 @@ static cudaError_t nn_layer(int cin, int cout, const Geom& g, const void* gauge,
   A.out_half = nn_half_bytes(g.Vh_pad, cout);
   A.w = w;
   A.err = err;
-  const int grid = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
-  if (cin == 4 && cout == 8) nn_layer_kernel<4, 8><<<grid, NN_TILE, 0, st>>>(A);
-  else if (cin == 8 && cout == 8) nn_layer_kernel<8, 8><<<grid, NN_TILE, 0, st>>>(A);
-  else if (cin == 8 && cout == 4) nn_layer_kernel<8, 4><<<grid, NN_TILE, 0, st>>>(A);
-  else if (cin == 4 && cout == 4) nn_layer_kernel<4, 4><<<grid, NN_TILE, 0, st>>>(A);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  const int ntiles = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  if (cin == 4 && cout == 8) return launch_layer<4, 8>(A, ntiles, st);
+  if (cin == 8 && cout == 8) return launch_layer<8, 8>(A, ntiles, st);
+  if (cin == 8 && cout == 4) return launch_layer<8, 4>(A, ntiles, st);
+  if (cin == 4 && cout == 4) return launch_layer<4, 4>(A, ntiles, st);
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------

@@ -142,8 +142,85 @@ __device__ __forceinline__ void nn_transport(cx<float> (&t)[C * 3], const NnLaye
   }
 }
 
+// Inference layer kernel.  Two threads per site, each transporting four input
+// channels of one direction per K = 16 chunk (CIN = 8: channels 4h..4h+3 of
+// the chunk's direction; CIN = 4: the whole site for direction 2c + h), so a
+// thread holds 12 complex activations instead of 24 and twice as many warps
+// hide the gather latency.  The CTA is persistent over 128-site tiles: the
+// TMEM accumulators and the BF16 weight tiles are set up once, and a chunk
+// counter carried across tiles drives the two A buffers' mbarrier phases.
+constexpr int NN_THREADS = 2 * NN_TILE;
+#ifndef WD_NN_MINB
+#define WD_NN_MINB 3   // CTAs per SM the register budget is sized for
+#endif
+
+// channels c0 .. c0+3 (12 complex, 6 groups) of site cb of a packed half
+template <int C>
+__device__ __forceinline__ void nn_load4(cx<float> (&v)[12], const char* half, int cb, int c0) {
+  constexpr int NG = 3 * C / 2;
+  const float4* p = (const float4*)half;
+  const int g0 = c0 * 3 / 2;
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    float4 q = __ldg(p + sbi(cb, g0 + k, NG));
+    v[2 * k] = mk<float>(q.x, q.y);
+    v[2 * k + 1] = mk<float>(q.z, q.w);
+  }
+}
+
+// neighbour checkerboard indices of the nine directions (index 0: the site)
+__device__ __forceinline__ void nn_nbr(int (&nb)[NN_NDIR], int& x3, int cb, int p, const Geom& g) {
+  int x0, x1, x2;
+  cb_coords(cb, p, g, x0, x1, x2, x3);
+  const int row = cb - (x0 >> 1);
+  nb[0] = cb;
+  nb[1] = row + ((x0 + 1 == g.L[0] ? 0 : x0 + 1) >> 1);
+  nb[2] = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
+  nb[3] = x1 == g.L[1] - 1 ? cb - (g.L[1] - 1) * g.S1 : cb + g.S1;
+  nb[4] = x1 == 0 ? cb + (g.L[1] - 1) * g.S1 : cb - g.S1;
+  nb[5] = x2 == g.L[2] - 1 ? cb - (g.L[2] - 1) * g.S2 : cb + g.S2;
+  nb[6] = x2 == 0 ? cb + (g.L[2] - 1) * g.S2 : cb - g.S2;
+  nb[7] = x3 == g.L[3] - 1 ? cb - (g.L[3] - 1) * g.S3 : cb + g.S3;
+  nb[8] = x3 == 0 ? cb + (g.L[3] - 1) * g.S3 : cb - g.S3;
+}
+
+// T_d of four input channels at this site
+template <int C>
+__device__ __forceinline__ void nn_transport4(cx<float> (&t)[12], const NnLayerArgs& A, int d,
+                                              int p, int cb, int n, int x3, int c0) {
+  cx<float> v[12];
+  nn_load4<C>(v, A.in + (d == 0 ? p : 1 - p) * A.in_half, n, c0);
+  if (d == 0) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) t[k] = v[k];
+    return;
+  }
+  const int mu = (d - 1) >> 1;
+  const bool fwd = (d & 1) != 0;
+  cx<float> u[9];
+  load_link<WD_F32, 12, float>(u, A.gauge, 2 * mu + (fwd ? p : 1 - p), fwd ? cb : n,
+                               A.g.Vh_pad);
+  const bool flip = mu == 3 && (fwd ? x3 == A.g.L[3] - 1 : x3 == 0);
+  const float sg = flip ? -1.f : 1.f;
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<float> w = mk<float>(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        if (fwd)
+          w = cmadd(u[a * 3 + b], v[c * 3 + b], w);
+        else
+          w = cjmadd(u[b * 3 + a], v[c * 3 + b], w);
+      }
+      t[c * 3 + a] = sg * w;
+    }
+  }
+}
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(NN_TILE) nn_layer_kernel(const NnLayerArgs A) {
+__global__ void __launch_bounds__(NN_THREADS, WD_NN_MINB) nn_layer_kernel(const NnLayerArgs A, int ntiles) {
   static_assert(CIN == 4 || CIN == 8, "4 or 8 input channels");
   static_assert(COUT == 4 || COUT == 8, "4 or 8 output channels");
   constexpr int DPC = 16 / (2 * CIN);                  // directions per K = 16 chunk
@@ -155,12 +232,11 @@ __global__ void __launch_bounds__(NN_TILE) nn_layer_kernel(const NnLayerArgs A) 
   __shared__ uint64_t bar[2];
   __shared__ uint32_t tmem_base;
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int s = tid & (NN_TILE - 1);   // site of the tile = A row = TMEM lane
+  const int hh = tid >> 7;             // which half of the chunk's K columns
   const Geom& g = A.g;
   const int tpp = (g.Vh + NN_TILE - 1) / NN_TILE;
-  const int p = blockIdx.x / tpp;
-  const int cb = (blockIdx.x - p * tpp) * NN_TILE + tid;
-  const bool valid = cb < g.Vh;
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -171,8 +247,8 @@ __global__ void __launch_bounds__(NN_TILE) nn_layer_kernel(const NnLayerArgs A) 
     tmem_alloc(&tmem_base, 64);
     tmem_relinquish();
   }
-  // weights -> BF16 B^T chunks (real form of the complex product)
-  for (int e = tid; e < NCHUNK * NPAD * 16; e += NN_TILE) {
+  // weights -> BF16 B^T chunks (real form of the complex product), once per CTA
+  for (int e = tid; e < NCHUNK * NPAD * 16; e += NN_THREADS) {
     const int c = e / (NPAD * 16), rem = e - c * NPAD * 16;
     const int n = rem / 16, k = rem - n * 16;
     const int j = k / (2 * CIN), i = (k / 2) % CIN, ri = k & 1;
@@ -187,72 +263,89 @@ __global__ void __launch_bounds__(NN_TILE) nn_layer_kernel(const NnLayerArgs A) 
     }
     *(__nv_bfloat16*)(sB[c] + kmajor_offset(n, k, 16)) = __float2bfloat16_rn(val);
   }
-  NnNeighbours nbs;
-  if (valid) nn_neighbours(nbs, cb, p, g);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
   const uint32_t idesc = make_idesc_bf16(NN_TILE, NPAD);
+  const int c0 = CIN == 8 ? 4 * hh : 0;
   bool ok = true;
+  uint32_t G = 0;  // chunks issued by this CTA so far
 
-  for (int c = 0; c < NCHUNK; c++) {
-    const int buf = c & 1;
-    if (c >= 2) ok = mbar_wait_bounded(&bar[buf], ((c - 2) >> 1) & 1, NN_SPIN_LIMIT) && ok;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int p = tile / tpp;
+    const int cb = (tile - p * tpp) * NN_TILE + s;
+    const bool valid = cb < g.Vh;
+    int nb[NN_NDIR];
+    int x3 = 0;
+    if (valid) nn_nbr(nb, x3, cb, p, g);
 #pragma unroll
-    for (int j = 0; j < DPC; j++) {
-      const int d = c * DPC + j;
-      cx<float> t[CIN * 3];
+    for (int c = 0; c < NCHUNK; c++, G++) {
+      const uint32_t buf = G & 1u;
+      if (G >= 2) ok = mbar_wait_bounded(&bar[buf], ((G - 2) >> 1) & 1u, NN_SPIN_LIMIT) && ok;
+      const int d = CIN == 8 ? c : 2 * c + hh;
+      // the neighbour index by compile-time subscripts only (nb stays in registers)
+      int n;
+      if constexpr (CIN == 8) {
+        n = nb[c];
+      } else {
+        n = hh ? nb[2 * c + 1 < NN_NDIR ? 2 * c + 1 : 0] : nb[2 * c];
+      }
+      cx<float> t[12];
       if (valid && d < NN_NDIR) {
-        nn_transport<CIN>(t, A, nbs, d, p);
+        nn_transport4<CIN>(t, A, d, p, cb, n, x3, c0);
       } else {
 #pragma unroll
-        for (int k = 0; k < CIN * 3; k++) t[k] = mk<float>(0.f, 0.f);
+        for (int k = 0; k < 12; k++) t[k] = mk<float>(0.f, 0.f);
       }
 #pragma unroll
       for (int a = 0; a < 3; a++) {
 #pragma unroll
-        for (int i = 0; i < CIN; i++) {
-          const int k = 2 * (j * CIN + i);
+        for (int i = 0; i < 4; i++) {
+          const int k = 2 * (4 * hh + i);
           __nv_bfloat162 h = __floats2bfloat162_rn(t[i * 3 + a].r, t[i * 3 + a].i);
-          *(__nv_bfloat162*)(sA[buf][a] + kmajor_offset(tid, k, 16)) = h;
+          *(__nv_bfloat162*)(sA[buf][a] + kmajor_offset(s, k, 16)) = h;
         }
       }
+      fence_smem_to_async();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        const uint64_t bd = make_smem_desc(smem_u32(sB[c]), 128, 256);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const uint64_t ad = make_smem_desc(smem_u32(sA[buf][a]), 128, 256);
+          tc_mma_bf16(tbase + (uint32_t)(a * NPAD), ad, bd, idesc, c > 0 ? 1u : 0u);
+        }
+        tc_commit(&bar[buf]);
+      }
     }
-    fence_smem_to_async();
-    tc_fence_before();
-    __syncthreads();
+    // the tile's last commit covers every MMA issued before it
+    ok = mbar_wait_bounded(&bar[(G - 1) & 1u], ((G - 1) >> 1) & 1u, NN_SPIN_LIMIT) && ok;
+    // tcgen05.ld is warp-collective: decide once for the whole CTA
+    ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
-    if (tid == 0) {
-      const uint64_t bd = make_smem_desc(smem_u32(sB[c]), 128, 256);
+    if (!ok) break;
+    if (warp < 4) {
+      cx<float> y[COUT * 3];
 #pragma unroll
       for (int a = 0; a < 3; a++) {
-        const uint64_t ad = make_smem_desc(smem_u32(sA[buf][a]), 128, 256);
-        tc_mma_bf16(tbase + (uint32_t)(a * NPAD), ad, bd, idesc, c > 0 ? 1u : 0u);
+        float v[16];
+        tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * NPAD), v);
+#pragma unroll
+        for (int o = 0; o < COUT; o++) y[o * 3 + a] = mk<float>(v[2 * o], v[2 * o + 1]);
       }
-      tc_commit(&bar[buf]);
+      if (valid) nn_store<COUT>(A.out + p * A.out_half, cb, g.Vh_pad, y);
     }
+    // the next tile's first MMA is issued after a __syncthreads that follows
+    // these TMEM reads
+    tc_fence_before();
   }
-  // the last commit covers every MMA issued before it
-  {
-    const int c = NCHUNK - 1;
-    ok = mbar_wait_bounded(&bar[c & 1], (c >> 1) & 1, NN_SPIN_LIMIT) && ok;
-  }
-  // tcgen05.ld is warp-collective: decide once for the whole CTA
-  ok = __syncthreads_and(ok) != 0;
-  tc_fence_after();
   if (!ok) {
     if (tid == 0) atomicExch(A.err, 1);
-  } else {
-    cx<float> y[COUT * 3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      float v[16];
-      tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * NPAD), v);
-#pragma unroll
-      for (int o = 0; o < COUT; o++) y[o * 3 + a] = mk<float>(v[2 * o], v[2 * o + 1]);
-    }
-    if (valid) nn_store<COUT>(A.out + p * A.out_half, cb, g.Vh_pad, y);
+    // give MMAs still in flight a second bounded wait before TMEM is freed
+    if (G > 0) mbar_wait_bounded(&bar[(G - 1) & 1u], ((G - 1) >> 1) & 1u, NN_SPIN_LIMIT);
   }
   tc_fence_before();
   __syncthreads();
