@@ -211,15 +211,43 @@ int wd_mhat(void *out, const void *in, const void *gauge, void *tmp, double kapp
  * nrhs packed half fields laid out back to back (consecutive fields
  * wd_spinor_bytes(dims, parity, prec) apart) share one gauge field:
  *     out_r = a * H_{p,1-p} in_r  [+ bx * x_r]          r = 0 .. nrhs-1
- * (H^+ when dagger != 0).  Each link is read from memory once per site and
- * applied to every right-hand side (links staged in shared memory for the
- * 12-real FP32/FP16 formats).  x may be NULL or alias out; in must not.  If
- * norm2 != NULL (device, nrhs doubles) it receives ||out_r||^2.
- * 1 <= nrhs <= 32.
+ * (H^+ when dagger != 0).  The CTAs that cover the right-hand sides of the
+ * same sites run together, so each link comes from memory once per site and
+ * serves every right-hand side from cache.  The tile shape (right-hand-side
+ * warps per CTA) comes from the autotuner below.  x may be NULL or alias out;
+ * in must not.  If norm2 != NULL (device, nrhs doubles) it receives
+ * ||out_r||^2, summed in a fixed order.  1 <= nrhs <= 32.
  */
 int wd_dslash_mrhs(void *out, const void *in, const void *gauge, int parity, int dagger,
                    double a, const void *x, double bx, int nrhs, double *norm2,
                    const int dims[4], int prec, int recon);
+
+/*
+ * Autotuner of the multi-right-hand-side tile shape: the right-hand-side
+ * warps per CTA (1, 2, 4 or 8) of wd_dslash_mrhs and of the hopping launches
+ * of wd_solve_batch (the paper has no such component).
+ *
+ * enable = 1 (the default): a batch shape (precision, link format, dagger,
+ * fused norm, tile count, largest nrhs, problem count) met for the first time
+ * outside stream capture is timed with every tile shape (CUDA events, one
+ * warm-up and three launches each) on temporary output buffers, so no caller
+ * data is written; the fastest shape is used from then on.  Tuning needs
+ * device memory for one copy of the outputs; without it the default shape (4)
+ * is kept.  wd_solve_batch tunes its inner launches before it captures its
+ * iteration graph.  enable = 0: shapes not yet tuned use the default.
+ * Returns the previous setting.
+ */
+int wd_set_autotune(int enable);
+
+/* Force one tile shape for every multi-RHS launch (lanes = 1, 2, 4 or 8), or
+ * go back to the tuned/default shapes (lanes = 0).  WD_ERR_ARG otherwise. */
+int wd_mrhs_set_lanes(int lanes);
+
+/* Text table of the tuned shapes, one line per batch shape with the
+ * microseconds of every candidate and the choice.  Writes at most len bytes,
+ * NUL-terminated, into buf (buf may be NULL when len is 0).  Returns the
+ * number of tuned shapes. */
+int wd_tune_report(char *buf, size_t len);
 
 /*
  * Temporal gauge (paper, section "Performance": fixing the temporal links to
@@ -379,6 +407,10 @@ typedef struct {
     float lr;                /* Adam learning rate (2e-3) */
     unsigned long long seed; /* seed of the on-device sample generator (4242) */
     int init;                /* 1: start from the hopping series (wd_nn_init) */
+    int smooth;              /* k > 0: every other x is damped k times,
+                              * x <- x - w D^+ D x with w = 1/(1+8 kappa)^2,
+                              * which keeps the low modes of D that set the
+                              * Krylov iteration count (0) */
 } wd_nn_train_params;
 
 typedef struct {

@@ -28,6 +28,9 @@ cudaError_t dslash_mrhs(void* out, const void* in, const void* gauge, int parity
 int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
                const wd_solve_params* prm, wd_solve_info* info);
 void solver_finalize();
+int set_autotune(int enable);
+int mrhs_set_lanes(int lanes);
+int tune_report(char* buf, size_t len);
 }  // namespace wd
 
 using namespace wd;
@@ -255,6 +258,12 @@ int wd_dslash_mrhs(void* out, const void* in, const void* gauge, int parity, int
                                  make_geom(dims), prec, recon, state().stream));
 }
 
+int wd_set_autotune(int enable) { return set_autotune(enable); }
+
+int wd_mrhs_set_lanes(int lanes) { return mrhs_set_lanes(lanes); }
+
+int wd_tune_report(char* buf, size_t len) { return tune_report(buf, len); }
+
 int wd_solve_batch(const wd_batch_problem* problems, int nproblems, const wd_solve_params* params,
                    wd_solve_info* info) {
   if (!problems) return WD_ERR_NULL;
@@ -310,6 +319,7 @@ void wd_nn_train_params_default(wd_nn_train_params* p) {
   p->lr = 2e-3f;
   p->seed = 4242ull;
   p->init = 1;
+  p->smooth = 0;
 }
 
 int wd_nn_layer(void* out, const void* in, const float* weights, int cin, int cout,

@@ -13,7 +13,9 @@
 // captured CUDA graph.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "wd_mrhs.cuh"
@@ -21,24 +23,247 @@
 namespace wd {
 
 cudaError_t launch_mrhs_f64(const MrhsBatch& bt, int recon, bool dagger, const int* active,
-                            RedScratch rs, double* norm_out, int grid, cudaStream_t st);
+                            RedScratch rs, bool norm, int lanes, cudaStream_t st);
 cudaError_t launch_mrhs_f32(const MrhsBatch& bt, int recon, bool dagger, const int* active,
-                            RedScratch rs, double* norm_out, int grid, cudaStream_t st);
+                            RedScratch rs, bool norm, int lanes, cudaStream_t st);
 cudaError_t launch_mrhs_f16(const MrhsBatch& bt, int recon, bool dagger, const int* active,
-                            RedScratch rs, double* norm_out, int grid, cudaStream_t st);
+                            RedScratch rs, bool norm, int lanes, cudaStream_t st);
+
+// Per-right-hand-side sums of the partials that a reducing batch kernel left
+// in [local rhs][unit] layout (unit = tile or sub-tile, `stride` units per
+// rhs row): problem j owns units s0[j] .. s0[j] + n[j] - 1.  One block per
+// batch-wide right-hand side; each thread sums a fixed strided subset, then a
+// fixed tree, so the result does not depend on scheduling.
+struct SumList {
+  int nprob, stride;
+  int rhs0[MRHS_MAX_PROBLEMS], nrhs[MRHS_MAX_PROBLEMS];
+  int s0[MRHS_MAX_PROBLEMS], n[MRHS_MAX_PROBLEMS];
+};
+
+constexpr int SUM_BS = 512;
+
+__global__ void __launch_bounds__(SUM_BS) sum_partials_kernel(const __grid_constant__ SumList L,
+                                                              const int* active,
+                                                              const double* __restrict__ partials,
+                                                              double* out) {
+  __shared__ double red[SUM_BS / 32];
+  const int gi = blockIdx.x;
+  int j = -1;
+  for (int k = 0; k < L.nprob; k++)
+    if (gi >= L.rhs0[k] && gi < L.rhs0[k] + L.nrhs[k]) j = k;
+  if (j < 0 || (active != nullptr && active[gi] == 0)) return;  // uniform per block
+  const int r = gi - L.rhs0[j];
+  const double* row = partials + (size_t)r * L.stride + L.s0[j];
+  // four independent chains per thread keep four loads in flight; they are
+  // combined in a fixed order
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int t = threadIdx.x;
+  for (; t + 3 * SUM_BS < L.n[j]; t += 4 * SUM_BS) {
+    a0 += __ldcg(row + t);
+    a1 += __ldcg(row + t + SUM_BS);
+    a2 += __ldcg(row + t + 2 * SUM_BS);
+    a3 += __ldcg(row + t + 3 * SUM_BS);
+  }
+  for (; t < L.n[j]; t += SUM_BS) a0 += __ldcg(row + t);
+  double v[1] = {(a0 + a1) + (a2 + a3)};
+  block_sum<1, SUM_BS>(v, red);
+  if (threadIdx.x == 0) out[gi] = v[0];
+}
+
+template <typename B>
+static cudaError_t sum_partials(const B& bt, int units_per_tile, const int* active,
+                                const double* partials, double* out, cudaStream_t st) {
+  SumList L;
+  std::memset(&L, 0, sizeof(L));
+  L.nprob = bt.nprob;
+  L.stride = bt.ntiles * units_per_tile;
+  int nr = 0;
+  for (int j = 0; j < bt.nprob; j++) {
+    L.rhs0[j] = bt.p[j].rhs0;
+    L.nrhs[j] = bt.p[j].nrhs;
+    L.s0[j] = bt.p[j].tile0 * units_per_tile;
+    L.n[j] = bt.p[j].ntiles * units_per_tile;
+    nr = bt.p[j].rhs0 + bt.p[j].nrhs > nr ? bt.p[j].rhs0 + bt.p[j].nrhs : nr;
+  }
+  if (nr < 1) return cudaSuccess;
+  sum_partials_kernel<<<nr, SUM_BS, 0, st>>>(L, active, partials, out);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mrhs_raw(int prec, const MrhsBatch& bt, int recon, bool dagger,
+                                   const int* active, RedScratch rs, double* norm_out, int lanes,
+                                   cudaStream_t st) {
+  const bool norm = norm_out != nullptr;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (prec) {
+    case WD_F64: e = launch_mrhs_f64(bt, recon, dagger, active, rs, norm, lanes, st); break;
+    case WD_F32: e = launch_mrhs_f32(bt, recon, dagger, active, rs, norm, lanes, st); break;
+    case WD_F16: e = launch_mrhs_f16(bt, recon, dagger, active, rs, norm, lanes, st); break;
+  }
+  if (e != cudaSuccess || !norm) return e;
+  return sum_partials(bt, MRHS_BS / MRHS_SUB, active, rs.partials, norm_out, st);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the multi-right-hand-side tile shape.  A batch shape (precision,
+// link format, dagger, fused norm, tile count, largest nrhs, problem count)
+// met for the first time outside stream capture is timed with every shape
+// (1, 2, 4, 8 right-hand-side warps per CTA): one warm-up and three timed
+// launches each, CUDA events on the launching stream, outputs (and norms)
+// redirected to a temporary buffer so that no caller data is written.  The
+// fastest shape is kept for the life of the process.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct MrhsKey {
+  int prec, recon, dagger, norm, ntiles, maxr, nprob;
+  bool operator<(const MrhsKey& o) const {
+    const int a[7] = {prec, recon, dagger, norm, ntiles, maxr, nprob};
+    const int b[7] = {o.prec, o.recon, o.dagger, o.norm, o.ntiles, o.maxr, o.nprob};
+    for (int k = 0; k < 7; k++)
+      if (a[k] != b[k]) return a[k] < b[k];
+    return false;
+  }
+};
+
+struct MrhsTuned {
+  int lanes;
+  float us[4];  // per candidate, 0 when not timed
+};
+
+constexpr int LANE_CHOICES[4] = {1, 2, 4, 8};
+
+std::map<MrhsKey, MrhsTuned>& tune_table() {
+  static std::map<MrhsKey, MrhsTuned> t;
+  return t;
+}
+int g_autotune = 1;
+int g_force_lanes = 0;
+
+MrhsKey make_key(int prec, const MrhsBatch& bt, int recon, bool dagger, bool norm) {
+  int maxr = 1;
+  for (int j = 0; j < bt.nprob; j++) maxr = bt.p[j].nrhs > maxr ? bt.p[j].nrhs : maxr;
+  return MrhsKey{prec, recon, dagger ? 1 : 0, norm ? 1 : 0, bt.ntiles, maxr, bt.nprob};
+}
+
+// The tuned (or default) shape for this batch; times the candidates when the
+// shape is new, tuning is on and the stream is not being captured.
+cudaError_t mrhs_lanes(int prec, const MrhsBatch& bt, int recon, bool dagger, const int* active,
+                       RedScratch rs, bool norm, cudaStream_t st, int* lanes) {
+  if (g_force_lanes) {
+    *lanes = g_force_lanes;
+    return cudaSuccess;
+  }
+  const MrhsKey key = make_key(prec, bt, recon, dagger, norm);
+  auto it = tune_table().find(key);
+  if (it != tune_table().end()) {
+    *lanes = it->second.lanes;
+    return cudaSuccess;
+  }
+  *lanes = MRHS_LANES;
+  if (!g_autotune) return cudaSuccess;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) return cudaSuccess;
+  // temporary outputs: every problem's nrhs fields, and the norms
+  size_t total = 256 + (size_t)MRHS_MAX_PROBLEMS * MRHS_MAX * sizeof(double);
+  for (int j = 0; j < bt.nprob; j++) total += ((size_t)bt.p[j].nrhs * bt.p[j].s_out + 255) / 256 * 256;
+  char* buf = nullptr;
+  if (cudaMalloc(&buf, total) != cudaSuccess) {
+    cudaGetLastError();  // no room to tune: keep the default shape
+    return cudaSuccess;
+  }
+  MrhsBatch t = bt;
+  size_t off = 256 + (size_t)MRHS_MAX_PROBLEMS * MRHS_MAX * sizeof(double);
+  for (int j = 0; j < bt.nprob; j++) {
+    t.p[j].out = buf + off;
+    // x and y keep pointing at the caller's fields: they are only read
+    off += ((size_t)bt.p[j].nrhs * bt.p[j].s_out + 255) / 256 * 256;
+  }
+  double* nt = norm ? (double*)(buf + 256) : nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MrhsTuned best{MRHS_LANES, {0.f, 0.f, 0.f, 0.f}};
+  float best_us = 0.f;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int c = 0; c < 4 && e == cudaSuccess; c++) {
+    const int L = LANE_CHOICES[c];
+    e = launch_mrhs_raw(prec, t, recon, dagger, active, rs, nt, L, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int k = 0; k < 3 && e == cudaSuccess; k++)
+      e = launch_mrhs_raw(prec, t, recon, dagger, active, rs, nt, L, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    const float us = ms * 1e3f / 3.f;
+    best.us[c] = us;
+    if (best_us == 0.f || us < best_us) {
+      best_us = us;
+      best.lanes = L;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaError_t fe = cudaFree(buf);
+  if (e != cudaSuccess) return e;
+  if (fe != cudaSuccess) return fe;
+  tune_table()[key] = best;
+  *lanes = best.lanes;
+  return cudaSuccess;
+}
+
+}  // namespace
 
 static cudaError_t launch_mrhs(int prec, const MrhsBatch& bt, int recon, bool dagger,
                                const int* active, RedScratch rs, double* norm_out, cudaStream_t st) {
-  // one CTA per 32-site sub-tile (4 per tile), grid-stride beyond ~16 per SM
-  const int nsub = bt.ntiles * (MRHS_BS / MRHS_SUB);
-  int grid = nsub < num_sms() * 16 ? nsub : num_sms() * 16;
-  if (grid < 1) grid = 1;
-  switch (prec) {
-    case WD_F64: return launch_mrhs_f64(bt, recon, dagger, active, rs, norm_out, grid, st);
-    case WD_F32: return launch_mrhs_f32(bt, recon, dagger, active, rs, norm_out, grid, st);
-    case WD_F16: return launch_mrhs_f16(bt, recon, dagger, active, rs, norm_out, grid, st);
+  int lanes = MRHS_LANES;
+  cudaError_t e = mrhs_lanes(prec, bt, recon, dagger, active, rs, norm_out != nullptr, st, &lanes);
+  if (e != cudaSuccess) return e;
+  return launch_mrhs_raw(prec, bt, recon, dagger, active, rs, norm_out, lanes, st);
+}
+
+int set_autotune(int enable) {
+  const int prev = g_autotune;
+  g_autotune = enable ? 1 : 0;
+  return prev;
+}
+
+int mrhs_set_lanes(int lanes) {
+  if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return WD_ERR_ARG;
+  g_force_lanes = lanes;
+  return WD_OK;
+}
+
+int tune_report(char* buf, size_t len) {
+  size_t used = 0;
+  if (buf && len) buf[0] = 0;
+  for (const auto& kv : tune_table()) {
+    const MrhsKey& k = kv.first;
+    const MrhsTuned& v = kv.second;
+    char line[256];
+    std::snprintf(line, sizeof(line),
+                  "mrhs prec=%d recon=%d dagger=%d norm=%d tiles=%d maxrhs=%d problems=%d "
+                  "us[1,2,4,8]=%.1f,%.1f,%.1f,%.1f lanes=%d\n",
+                  k.prec, k.recon, k.dagger, k.norm, k.ntiles, k.maxr, k.nprob, v.us[0], v.us[1],
+                  v.us[2], v.us[3], v.lanes);
+    const size_t n = std::strlen(line);
+    if (buf && used + n + 1 <= len) {
+      std::memcpy(buf + used, line, n + 1);
+      used += n;
+    }
   }
-  return cudaErrorInvalidValue;
+  return (int)tune_table().size();
+}
+
+// tune a launch shape without running it (before a graph capture)
+static cudaError_t tune_mrhs(int prec, const MrhsBatch& bt, int recon, bool dagger,
+                             const int* active, RedScratch rs, bool norm, cudaStream_t st) {
+  int lanes = MRHS_LANES;
+  return mrhs_lanes(prec, bt, recon, dagger, active, rs, norm, st, &lanes);
 }
 
 // ---------------------------------------------------------------------------
@@ -57,34 +282,6 @@ struct BlasBatch {
   BlasProblem p[MRHS_MAX_PROBLEMS];
 };
 
-// sums the per-(tile, rhs) partials of every active right-hand side in tile
-// order; called by every thread of every CTA at the end of a reducing kernel
-__device__ __forceinline__ void batch_finalize(const BlasBatch& bt, const int* active,
-                                               RedScratch rs, double* out, double* red) {
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned t = atomicAdd(rs.counter, 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  for (int j = 0; j < bt.nprob; j++) {
-    const BlasProblem& pr = bt.p[j];
-    for (int r = 0; r < pr.nrhs; r++) {
-      if (active[pr.rhs0 + r] == 0) continue;
-      double v[1] = {0.0};
-      for (int t = threadIdx.x; t < pr.ntiles; t += MRHS_BS)
-        v[0] += __ldcg(rs.partials + (size_t)(pr.tile0 + t) * MRHS_MAX + r);
-      block_sum<1, MRHS_BS>(v, red);
-      if (threadIdx.x == 0) out[pr.rhs0 + r] = v[0];
-    }
-  }
-  if (threadIdx.x == 0) *rs.counter = 0u;
-}
-
 #define WD_TILE_LOOP                                                   \
   for (int tile = blockIdx.x; tile < bt.ntiles; tile += gridDim.x) {   \
     int j = 0;                                                         \
@@ -94,12 +291,14 @@ __device__ __forceinline__ void batch_finalize(const BlasBatch& bt, const int* a
     const bool valid = cb < pr.g.Vh;                                   \
     const int VP = pr.g.Vh_pad;
 
-// r -= alpha q (f0 = r, f1 = q); rr = ||r||^2 ; alpha = gk / qq per rhs
+// r -= alpha q (f0 = r, f1 = q); alpha = gk / qq per rhs; per-(rhs, tile)
+// partials of ||r||^2, summed into rr by sum_partials_kernel
 template <int P>
 __global__ void __launch_bounds__(MRHS_BS) batch_update_r(const __grid_constant__ BlasBatch bt, const int* active,
                                                           const double* gk, const double* qq,
                                                           RedScratch rs, double* rr) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
+  (void)rr;
   __shared__ double red[MRHS_BS / 32];
   WD_TILE_LOOP
   for (int r = 0; r < pr.nrhs; r++) {
@@ -123,10 +322,9 @@ __global__ void __launch_bounds__(MRHS_BS) batch_update_r(const __grid_constant_
     }
     double v[1] = {t};
     block_sum<1, MRHS_BS>(v, red);
-    if (threadIdx.x == 0) rs.partials[(size_t)tile * MRHS_MAX + r] = v[0];
+    if (threadIdx.x == 0) rs.partials[(size_t)r * bt.ntiles + tile] = v[0];
   }
   }
-  batch_finalize(bt, active, rs, rr, red);
 }
 
 // x += alpha p ; p = s + beta p   (f0 = x [PX], f1 = p, f2 = s)
@@ -385,6 +583,7 @@ cudaError_t batch_iteration_t(BatchCtx& c, const Plan& pl, int kp, cudaStream_t 
   if ((e = launch_mrhs(c.sprec, pl.d_eo_q, c.srecon, false, c.active, rs, sc.qq, st))) return e;
   batch_update_r<P><<<grid, MRHS_BS, 0, st>>>(pl.upd_r, c.active, sc.gamma[kp], sc.qq, rs, sc.rr);
   if ((e = cudaGetLastError())) return e;
+  if ((e = sum_partials(pl.upd_r, 1, c.active, rs.partials, sc.rr, st))) return e;
   if ((e = launch_mrhs(c.sprec, pl.d_oe_r_dag, c.srecon, true, c.active, rs, nullptr, st))) return e;
   if ((e = launch_mrhs(c.sprec, pl.d_eo_s_dag, c.srecon, true, c.active, rs, sc.gamma[1 - kp], st)))
     return e;
@@ -621,6 +820,14 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
   // ---- the iteration graph ----
   cudaGraphExec_t exec = nullptr;
   if (P.use_graph && nact > 0) {
+    // the inner launch shapes, tuned before they are frozen into the graph
+    {
+      RedScratch rs = scratch();
+      WD_BCK(tune_mrhs(c.sprec, pl.d_oe_p, c.srecon, false, c.active, rs, false, st));
+      WD_BCK(tune_mrhs(c.sprec, pl.d_eo_q, c.srecon, false, c.active, rs, true, st));
+      WD_BCK(tune_mrhs(c.sprec, pl.d_oe_r_dag, c.srecon, true, c.active, rs, false, st));
+      WD_BCK(tune_mrhs(c.sprec, pl.d_eo_s_dag, c.srecon, true, c.active, rs, true, st));
+    }
     cudaGraph_t graph = nullptr;
     WD_BCK(cudaStreamBeginCapture(c.cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;

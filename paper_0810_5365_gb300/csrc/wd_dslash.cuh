@@ -234,10 +234,6 @@ __device__ __forceinline__ RawF16 fetch_f16(const void* __restrict__ in,
   return r;
 }
 
-#ifndef WD_F16_HMATH
-#define WD_F16_HMATH 1
-#endif
-
 // Packed half2 complex arithmetic for the FP16 link product.  With
 // hx = (-h.i, h.r) = i h:  u h = u.r h + u.i hx, and with hx = (h.i, -h.r) =
 // -i h:  conj(u) h = u.r h + u.i hx, so one routine serves U h and U^+ h.
@@ -306,66 +302,18 @@ __device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& 
   }
   __half2 hh[6];
   project_h2<MU, S>(v, hh);
-#if WD_F16_HMATH
-  {
-    __half2 t2[6];
-    if (MU == 3 && unit) {
-#pragma unroll
-      for (int k = 0; k < 6; k++) t2[k] = hh[k];
-    } else {
-      transport_h2<FWD>(r, hh, t2);
-    }
-    cx<float> t[6];
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-      const float2 f = __half22float2(t2[k]);
-      t[k] = mk<float>(f.x, f.y);
-    }
-    const float sc = (MU == 3 && flip) ? -r.sc : r.sc;
-    expand_add<MU, S, false>(acc, t, sc);
-    return;
-  }
-#endif
-  cx<float> h[6];
-#pragma unroll
-  for (int k = 0; k < 6; k++) {
-    float2 f = __half22float2(hh[k]);
-    h[k] = mk<float>(f.x, f.y);
-  }
-  cx<float> t[6];
+  __half2 t2[6];
   if (MU == 3 && unit) {
 #pragma unroll
-    for (int k = 0; k < 6; k++) t[k] = h[k];
+    for (int k = 0; k < 6; k++) t2[k] = hh[k];
   } else {
-    cx<float> u[9];
-    const __half2* ha = reinterpret_cast<const __half2*>(&r.la);
-    const __half2* hb = reinterpret_cast<const __half2*>(&r.lb);
+    transport_h2<FWD>(r, hh, t2);
+  }
+  cx<float> t[6];
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      float2 f = __half22float2(ha[j]);
-      u[j] = mk<float>(f.x, f.y);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; j++) {
-      float2 f = __half22float2(hb[j]);
-      u[4 + j] = mk<float>(f.x, f.y);
-    }
-    reconstruct_row2(u);
-#pragma unroll
-    for (int hs = 0; hs < 2; hs++) {
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        cx<float> w = mk<float>(0, 0);
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-          if (FWD)
-            w = cmadd(u[c * 3 + d], h[hs * 3 + d], w);
-          else
-            w = cjmadd(u[d * 3 + c], h[hs * 3 + d], w);
-        }
-        t[hs * 3 + c] = w;
-      }
-    }
+  for (int k = 0; k < 6; k++) {
+    const float2 f = __half22float2(t2[k]);
+    t[k] = mk<float>(f.x, f.y);
   }
   const float sc = (MU == 3 && flip) ? -r.sc : r.sc;
   expand_add<MU, S, false>(acc, t, sc);
@@ -374,6 +322,53 @@ __device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& 
 #ifndef WD_F16_PREFETCH
 #define WD_F16_PREFETCH 2
 #endif
+
+// The eight hops of one FP16 site: the loads of the next hops are issued
+// before the current one is computed (WD_F16_PREFETCH hops in flight).
+// funit/bunit: the forward/backward time link is the identity (temporal gauge).
+template <int SF, int SB_>
+__device__ __forceinline__ void hops_f16(cx<float> (&acc)[12], const void* __restrict__ in,
+                                         const void* __restrict__ ga, int p, int cb, int f0,
+                                         int b0, int f1, int b1, int f2, int b2, int f3, int b3,
+                                         bool fflip, bool bflip, bool funit, bool bunit, int VP) {
+  const int q = 1 - p;
+#define WD_F(nb, reg, lcb) fetch_f16(in, ga, nb, reg, lcb, VP)
+#if WD_F16_PREFETCH >= 2
+  RawF16 r0 = WD_F(f0, 0 + p, cb), r1 = WD_F(b0, 0 + q, b0);
+  RawF16 r2 = WD_F(f1, 2 + p, cb);
+  compute_f16<0, SF, true>(acc, r0, false);
+  RawF16 r3 = WD_F(b1, 2 + q, b1);
+  compute_f16<0, SB_, false>(acc, r1, false);
+  r0 = WD_F(f2, 4 + p, cb);
+  compute_f16<1, SF, true>(acc, r2, false);
+  r1 = WD_F(b2, 4 + q, b2);
+  compute_f16<1, SB_, false>(acc, r3, false);
+  r2 = fetch_f16(in, ga, f3, 6 + p, cb, VP, funit);
+  compute_f16<2, SF, true>(acc, r0, false);
+  r3 = fetch_f16(in, ga, b3, 6 + q, b3, VP, bunit);
+  compute_f16<2, SB_, false>(acc, r1, false);
+  compute_f16<3, SF, true>(acc, r2, fflip, funit);
+  compute_f16<3, SB_, false>(acc, r3, bflip, bunit);
+#else
+  RawF16 r0 = WD_F(f0, 0 + p, cb);
+  RawF16 r1 = WD_F(b0, 0 + q, b0);
+  compute_f16<0, SF, true>(acc, r0, false);
+  r0 = WD_F(f1, 2 + p, cb);
+  compute_f16<0, SB_, false>(acc, r1, false);
+  r1 = WD_F(b1, 2 + q, b1);
+  compute_f16<1, SF, true>(acc, r0, false);
+  r0 = WD_F(f2, 4 + p, cb);
+  compute_f16<1, SB_, false>(acc, r1, false);
+  r1 = WD_F(b2, 4 + q, b2);
+  compute_f16<2, SF, true>(acc, r0, false);
+  r0 = fetch_f16(in, ga, f3, 6 + p, cb, VP, funit);
+  compute_f16<2, SB_, false>(acc, r1, false);
+  r1 = fetch_f16(in, ga, b3, 6 + q, b3, VP, bunit);
+  compute_f16<3, SF, true>(acc, r0, fflip, funit);
+  compute_f16<3, SB_, false>(acc, r1, bflip, bunit);
+#endif
+#undef WD_F
+}
 
 // TG: links in temporal gauge (compile-time, so that the ordinary kernel keeps
 // its register budget)
@@ -419,44 +414,8 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, RED != RED_NONE>::value
     for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
 
     if constexpr (P == WD_F16) {
-      const void* in = a.in;
-      const void* ga = a.gauge;
-#define WD_F(nb, reg, lcb) fetch_f16(in, ga, nb, reg, lcb, VP)
-#if WD_F16_PREFETCH >= 2
-      RawF16 r0 = WD_F(f0, 0 + p, cb), r1 = WD_F(b0, 0 + q, b0);
-      RawF16 r2 = WD_F(f1, 2 + p, cb);
-      compute_f16<0, SF, true>(acc, r0, false);
-      RawF16 r3 = WD_F(b1, 2 + q, b1);
-      compute_f16<0, SB_, false>(acc, r1, false);
-      r0 = WD_F(f2, 4 + p, cb);
-      compute_f16<1, SF, true>(acc, r2, false);
-      r1 = WD_F(b2, 4 + q, b2);
-      compute_f16<1, SB_, false>(acc, r3, false);
-      r2 = fetch_f16(in, ga, f3, 6 + p, cb, VP, funit);
-      compute_f16<2, SF, true>(acc, r0, false);
-      r3 = fetch_f16(in, ga, b3, 6 + q, b3, VP, bunit);
-      compute_f16<2, SB_, false>(acc, r1, false);
-      compute_f16<3, SF, true>(acc, r2, fflip, funit);
-      compute_f16<3, SB_, false>(acc, r3, bflip, bunit);
-#else
-      RawF16 r0 = WD_F(f0, 0 + p, cb);
-      RawF16 r1 = WD_F(b0, 0 + q, b0);
-      compute_f16<0, SF, true>(acc, r0, false);
-      r0 = WD_F(f1, 2 + p, cb);
-      compute_f16<0, SB_, false>(acc, r1, false);
-      r1 = WD_F(b1, 2 + q, b1);
-      compute_f16<1, SF, true>(acc, r0, false);
-      r0 = WD_F(f2, 4 + p, cb);
-      compute_f16<1, SB_, false>(acc, r1, false);
-      r1 = WD_F(b2, 4 + q, b2);
-      compute_f16<2, SF, true>(acc, r0, false);
-      r0 = fetch_f16(in, ga, f3, 6 + p, cb, VP, funit);
-      compute_f16<2, SB_, false>(acc, r1, false);
-      r1 = fetch_f16(in, ga, b3, 6 + q, b3, VP, bunit);
-      compute_f16<3, SF, true>(acc, r0, fflip, funit);
-      compute_f16<3, SB_, false>(acc, r1, bflip, bunit);
-#endif
-#undef WD_F
+      hops_f16<SF, SB_>(acc, a.in, a.gauge, p, cb, f0, b0, f1, b1, f2, b2, f3, b3, fflip, bflip,
+                        funit, bunit, VP);
     } else {
       hop<P, RC, 0, SF, true>(acc, a.in, a.gauge, f0, 0 + p, cb, false, VP);
       hop<P, RC, 0, SB_, false>(acc, a.in, a.gauge, b0, 0 + q, b0, false, VP);

@@ -8,7 +8,8 @@
 // link crosses HBM once per site instead of once per site and right-hand side
 // (the repeats are served by L1/L2).  Per right-hand side the epilogue is the one of the
 // single-field kernel (out = a H in + bx x + cy y), optionally with ||out||^2
-// reduced deterministically per right-hand side.
+// reduced deterministically per right-hand side (per-sub-tile partials here,
+// their fixed-order sum in sum_partials_kernel).
 #pragma once
 
 #include "wd_dslash.cuh"
@@ -43,38 +44,6 @@ struct MrhsBatch {
   MrhsProblem p[MRHS_MAX_PROBLEMS];
 };
 
-// one hop with a link already in registers
-template <int P, int MU, int S, bool FWD, typename R>
-__device__ __forceinline__ void hop_with_link(cx<R> (&acc)[12], const void* __restrict__ in, int nb,
-                                              const cx<R> (&u)[9], bool flip, int VP) {
-  cx<R> h[6];
-  R sc = load_project<P, MU, S, R>(h, in, nb, VP);
-  cx<R> t[6];
-#pragma unroll
-  for (int hs = 0; hs < 2; hs++) {
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      cx<R> v = mk<R>(0, 0);
-#pragma unroll
-      for (int d = 0; d < 3; d++) {
-        if (FWD)
-          v = cmadd(u[c * 3 + d], h[hs * 3 + d], v);
-        else
-          v = cjmadd(u[d * 3 + c], h[hs * 3 + d], v);
-      }
-      t[hs * 3 + c] = v;
-    }
-  }
-  if constexpr (P == WD_F16) {
-    if (MU == 3 && flip) sc = -sc;
-    expand_add<MU, S, false>(acc, t, sc);
-  } else if constexpr (MU == 3) {
-    expand_add<MU, S, false>(acc, t, flip ? (R)-1 : (R)1);
-  } else {
-    expand_add<MU, S, true>(acc, t, (R)1);
-  }
-}
-
 // One CTA = 32 sites x 4 right-hand-side lanes (one warp per right-hand
 // side).  Block b covers sub-tile b / G and right-hand sides 4 (b % G) .. +3,
 // G = ceil(max nrhs / 4): the G blocks of a sub-tile are adjacent in launch
@@ -82,22 +51,30 @@ __device__ __forceinline__ void hop_with_link(cx<R> (&acc)[12], const void* __re
 // per site for all right-hand sides.  Each thread computes one right-hand
 // side of one site, so the kernel keeps the registers (and occupancy) of the
 // single-field kernel.
-constexpr int MRHS_LANES = 4;   // right-hand-side lanes (warps) per CTA
+constexpr int MRHS_LANES = 4;   // default right-hand-side lanes (warps) per CTA
 constexpr int MRHS_SUB = 32;    // sites per CTA
 
-template <int P, int RC, bool DAG, bool NORM>
-__global__ void __launch_bounds__(MRHS_SUB* MRHS_LANES, DslashMinBlocks<P, NORM>::value)
+// The tile shape is a template parameter (1, 2, 4 or 8 right-hand-side warps
+// per CTA) chosen per batch shape by the autotuner; the register budget per
+// thread is the single-field kernel's for every shape.
+template <int P, bool NORM, int LANES>
+struct MrhsMinBlocks {
+  static constexpr int raw = DslashMinBlocks<P, NORM>::value * MRHS_LANES / LANES;
+  static constexpr int value = raw < 1 ? 1 : (raw > 32 ? 32 : raw);
+};
+
+template <int P, int RC, bool DAG, bool NORM, int LANES>
+__global__ void __launch_bounds__(MRHS_SUB* LANES, (MrhsMinBlocks<P, NORM, LANES>::value))
     mrhs_dslash_kernel(const __grid_constant__ MrhsBatch bt, int groups,
-                       const int* __restrict__ active, RedScratch rs, double* norm_out) {
+                       const int* __restrict__ active, RedScratch rs) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
-  __shared__ double red[MRHS_LANES];
   const int tx = threadIdx.x, ry = threadIdx.y;
   constexpr int SF = DAG ? -1 : 1;
   constexpr int SB_ = -SF;
   constexpr int SUBS = MRHS_BS / MRHS_SUB;  // sub-tiles per tile
   const int nprob = bt.nprob;
   const int sub = blockIdx.x / groups;
-  const int r = (blockIdx.x - sub * groups) * MRHS_LANES + ry;
+  const int r = (blockIdx.x - sub * groups) * LANES + ry;
   const int tile = sub / SUBS, q = sub - tile * SUBS;
   int j = 0;
   while (j + 1 < nprob && tile >= bt.p[j + 1].tile0) j++;
@@ -126,14 +103,19 @@ __global__ void __launch_bounds__(MRHS_SUB* MRHS_LANES, DslashMinBlocks<P, NORM>
     cx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
-    hop<P, RC, 0, SF, true>(acc, in, ga, f0, 0 + p, cb, false, VP);
-    hop<P, RC, 0, SB_, false>(acc, in, ga, b0, 0 + qq, b0, false, VP);
-    hop<P, RC, 1, SF, true>(acc, in, ga, f1, 2 + p, cb, false, VP);
-    hop<P, RC, 1, SB_, false>(acc, in, ga, b1, 2 + qq, b1, false, VP);
-    hop<P, RC, 2, SF, true>(acc, in, ga, f2, 4 + p, cb, false, VP);
-    hop<P, RC, 2, SB_, false>(acc, in, ga, b2, 4 + qq, b2, false, VP);
-    hop<P, RC, 3, SF, true>(acc, in, ga, f3, 6 + p, cb, fflip, VP);
-    hop<P, RC, 3, SB_, false>(acc, in, ga, b3, 6 + qq, b3, bflip, VP);
+    if constexpr (P == WD_F16) {
+      hops_f16<SF, SB_>(acc, in, ga, p, cb, f0, b0, f1, b1, f2, b2, f3, b3, fflip, bflip,
+                        false, false, VP);
+    } else {
+      hop<P, RC, 0, SF, true>(acc, in, ga, f0, 0 + p, cb, false, VP);
+      hop<P, RC, 0, SB_, false>(acc, in, ga, b0, 0 + qq, b0, false, VP);
+      hop<P, RC, 1, SF, true>(acc, in, ga, f1, 2 + p, cb, false, VP);
+      hop<P, RC, 1, SB_, false>(acc, in, ga, b1, 2 + qq, b1, false, VP);
+      hop<P, RC, 2, SF, true>(acc, in, ga, f2, 4 + p, cb, false, VP);
+      hop<P, RC, 2, SB_, false>(acc, in, ga, b2, 4 + qq, b2, false, VP);
+      hop<P, RC, 3, SF, true>(acc, in, ga, f3, 6 + p, cb, fflip, VP);
+      hop<P, RC, 3, SB_, false>(acc, in, ga, b3, 6 + qq, b3, bflip, VP);
+    }
     const R ca = (R)pr.a;
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
@@ -165,68 +147,55 @@ __global__ void __launch_bounds__(MRHS_SUB* MRHS_LANES, DslashMinBlocks<P, NORM>
     }
   }
   if constexpr (NORM) {
-    // one warp = one right-hand side of these 32 sites
+    // one warp = one right-hand side of these 32 sites; the per-(rhs,
+    // sub-tile) partials are summed in a fixed order by sum_partials_kernel
+    // ([local rhs][sub-tile] layout, so that those reads coalesce)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    if (tx == 0 && act) rs.partials[(size_t)sub * MRHS_MAX + r] = nrm;
-
-    // the last CTA to finish sums each right-hand side's sub-tiles in order
-    __shared__ bool last;
-    const int tid = ry * MRHS_SUB + tx;
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      unsigned t = atomicAdd(rs.counter, 1u);
-      last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (int jj = 0; jj < nprob; jj++) {
-      const MrhsProblem& pj = bt.p[jj];
-      for (int rr = 0; rr < pj.nrhs; rr++) {
-        if (active != nullptr && active[pj.rhs0 + rr] == 0) continue;
-        double v[1] = {0.0};
-        const int s0 = pj.tile0 * SUBS, ns = pj.ntiles * SUBS;
-        for (int t = tid; t < ns; t += MRHS_SUB * MRHS_LANES)
-          v[0] += __ldcg(rs.partials + (size_t)(s0 + t) * MRHS_MAX + rr);
-        block_sum<1, MRHS_SUB * MRHS_LANES>(v, red);
-        if (tid == 0) norm_out[pj.rhs0 + rr] = v[0];
-      }
-    }
-    if (tid == 0) *rs.counter = 0u;
+    if (tx == 0 && act) rs.partials[(size_t)r * (bt.ntiles * SUBS) + sub] = nrm;
   }
 }
 
-template <int P, int RC, bool DG, bool NM>
+template <int P, int RC, bool DG, bool NM, int L>
 cudaError_t launch_mrhs_one(const MrhsBatch& bt, const int* active, RedScratch rs,
-                            double* norm_out, int grid, cudaStream_t st) {
+                            cudaStream_t st) {
   int maxr = 1;
   for (int j = 0; j < bt.nprob; j++) maxr = bt.p[j].nrhs > maxr ? bt.p[j].nrhs : maxr;
-  const int groups = (maxr + MRHS_LANES - 1) / MRHS_LANES;
+  const int groups = (maxr + L - 1) / L;
   const long long nblk = (long long)bt.ntiles * (MRHS_BS / MRHS_SUB) * groups;
-  (void)grid;
-  mrhs_dslash_kernel<P, RC, DG, NM><<<(unsigned)nblk, dim3(MRHS_SUB, MRHS_LANES), 0, st>>>(
-      bt, groups, active, rs, norm_out);
+  mrhs_dslash_kernel<P, RC, DG, NM, L><<<(unsigned)nblk, dim3(MRHS_SUB, L), 0, st>>>(
+      bt, groups, active, rs);
   return cudaGetLastError();
 }
 
+template <int P, int RC, bool DG, bool NM>
+cudaError_t launch_mrhs_lanes(const MrhsBatch& bt, const int* active, RedScratch rs, int lanes,
+                              cudaStream_t st) {
+  switch (lanes) {
+    case 1: return launch_mrhs_one<P, RC, DG, NM, 1>(bt, active, rs, st);
+    case 2: return launch_mrhs_one<P, RC, DG, NM, 2>(bt, active, rs, st);
+    case 4: return launch_mrhs_one<P, RC, DG, NM, 4>(bt, active, rs, st);
+    case 8: return launch_mrhs_one<P, RC, DG, NM, 8>(bt, active, rs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// norm: the kernel leaves per-(rhs, sub-tile) partials of ||out||^2 in rs
 template <int P>
 cudaError_t launch_mrhs_prec(const MrhsBatch& bt, int recon, bool dagger, const int* active,
-                             RedScratch rs, double* norm_out, int grid, cudaStream_t st) {
-  const bool nm = norm_out != nullptr;
+                             RedScratch rs, bool norm, int lanes, cudaStream_t st) {
   if (recon == 12) {
-    if (dagger) return nm ? launch_mrhs_one<P, 12, true, true>(bt, active, rs, norm_out, grid, st)
-                          : launch_mrhs_one<P, 12, true, false>(bt, active, rs, norm_out, grid, st);
-    return nm ? launch_mrhs_one<P, 12, false, true>(bt, active, rs, norm_out, grid, st)
-              : launch_mrhs_one<P, 12, false, false>(bt, active, rs, norm_out, grid, st);
+    if (dagger) return norm ? launch_mrhs_lanes<P, 12, true, true>(bt, active, rs, lanes, st)
+                            : launch_mrhs_lanes<P, 12, true, false>(bt, active, rs, lanes, st);
+    return norm ? launch_mrhs_lanes<P, 12, false, true>(bt, active, rs, lanes, st)
+                : launch_mrhs_lanes<P, 12, false, false>(bt, active, rs, lanes, st);
   }
   if constexpr (P != WD_F16) {
     if (recon == 18) {
-      if (dagger) return nm ? launch_mrhs_one<P, 18, true, true>(bt, active, rs, norm_out, grid, st)
-                            : launch_mrhs_one<P, 18, true, false>(bt, active, rs, norm_out, grid, st);
-      return nm ? launch_mrhs_one<P, 18, false, true>(bt, active, rs, norm_out, grid, st)
-                : launch_mrhs_one<P, 18, false, false>(bt, active, rs, norm_out, grid, st);
+      if (dagger) return norm ? launch_mrhs_lanes<P, 18, true, true>(bt, active, rs, lanes, st)
+                              : launch_mrhs_lanes<P, 18, true, false>(bt, active, rs, lanes, st);
+      return norm ? launch_mrhs_lanes<P, 18, false, true>(bt, active, rs, lanes, st)
+                  : launch_mrhs_lanes<P, 18, false, false>(bt, active, rs, lanes, st);
     }
   }
   return cudaErrorInvalidValue;

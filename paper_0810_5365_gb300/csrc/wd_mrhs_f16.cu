@@ -4,8 +4,8 @@
 namespace wd {
 
 cudaError_t launch_mrhs_f16(const MrhsBatch& bt, int recon, bool dagger, const int* active,
-                            RedScratch rs, double* norm_out, int grid, cudaStream_t st) {
-  return launch_mrhs_prec<WD_F16>(bt, recon, dagger, active, rs, norm_out, grid, st);
+                            RedScratch rs, bool norm, int lanes, cudaStream_t st) {
+  return launch_mrhs_prec<WD_F16>(bt, recon, dagger, active, rs, norm, lanes, st);
 }
 
 }  // namespace wd

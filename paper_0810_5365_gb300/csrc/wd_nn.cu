@@ -30,13 +30,32 @@ constexpr int NN_PARAMS = nn_layer_offset(3);  // 2304 floats
 // the 512 TMEM columns / 64 per CTA), never more than there are tiles
 template <int CIN, int COUT>
 static cudaError_t launch_layer(const NnLayerArgs& A, int ntiles, cudaStream_t st) {
+  // residency from the kernel's own register and shared-memory footprint
+  // (registers are allocated per warp in units of 256)
   static int per_sm = 0;
   if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, nn_layer_kernel<CIN, COUT>, NN_THREADS, 0);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, nn_layer_kernel<CIN, COUT>);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    int regs_sm = 0, smem_sm = 0, thr_sm = 0;
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = regs_sm / (warp_regs * (NN_THREADS / 32));
+    const int by_smem = smem_sm / ((int)fa.sharedSizeBytes + 1024);
+    const int by_thr = thr_sm / NN_THREADS;
+    int n = by_regs < by_smem ? by_regs : by_smem;
+    n = n < by_thr ? n : by_thr;
+    n = n < 1 ? 1 : (n > 8 ? 8 : n);
+    // ask for a shared-memory carveout that holds all n CTAs
+    const int pct = (int)((100LL * n * ((int)fa.sharedSizeBytes + 1024) + smem_sm - 1) / smem_sm);
+    e = cudaFuncSetAttribute(nn_layer_kernel<CIN, COUT>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, pct < 100 ? pct : 100);
+    if (e != cudaSuccess) return e;
+    per_sm = n;
   }
   const int cap = num_sms() * per_sm;
   const int grid = ntiles < cap ? ntiles : cap;
@@ -492,7 +511,8 @@ bool on_device(const void* p) {
 // out = in - kappa H in on packed full fields (a = -kappa) or the variant
 // out = in - D in ... through the single-field kernel
 cudaError_t full_op(int prec, int recon, const void* gauge, void* out, const void* in,
-                    double kappa, const Geom& g, cudaStream_t st, const void* bfield = nullptr) {
+                    double kappa, const Geom& g, cudaStream_t st, const void* bfield = nullptr,
+                    bool dagger = false) {
   const size_t h = spinor_half_bytes(g, prec);
   for (int p = 0; p < 2; p++) {
     DslashArgs d;
@@ -517,7 +537,7 @@ cudaError_t full_op(int prec, int recon, const void* gauge, void* out, const voi
     d.rs = scratch();
     d.g = g;
     d.parity = p;
-    cudaError_t e = launch_dslash(prec, d, recon, false, st);
+    cudaError_t e = launch_dslash(prec, d, recon, dagger, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -598,7 +618,8 @@ int nn_train_impl(float* w, const double* gauge, double kappa, const int dims[4]
                   const wd_nn_train_params* prm, wd_nn_train_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
   wd_nn_train_params P = *prm;
-  if (P.samples < 1 || P.batch < 1 || P.epochs < 1 || !(P.lr > 0)) return WD_ERR_ARG;
+  if (P.samples < 1 || P.batch < 1 || P.epochs < 1 || !(P.lr > 0) || P.smooth < 0)
+    return WD_ERR_ARG;
   const Geom g = make_geom(dims);
   cudaStream_t st = state().stream;
   Alloc al;
@@ -657,6 +678,16 @@ int nn_train_impl(float* w, const double* gauge, double kappa, const int dims[4]
       gaussian_spinor_kernel<<<grid, 256, 0, st>>>((char*)x, key,
                                                    (unsigned long long)sample * V * 12, g, h32);
       NCK(cudaGetLastError());
+      if (P.smooth > 0 && (sample & 1)) {
+        // x <- x - w D^+ D x damps the large singular values of D (y and dl
+        // are free at this point and serve as the two temporaries)
+        const double wd = 1.0 / ((1.0 + 8.0 * kappa) * (1.0 + 8.0 * kappa));
+        for (int k = 0; k < P.smooth; k++) {
+          NCK(full_op(WD_F32, 12, gp, y, x, kappa, g, st));
+          NCK(full_op(WD_F32, 12, gp, dl, y, kappa, g, st, nullptr, true));
+          NCK(axpby(-wd, dl, 1.0, x, g, WD_F32, 2, st));
+        }
+      }
       NCK(full_op(WD_F32, 12, gp, b, x, kappa, g, st));                    // b = D x
       NCK(nn_forward(g, gp, W, b, y, B, flag, st));                        // y = N(b)
       NCK(axpby(1.0, y, 0.0, dl, g, WD_F32, 2, st));                       // dl = y

@@ -41,7 +41,7 @@ EXPORTS = [
     "wd_dslash_ex_noalloc", "wd_dslash_mrhs", "wd_solve_batch", "wd_gauge_fix_temporal",
     "wd_rotate_spinor", "wd_tc_gemm_bf16", "wd_nn_train_params_default", "wd_nn_init",
     "wd_nn_apply", "wd_nn_train", "wd_solve_fgcr", "wd_nn_layer", "wd_gaussian_spinor",
-    "wd_nn_wgrad",
+    "wd_nn_wgrad", "wd_set_autotune", "wd_mrhs_set_lanes", "wd_tune_report",
 ]
 
 WD_NN_PARAMS = 2304
@@ -70,7 +70,8 @@ class wd_batch_problem(C.Structure):
 
 class wd_nn_train_params(C.Structure):
     _fields_ = [("samples", C.c_int), ("batch", C.c_int), ("epochs", C.c_int),
-                ("lr", C.c_float), ("seed", C.c_ulonglong), ("init", C.c_int)]
+                ("lr", C.c_float), ("seed", C.c_ulonglong), ("init", C.c_int),
+                ("smooth", C.c_int)]
 
 
 class wd_nn_train_info(C.Structure):
@@ -141,6 +142,9 @@ def lib():
         "wd_rotate_spinor": (C.c_int, [dp, dp, dp, i4, C.c_int]),
         "wd_dslash_mrhs": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
                                      C.c_int, dp, i4, C.c_int, C.c_int]),
+        "wd_set_autotune": (C.c_int, [C.c_int]),
+        "wd_mrhs_set_lanes": (C.c_int, [C.c_int]),
+        "wd_tune_report": (C.c_int, [C.c_char_p, C.c_size_t]),
         "wd_solve_batch": (C.c_int, [C.POINTER(wd_batch_problem), C.c_int,
                                      C.POINTER(wd_solve_params), C.POINTER(wd_solve_info)]),
         "wd_norm2": (C.c_int, [dp, vp, i4, C.c_int, C.c_int]),
@@ -267,6 +271,26 @@ def wd_dslash_mrhs(out, inp, gauge, parity, dagger, a, x, bx, nrhs, norm2, dims,
     _ck(lib().wd_dslash_mrhs(_p(out), _p(inp), _p(gauge), int(parity), int(dagger), float(a),
                              _p(x), float(bx), int(nrhs), _p(norm2), _d(dims), int(prec),
                              int(recon)), "wd_dslash_mrhs")
+
+
+def wd_set_autotune(enable):
+    """Turn the multi-RHS tile-shape autotuner on or off; returns the previous
+    setting."""
+    return int(lib().wd_set_autotune(int(enable)))
+
+
+def wd_mrhs_set_lanes(lanes):
+    """Force the multi-RHS tile shape (1, 2, 4, 8 right-hand sides per CTA) or
+    return to the tuned shapes (0)."""
+    _ck(lib().wd_mrhs_set_lanes(int(lanes)), "wd_mrhs_set_lanes")
+
+
+def wd_tune_report():
+    """(number of tuned shapes, text table)."""
+    n = int(lib().wd_tune_report(None, 0))
+    buf = C.create_string_buffer(256 * (n + 1))
+    n = int(lib().wd_tune_report(buf, len(buf)))
+    return n, buf.value.decode()
 
 
 def wd_solve_batch(problems, params=None, check=True):

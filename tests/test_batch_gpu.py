@@ -56,6 +56,82 @@ def test_mrhs_dslash_matches_oracle(dims, prec, recon, dagger):
         assert abs(nrm[r].item() - n2) <= NORM_TOL[prec] * n2
 
 
+def _mrhs_run(dims, prec, recon, nrhs, dagger=0):
+    U = fields.su3_links(dims, workers=1)
+    g = pack_gauge(U, dims, prec, recon)
+    srcs = [oracle.restrict(fields.gaussian_spinor(dims, seed=700 + r), dims, 1)
+            for r in range(nrhs)]
+    xs = [oracle.restrict(fields.gaussian_spinor(dims, seed=800 + r), dims, 0)
+          for r in range(nrhs)]
+    inp, h = pack_many(srcs, dims, 1, prec)
+    out, _ = pack_many(xs, dims, 0, prec)
+    nrm = torch.zeros(nrhs, dtype=torch.float64, device="cuda")
+    W.wd_dslash_mrhs(out, inp, g, 0, dagger, -0.13, out, 1.0, nrhs, nrm, dims, prec, recon)
+    torch.cuda.synchronize()
+    return out, nrm, h, U, srcs, xs
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 8])
+@pytest.mark.parametrize("prec,recon", [(W.WD_F64, 18), (W.WD_F32, 12), (W.WD_F16, 12)])
+def test_mrhs_every_tile_shape(lanes, prec, recon):
+    """Every tile shape the autotuner may choose gives bit-identical fields and
+    norms to the default shape (each thread computes one right-hand side of one
+    site the same way), and both match the oracle; 6x4x4x6 has a ragged last
+    tile and nrhs = 7 leaves idle lanes for lanes = 2, 8."""
+    dims, nrhs = (6, 4, 4, 6), 7
+    try:
+        W.wd_mrhs_set_lanes(4)
+        ref, nref, h, U, srcs, xs = _mrhs_run(dims, prec, recon, nrhs, dagger=1)
+        W.wd_mrhs_set_lanes(lanes)
+        got, ngot, _, _, _, _ = _mrhs_run(dims, prec, recon, nrhs, dagger=1)
+    finally:
+        W.wd_mrhs_set_lanes(0)
+    # compare the stored sites (the FP16 half field has pad bytes after its
+    # scales that no kernel writes)
+    assert torch.equal(nref, ngot)
+    for r in range(nrhs):
+        g = unpack_spinor(got[r * h:(r + 1) * h], dims, 0, prec)
+        assert np.array_equal(g, unpack_spinor(ref[r * h:(r + 1) * h], dims, 0, prec))
+        want = -0.13 * oracle.hop_block(0, srcs[r], U, dims, dagger=True) + xs[r]
+        assert rel_l2(g, want) <= PREC_TOL[prec]
+
+
+def test_mrhs_set_lanes_rejects_other_shapes():
+    with pytest.raises(W.WdError):
+        W.wd_mrhs_set_lanes(3)
+
+
+def test_autotuner_times_every_shape_and_leaves_outputs_alone():
+    """A new batch shape is timed with all four tile shapes on temporary
+    outputs: the caller's output equals the untuned (default-shape) result
+    exactly, and the report lists the shape with four timings and a choice."""
+    dims, prec, nrhs = (8, 4, 6, 10), W.WD_F32, 6
+    prev = W.wd_set_autotune(0)
+    try:
+        W.wd_mrhs_set_lanes(4)
+        ref, nref, h, _, _, _ = _mrhs_run(dims, prec, 12, nrhs)
+        W.wd_mrhs_set_lanes(0)
+        W.wd_set_autotune(1)
+        got, ngot, _, _, _, _ = _mrhs_run(dims, prec, 12, nrhs)
+    finally:
+        W.wd_mrhs_set_lanes(0)
+        W.wd_set_autotune(prev)
+    assert torch.equal(nref, ngot)
+    for r in range(nrhs):
+        assert np.array_equal(unpack_spinor(got[r * h:(r + 1) * h], dims, 0, prec),
+                              unpack_spinor(ref[r * h:(r + 1) * h], dims, 0, prec))
+    n, text = W.wd_tune_report()
+    assert n >= 1
+    tiles = (int(np.prod(dims)) // 2 + 127) // 128
+    mine = [l for l in text.splitlines()
+            if f"tiles={tiles} " in l and f"maxrhs={nrhs} " in l and "norm=1" in l]
+    assert len(mine) == 1, text
+    us = [float(v) for v in mine[0].split("us[1,2,4,8]=")[1].split()[0].split(",")]
+    assert all(v > 0 for v in us)
+    lanes = int(mine[0].split("lanes=")[1])
+    assert lanes in (1, 2, 4, 8) and us[[1, 2, 4, 8].index(lanes)] == min(us)
+
+
 def test_mrhs_agrees_with_single_rhs_kernel():
     """The multi-RHS kernel and the single-field kernel agree to FP32 rounding."""
     dims, prec = (8, 8, 8, 8), W.WD_F32
