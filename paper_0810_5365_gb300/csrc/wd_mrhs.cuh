@@ -57,9 +57,17 @@ constexpr int MRHS_SUB = 32;    // sites per CTA
 // The tile shape is a template parameter (1, 2, 4 or 8 right-hand-side warps
 // per CTA) chosen per batch shape by the autotuner; the register budget per
 // thread is the single-field kernel's for every shape.
+#ifndef WD_MRHS_MINB_F32_NORM
+#define WD_MRHS_MINB_F32_NORM WD_DSLASH_MINB_F32_NORM
+#endif
+template <int P, bool NORM>
+struct MrhsMinBlocks4 {  // CTAs per SM the budget is sized for, at 4 lanes
+  static constexpr int value =
+      (P == WD_F32 && NORM) ? WD_MRHS_MINB_F32_NORM : DslashMinBlocks<P, NORM>::value;
+};
 template <int P, bool NORM, int LANES>
 struct MrhsMinBlocks {
-  static constexpr int raw = DslashMinBlocks<P, NORM>::value * MRHS_LANES / LANES;
+  static constexpr int raw = MrhsMinBlocks4<P, NORM>::value * MRHS_LANES / LANES;
   static constexpr int value = raw < 1 ? 1 : (raw > 32 ? 32 : raw);
 };
 
