@@ -125,6 +125,47 @@ __device__ __forceinline__ void project_h2(const __half2 (&p)[12], __half2 (&h)[
   }
 }
 
+#ifndef WD_F32X2
+#define WD_F32X2 1
+#endif
+#if WD_F32X2
+// t = U h (FWD) or U^+ h for both half-spinor rows at once with packed
+// two-wide FP32 FMAs: each link element multiplies row 0 and row 1, so the
+// rows are the two lanes (real parts in one pair, imaginary in the other).
+template <bool FWD>
+__device__ __forceinline__ void su3_mul_f32x2(const cx<float> (&u)[9], const cx<float> (&h)[6],
+                                              cx<float> (&t)[6]) {
+  float2 hr[3], hi[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    hr[d] = make_float2(h[d].r, h[3 + d].r);
+    hi[d] = make_float2(h[d].i, h[3 + d].i);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float2 tr = make_float2(0.f, 0.f), ti = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const cx<float> e = FWD ? u[c * 3 + d] : u[d * 3 + c];
+      const float2 er = make_float2(e.r, e.r);
+      const float2 ei = make_float2(e.i, e.i);
+      const float2 en = make_float2(-e.i, -e.i);
+      tr = __ffma2_rn(er, hr[d], tr);
+      ti = __ffma2_rn(er, hi[d], ti);
+      if (FWD) {  // (e.r + i e.i)(h.r + i h.i)
+        tr = __ffma2_rn(en, hi[d], tr);
+        ti = __ffma2_rn(ei, hr[d], ti);
+      } else {    // (e.r - i e.i)(h.r + i h.i)
+        tr = __ffma2_rn(ei, hi[d], tr);
+        ti = __ffma2_rn(en, hr[d], ti);
+      }
+    }
+    t[c] = mk<float>(tr.x, ti.x);
+    t[3 + c] = mk<float>(tr.y, ti.y);
+  }
+}
+#endif
+
 // Load the neighbour spinor and project it: h receives the half spinor, the
 // return value the factor still to apply (the FP16 site scale, else 1).
 template <int P, int MU, int S, typename R>
@@ -176,19 +217,26 @@ __device__ __forceinline__ void hop(cx<R> (&acc)[12], const void* __restrict__ i
   } else {
     cx<R> u[9];
     load_link<P, RC, R>(u, gauge, region, lcb, Vh_pad);
+#if WD_F32X2
+    if constexpr (P == WD_F32) {
+      su3_mul_f32x2<FWD>(u, h, t);
+    } else
+#endif
+    {
 #pragma unroll
-    for (int hs = 0; hs < 2; hs++) {
+      for (int hs = 0; hs < 2; hs++) {
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        cx<R> v = mk<R>(0, 0);
+        for (int c = 0; c < 3; c++) {
+          cx<R> v = mk<R>(0, 0);
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-          if (FWD)
-            v = cmadd(u[c * 3 + d], h[hs * 3 + d], v);
-          else
-            v = cjmadd(u[d * 3 + c], h[hs * 3 + d], v);
+          for (int d = 0; d < 3; d++) {
+            if (FWD)
+              v = cmadd(u[c * 3 + d], h[hs * 3 + d], v);
+            else
+              v = cjmadd(u[d * 3 + c], h[hs * 3 + d], v);
+          }
+          t[hs * 3 + c] = v;
         }
-        t[hs * 3 + c] = v;
       }
     }
   }
