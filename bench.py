@@ -181,10 +181,37 @@ def cpu_baseline(U, psi, dims, budget_s=12.0):
         oracle.hop(psi, U, dims, dagger=False, out_parity=0)
         t += time.perf_counter() - t0
         n += 1
-    return {"value": FLOPS_PER_SITE * Vh * n / t / 1e9, "unit": "Gflops",
-            "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{n} full even-parity applications of the FP64 oracle hopping term "
-                      f"on the 32^3x64 fields ({t:.1f} s)"}
+    out = {"value": FLOPS_PER_SITE * Vh * n / t / 1e9, "unit": "Gflops",
+           "cores": oracle.get_threads(), "kind": "oracle",
+           "sample": f"{n} full even-parity applications of the FP64 oracle hopping term "
+                     f"on the 32^3x64 fields ({t:.1f} s)"}
+    # one thread, on a slice of the same fields (every 128th site)
+    sites = np.arange(0, Vh * 2, 128)
+    oracle.set_threads(1)
+    n1, t1 = 0, 0.0
+    while t1 < 2.0:
+        t0 = time.perf_counter()
+        oracle.hop_sites(psi, U, dims, sites)
+        t1 += time.perf_counter() - t0
+        n1 += 1
+    oracle.set_threads(cores)
+    out["single_thread_gflops"] = FLOPS_PER_SITE * len(sites) * n1 / t1 / 1e9
+    return out
+
+
+def oracle_cg_estimate(budget_iters=4):
+    """Plain FP64 CG of the oracle on the 24^3x48 solve problem, estimated:
+    the time of a few iterations (two D applications each, all host cores)
+    times the iteration count the GPU's plain FP64 CG needs."""
+    import oracle
+    from synth import fields
+    oracle.set_threads(os.cpu_count() or 1)
+    U = fields.su3_links(SOLVE_DIMS)
+    b = fields.gaussian_spinor(SOLVE_DIMS, seed=2025)
+    t0 = time.perf_counter()
+    _, its, _, _ = oracle.cgnr(b, U, SOLVE_DIMS, SOLVE_KAPPA, 1e-10, budget_iters)
+    dt = time.perf_counter() - t0
+    return dt / max(its, 1)
 
 
 def run_reference(args, rank, world):
@@ -247,6 +274,38 @@ def time_dslash(W, torch, prec_id, recon, gauge, bufs, dims, steps, warmup, stre
         step(k)
     e1.record(stream)
     e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def time_dslash_graph(W, torch, gauge, bufs, dims, steps):
+    """The same K back-to-back FP32 launches captured once as a CUDA graph and
+    replayed (one host launch for all K).  Returns elapsed seconds."""
+    a, b = bufs
+    cap = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    W.wd_set_stream(cap)
+    try:
+        with torch.cuda.graph(graph, stream=cap):
+            for k in range(steps):
+                if k & 1:
+                    W.wd_dslash_ex(a, b, gauge, W.WD_ODD, 0, -KAPPA, None, 0.0, None, 0.0, None,
+                                   dims, W.WD_F32, 12)
+                else:
+                    W.wd_dslash_ex(b, a, gauge, W.WD_EVEN, 0, -KAPPA, None, 0.0, None, 0.0,
+                                   None, dims, W.WD_F32, 12)
+    finally:
+        W.wd_set_stream(torch.cuda.current_stream())
+    graph.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    e0.record(st)
+    graph.replay()
+    e1.record(st)
+    e1.synchronize()
+    del graph
     return e0.elapsed_time(e1) / 1e3
 
 
@@ -676,6 +735,9 @@ def run_ours(args, rank, world, local):
                 dt = max_over_ranks(dt, "cuda")
             results[name] = (dt, steps)
             del g, a, b
+        # the headline launches once more, captured as one CUDA graph
+        g32, a32, b32, _ = gauges["f32"]
+        dt_graph = time_dslash_graph(W, torch, g32, (a32, b32), dims, args.steps)
         # end to end through the C ABI with pinned host buffers: every step
         # copies its input spinor in, applies the operator and copies the
         # result out.  Three streams and two device buffer pairs let step
@@ -753,7 +815,11 @@ def run_ours(args, rank, world, local):
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "traffic": profiled_traffic("f32"),
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                     "bytes_per_site": BYTES_PER_SITE["f32"]},
+                     "bytes_per_site": BYTES_PER_SITE["f32"],
+                     "frac_of_nominal_8tbs": achieved / 8000.0},
+        "graph": {"ms_per_step": 1e3 * dt_graph / args.steps,
+                  "value": FLOPS_PER_SITE * Vh * args.steps * world / dt_graph / 1e9,
+                  "unit": "Gflops", "note": "the same launches captured as one CUDA graph"},
         "gpu_launches": steps,
         "variants": {},
     }
@@ -777,7 +843,7 @@ def run_ours(args, rank, world, local):
                    "steps": k_e2e, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
                    "overlap": "3 streams, 2 device buffer pairs: step k+1's input copy and "
                               "step k-1's output copy run under step k's kernel"}
-    line["gpu_launches"] += k_e2e
+    line["gpu_launches"] += k_e2e + args.steps  # e2e steps and the graph replay
     line["clocks"] = clocks
     if not args.no_solve and not args.quick:
         line["solve"] = solve_section(W, torch)
@@ -788,6 +854,16 @@ def run_ours(args, rank, world, local):
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(U, psi, dims)
+        if "solve" in line:
+            # plain FP64 CG of the oracle (full system, 2 D applications per
+            # iteration), per iteration, and scaled to the iteration count of
+            # the GPU's plain FP64 CG at the same kappa: an estimate
+            spi = oracle_cg_estimate()
+            its = line["solve"]["f64"]["iters"]
+            line["cpu_baseline"]["oracle_cg_24x24x24x48"] = {
+                "s_per_iteration": spi, "estimated_s": spi * its, "iterations_assumed": its,
+                "kind": "estimate: oracle CGNR time per iteration x GPU plain FP64 CG "
+                        "iterations", "gpu_plain_f64_cg_s": line["solve"]["f64"]["wall_s"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
