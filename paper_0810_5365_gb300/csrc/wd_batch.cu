@@ -606,7 +606,8 @@ void convert_b(const BlasBatch& b, const int* active, int grid, cudaStream_t st)
   batch_convert<PD, PS><<<grid, MRHS_BS, 0, st>>>(b, active);
 }
 
-cudaError_t batch_reliable_update(BatchCtx& c, const Plan& pl, bool accumulate, cudaStream_t st) {
+cudaError_t batch_reliable_update(BatchCtx& c, const Plan& pl, bool accumulate, cudaStream_t st,
+                                  bool x_is_zero = false) {
   RedScratch rs = scratch();
   const int grid = blas_grid_tiles(pl.ntiles);
   cudaError_t e;
@@ -617,9 +618,26 @@ cudaError_t batch_reliable_update(BatchCtx& c, const Plan& pl, bool accumulate, 
       batch_ru_accumulate<WD_F32><<<grid, MRHS_BS, 0, st>>>(pl.ru, c.active);
     if ((e = cudaGetLastError())) return e;
   }
-  c.dslash_calls += 4;
-  if ((e = launch_mrhs(WD_F64, pl.r_t64, c.orecon, false, c.active, rs, nullptr, st))) return e;
-  if ((e = launch_mrhs(WD_F64, pl.r_r64, c.orecon, false, c.active, rs, c.sc.r64, st))) return e;
+  if (x_is_zero) {
+    // a start from x = 0: r64 = bhat exactly, no FP64 operator needed
+    c.dslash_calls += 2;
+    for (int j = 0; j < pl.r_r64.nprob; j++) {
+      const MrhsProblem& m = pl.r_r64.p[j];
+      const char* bh = (const char*)m.y;  // bhat of this problem (rhs stride s_y)
+      if ((e = cudaMemcpyAsync(m.out, bh, (size_t)m.nrhs * m.s_out, cudaMemcpyDeviceToDevice,
+                               st)))
+        return e;
+      for (int r = 0; r < m.nrhs; r++)
+        if ((e = norm2(c.sc.r64 + m.rhs0 + r, (const char*)m.out + (size_t)r * m.s_out, m.g,
+                       WD_F64, 1, st)))
+          return e;
+    }
+  } else {
+    c.dslash_calls += 4;
+    if ((e = launch_mrhs(WD_F64, pl.r_t64, c.orecon, false, c.active, rs, nullptr, st))) return e;
+    if ((e = launch_mrhs(WD_F64, pl.r_r64, c.orecon, false, c.active, rs, c.sc.r64, st)))
+      return e;
+  }
   switch (c.sprec) {
     case WD_F64: convert_b<WD_F64, WD_F64>(pl.cvt_r, c.active, grid, st); break;
     case WD_F32: convert_b<WD_F32, WD_F64>(pl.cvt_r, c.active, grid, st); break;
@@ -789,7 +807,7 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
     c.dslash_calls += 1;
     WD_BCK(launch_mrhs(WD_F64, pl.bhat, c.orecon, false, c.active, rs, nullptr, st));
   }
-  WD_BCK(batch_reliable_update(c, pl, false, st));
+  WD_BCK(batch_reliable_update(c, pl, false, st, !P.use_initial_guess));
   auto read_scal = [&]() -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(c.scal_h, c.scal, 8 * (size_t)nr * sizeof(double),
                                     cudaMemcpyDeviceToHost, st);

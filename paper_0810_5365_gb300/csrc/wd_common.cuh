@@ -435,12 +435,33 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[N], RedScratch rs, doubl
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // CH independent chains per thread keep CH loads of the partials in flight
+  // (a single chain waits one L2 round trip per partial); the chains are
+  // combined in a fixed order, so the sum does not depend on scheduling
+  constexpr int CH = N == 1 ? 8 : (N <= 4 ? 4 : 1);
+  double part[CH][N];
+#pragma unroll
+  for (int c = 0; c < CH; c++)
+#pragma unroll
+    for (int j = 0; j < N; j++) part[c][j] = 0.0;
+  int b = threadIdx.x;
+  for (; b + (CH - 1) * BS < (int)gridDim.x; b += CH * BS) {
+#pragma unroll
+    for (int c = 0; c < CH; c++)
+#pragma unroll
+      for (int j = 0; j < N; j++) part[c][j] += __ldcg(rs.partials + (size_t)(b + c * BS) * N + j);
+  }
+  for (; b < (int)gridDim.x; b += BS) {
+#pragma unroll
+    for (int j = 0; j < N; j++) part[0][j] += __ldcg(rs.partials + (size_t)b * N + j);
+  }
   double acc[N];
 #pragma unroll
-  for (int j = 0; j < N; j++) acc[j] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += BS) {
+  for (int j = 0; j < N; j++) {
+    double t = part[0][j];
 #pragma unroll
-    for (int j = 0; j < N; j++) acc[j] += __ldcg(rs.partials + (size_t)b * N + j);
+    for (int c = 1; c < CH; c++) t += part[c][j];
+    acc[j] = t;
   }
   __syncthreads();
   block_sum<N, BS>(acc, smem);

@@ -473,8 +473,9 @@ cudaError_t iteration(Ctx& c, int kp, cudaStream_t st) {
 }
 
 // fold xs into x64 (even half), recompute r64 = bhat - Mhat x64 in FP64, and
-// restart the sloppy recurrences: r = r64, s = Mhat^+ r, p = s, gamma[0] = ||s||^2
-cudaError_t reliable_update(Ctx& c, bool accumulate, cudaStream_t st) {
+// restart the sloppy recurrences: r = r64, s = Mhat^+ r, p = s, gamma[0] = ||s||^2.
+// x_is_zero (a start from x = 0): r64 = bhat exactly, no FP64 operator needed.
+cudaError_t reliable_update(Ctx& c, bool accumulate, cudaStream_t st, bool x_is_zero = false) {
   Workspace& w = *c.w;
   const Geom& g = w.g;
   cudaError_t e;
@@ -486,13 +487,19 @@ cudaError_t reliable_update(Ctx& c, bool accumulate, cudaStream_t st) {
       ru_accumulate<WD_F32, 256><<<grid, 256, 0, st>>>((char*)w.x64, (char*)w.xs, g);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // t64 = H_oe x64_e ; r64 = kappa^2 H_eo t64 - x64_e + bhat
-  e = dsl(c, WD_F64, c.orecon, w.g64, w.t64, w.x64, WD_ODD, 0, 1.0, nullptr, 0, nullptr, 0,
-          nullptr, st);
-  if (e != cudaSuccess) return e;
-  e = dsl(c, WD_F64, c.orecon, w.g64, w.r64, w.t64, WD_EVEN, 0, c.kappa * c.kappa, w.x64, -1.0,
-          w.bhat, 1.0, &w.sc->r64, st);
-  if (e != cudaSuccess) return e;
+  if (x_is_zero) {
+    e = cudaMemcpyAsync(w.r64, w.bhat, spinor_half_bytes(g, WD_F64), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if ((e = norm2(&w.sc->r64, w.r64, g, WD_F64, 1, st)) != cudaSuccess) return e;
+  } else {
+    // t64 = H_oe x64_e ; r64 = kappa^2 H_eo t64 - x64_e + bhat
+    e = dsl(c, WD_F64, c.orecon, w.g64, w.t64, w.x64, WD_ODD, 0, 1.0, nullptr, 0, nullptr, 0,
+            nullptr, st);
+    if (e != cudaSuccess) return e;
+    e = dsl(c, WD_F64, c.orecon, w.g64, w.r64, w.t64, WD_EVEN, 0, c.kappa * c.kappa, w.x64,
+            -1.0, w.bhat, 1.0, &w.sc->r64, st);
+    if (e != cudaSuccess) return e;
+  }
   if ((e = convert_spinor(w.r, c.sprec, w.r64, WD_F64, g, 1, st)) != cudaSuccess) return e;
   if (c.bicg) {
     // restart BiCGstab: r0 = r, p = v = 0, rho = ||r||^2
@@ -602,7 +609,7 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
   // bhat_e = b_e + kappa H_eo b_o
   WD_CK(dsl(c, WD_F64, c.orecon, w.g64, w.bhat, b_o, WD_EVEN, 0, kappa, b_e, 1.0, nullptr, 0,
             nullptr, st));
-  WD_CK(reliable_update(c, false, st));
+  WD_CK(reliable_update(c, false, st, !P.use_initial_guess));
   WD_CK(read_scalars(c));
   int ru = 0;
   const double bnorm = std::sqrt(w.sc_host->bnorm2);
