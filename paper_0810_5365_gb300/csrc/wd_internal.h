@@ -26,7 +26,7 @@ namespace wd {
 #define WD_DSLASH_MINB_F32_NORM 6
 #endif
 #ifndef WD_DSLASH_MINB_F16
-#define WD_DSLASH_MINB_F16 5
+#define WD_DSLASH_MINB_F16 6
 #endif
 constexpr int DSLASH_BS = WD_DSLASH_BS;
 // (the fused-norm FP32 variant needs 80 registers to stay free of spills)

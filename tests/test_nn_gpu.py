@@ -199,3 +199,34 @@ def test_training_lowers_loss_and_trained_network_preconditions():
     res = W.wd_solve_fgcr(x, b, U, kappa, dims, w, 10)
     r = np.linalg.norm(b - oracle.apply_D(x, U, dims, kappa)) / np.linalg.norm(b)
     assert res["status"] == W.WD_OK and r <= 1.05e-10
+
+
+def test_training_with_damped_samples():
+    """smooth = k damps every other training vector k times with
+    x <- x - w D^+ D x before the pair (D x, x) is formed; training still runs
+    to finite, decreasing losses and the network still preconditions."""
+    dims, kappa = (4, 4, 4, 8), 0.13
+    U = fields.su3_links(dims, workers=1)
+    # from the identity network (the series start is already near its best)
+    Ws = [np.zeros((9, 8, 4), complex), np.zeros((9, 8, 8), complex), np.zeros((9, 4, 8), complex)]
+    for Wl in Ws:
+        for o in range(min(Wl.shape[1], Wl.shape[2])):
+            Wl[0, o, o] = 1
+    w = torch.from_numpy(nn.join_weights(Ws)).cuda()
+    p = W.wd_nn_train_params_default()
+    p.init = 0
+    p.samples = 512
+    p.batch = 8
+    p.epochs = 2
+    p.smooth = 4
+    info = W.wd_nn_train(w, U, kappa, dims, p)
+    assert np.isfinite(info["loss_first"]) and np.isfinite(info["loss_last"])
+    assert info["loss_last"] < 0.8 * info["loss_first"], info
+    b = fields.gaussian_spinor(dims, seed=63)
+    x = np.zeros_like(b)
+    res = W.wd_solve_fgcr(x, b, U, kappa, dims, w, 10)
+    r = np.linalg.norm(b - oracle.apply_D(x, U, dims, kappa)) / np.linalg.norm(b)
+    assert res["status"] == W.WD_OK and r <= 1.05e-10
+    p.smooth = -1
+    with pytest.raises(W.WdError):
+        W.wd_nn_train(w, U, kappa, dims, p)
