@@ -6,8 +6,8 @@
 // iterations, FP64 reliable updates every `reliable_interval` iterations).
 // What changes is the execution: every step of an iteration is ONE launch
 // over all problems and right-hand sides (the multi-RHS hopping kernel of
-// wd_mrhs.cuh reuses each staged link across the right-hand sides of its
-// problem; the BLAS steps walk the same tile list), CG scalars are per
+// wd_mrhs.cuh reads each link from HBM once for all the right-hand sides of
+// its problem; the BLAS steps walk the same tile list), CG scalars are per
 // right-hand side on the device, a convergence mask switches finished
 // right-hand sides off, and each block of `check_interval` iterations is one
 // captured CUDA graph.

@@ -3,10 +3,12 @@
 // A batch is a list of problems (lattice geometry, gauge field, nrhs fields);
 // the problems may have different lattice sizes.  Their sites of one parity
 // are cut into tiles of MRHS_BS checkerboard sites and all tiles of all
-// problems form one launch.  The four warps of a CTA apply the hopping term to
-// different right-hand sides of the same 32 sites at the same time, so each
-// link crosses HBM once per site instead of once per site and right-hand side
-// (the repeats are served by L1/L2).  Per right-hand side the epilogue is the one of the
+// problems form one launch.  The warps of a CTA (1, 2, 4 or 8, chosen by the
+// autotuner) apply the hopping term to different right-hand sides of the same
+// 32 sites, and the CTAs covering the other right-hand sides of those sites
+// are adjacent in launch order, so each link crosses HBM once per site instead
+// of once per site and right-hand side (the repeats are served by L1/L2).
+// Per right-hand side the epilogue is the one of the
 // single-field kernel (out = a H in + bx x + cy y), optionally with ||out||^2
 // reduced deterministically per right-hand side (per-sub-tile partials here,
 // their fixed-order sum in sum_partials_kernel).
@@ -44,13 +46,13 @@ struct MrhsBatch {
   MrhsProblem p[MRHS_MAX_PROBLEMS];
 };
 
-// One CTA = 32 sites x 4 right-hand-side lanes (one warp per right-hand
-// side).  Block b covers sub-tile b / G and right-hand sides 4 (b % G) .. +3,
-// G = ceil(max nrhs / 4): the G blocks of a sub-tile are adjacent in launch
-// order, run together, and read the same links, which L1/L2 then return once
-// per site for all right-hand sides.  Each thread computes one right-hand
-// side of one site, so the kernel keeps the registers (and occupancy) of the
-// single-field kernel.
+// One CTA = 32 sites x L right-hand-side lanes (one warp per right-hand
+// side).  Block b covers sub-tile b / G and right-hand sides L (b % G) ..
+// L (b % G) + L - 1, G = ceil(max nrhs / L): the G blocks of a sub-tile are
+// adjacent in launch order, run together, and read the same links, which
+// L1/L2 then return once per site for all right-hand sides.  Each thread
+// computes one right-hand side of one site, so the kernel keeps the registers
+// (and occupancy) of the single-field kernel.
 constexpr int MRHS_LANES = 4;   // default right-hand-side lanes (warps) per CTA
 constexpr int MRHS_SUB = 32;    // sites per CTA
 
