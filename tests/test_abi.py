@@ -117,3 +117,29 @@ def test_product_path_has_no_oracle_or_fallback():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower() or f == "build.py", f
                 assert "import synth" not in text and "from synth" not in text, f
+
+
+def test_stream_and_error_state_roundtrip(W):
+    """wd_set_stream / wd_get_stream keep the handle they were given, and
+    wd_last_cuda_error starts at 0 (host state only; no CUDA call)."""
+    prev = W.wd_get_stream()
+    W.wd_set_stream(0x1234)
+    assert W.wd_get_stream() == 0x1234
+    W.wd_set_stream(prev)
+    assert W.wd_get_stream() == prev
+    assert W.wd_last_cuda_error() == 0
+
+
+def test_tuner_controls_on_host(W):
+    """The autotuner switches and report answer on the host: the setting
+    round-trips, only 0, 1, 2, 4, 8 lanes are accepted, and an empty table
+    reports no shapes."""
+    prev = W.wd_set_autotune(0)
+    assert W.wd_set_autotune(prev) == 0
+    for lanes in (1, 2, 4, 8, 0):
+        W.wd_mrhs_set_lanes(lanes)
+    for bad in (-1, 3, 16):
+        with pytest.raises(W.WdError):
+            W.wd_mrhs_set_lanes(bad)
+    n, text = W.wd_tune_report()
+    assert n == 0 and text == ""
