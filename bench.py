@@ -4,8 +4,8 @@ One step = one parity-restricted hopping application (Dslash of the paper's
 section "Wilson inverter: Main features") over the V/2 = 1,048,576 sites of
 one parity, FP32 with 12-real links (the headline), alternating the output
 parity each step.  Effective Gflops use the nominal 1320 flops per site
-(reconstruction work not counted, as in the paper's "effective gigaflops",
-section "Performance").  The FP16 (per-site scale) variant is timed too.
+(reconstruction work not counted, as the paper counts its effective
+Gflops, section "Performance").  The FP16 (per-site scale) variant is timed too.
 
 Contract: one JSON line on rank 0 with metric/value/unit, roofline (HBM),
 cpu_baseline (the FP64 oracle on the host cores), e2e (through the C ABI with

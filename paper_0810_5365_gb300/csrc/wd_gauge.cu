@@ -1,4 +1,4 @@
-// Temporal gauge fixing (the paper's "gauge-fixing trick", section
+// Temporal gauge fixing (the paper's gauge-fixing variant, section
 // "Performance": the temporal links are fixed to the identity on all but one
 // time slice, which saves their memory traffic in the hopping term).
 //

@@ -25,7 +25,7 @@ def header_functions():
     return sorted(set(re.findall(r"\b(wd_[a-z0-9_]+)\s*\(", text)))
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_dslash_and_solve_calls():
     fns = header_functions()
     for name in ("wd_dslash", "wd_solve", "wd_dslash_dag", "wd_solve_ex", "wd_pack_gauge",
                  "wd_pack_spinor", "wd_unpack_spinor", "wd_set_stream", "wd_finalize"):
