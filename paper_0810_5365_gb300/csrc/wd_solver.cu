@@ -269,6 +269,14 @@ struct Workspace {
   CgScalars* sc = nullptr;
   CgScalars* sc_host = nullptr;    // pinned
   cudaStream_t cap = nullptr;      // private capture stream
+  // the instantiated iteration graph of the last solve, reused by the next
+  // solve on this workspace with the same key (its kernels hold workspace
+  // pointers, kappa and the reduction scratch by value)
+  cudaGraphExec_t exec = nullptr;
+  double ex_kappa = 0.0;
+  int ex_chunk = 0, ex_tg = -1, ex_bicg = -1;
+  const void* ex_partials = nullptr;
+  const void* ex_counter = nullptr;
 };
 
 static Workspace& ws() {
@@ -278,6 +286,8 @@ static Workspace& ws() {
 
 static void ws_free() {
   Workspace& w = ws();
+  if (w.exec) cudaGraphExecDestroy(w.exec);
+  w.exec = nullptr;
   void* bufs[] = {w.g64, w.b64, w.x64, w.rf64, w.bhat, w.r64, w.t64, w.p, w.q, w.r,
                   w.s, w.ts, w.t, w.r0, w.xs, w.canon_spinor, w.canon_gauge, w.sc,
                   w.gf_gauge, w.gf_omega, w.gf_spinor};
@@ -625,7 +635,13 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
   WD_CK(cudaStreamSynchronize(st));
   // ---- the iteration graph ----
   cudaGraphExec_t exec = nullptr;
-  if (P.use_graph) {
+  const RedScratch rsk = scratch();
+  if (P.use_graph && w.exec && w.ex_kappa == kappa && w.ex_chunk == chunk && w.ex_tg == c.tg &&
+      w.ex_bicg == c.bicg && w.ex_partials == rsk.partials && w.ex_counter == rsk.counter) {
+    exec = w.exec;  // the same workspace, parameters and scratch: reuse
+  } else if (P.use_graph) {
+    if (w.exec) cudaGraphExecDestroy(w.exec);
+    w.exec = nullptr;
     cudaGraph_t graph = nullptr;
     WD_CK(cudaStreamBeginCapture(w.cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
@@ -643,6 +659,13 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
       state().last_cuda_error = (int)ie;
       return WD_ERR_CUDA;
     }
+    w.exec = exec;
+    w.ex_kappa = kappa;
+    w.ex_chunk = chunk;
+    w.ex_tg = c.tg;
+    w.ex_bicg = c.bicg;
+    w.ex_partials = rsk.partials;
+    w.ex_counter = rsk.counter;
   }
 
   auto now = [] { return std::chrono::steady_clock::now(); };
@@ -722,7 +745,6 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
       if (r64 <= target) converged = true;
     }
   }
-  if (exec) cudaGraphExecDestroy(exec);
   const auto t_fin = now();
   I.reliable_seconds = t_ru;
   I.iterate_seconds = secs(t_loop, t_fin) - t_ru;
