@@ -143,3 +143,22 @@ def test_tuner_controls_on_host(W):
             W.wd_mrhs_set_lanes(bad)
     n, text = W.wd_tune_report()
     assert n == 0 and text == ""
+
+
+def test_batch_limits_rejected_on_host(W):
+    """wd_solve_batch takes 1..16 problems of 1..32 right-hand sides each;
+    anything else is WD_ERR_ARG before any CUDA call."""
+    import numpy as np
+    dims = (4, 4, 4, 4)
+    V = 256
+    U = np.zeros((4, V, 3, 3), dtype=np.complex128)
+
+    def prob(nrhs):
+        b = np.zeros((nrhs, V, 4, 3), dtype=np.complex128)
+        return {"dims": dims, "kappa": 0.12, "nrhs": nrhs, "gauge": U, "b": b,
+                "x": np.zeros_like(b)}
+
+    rc, _ = W.wd_solve_batch([prob(33)], check=False)
+    assert rc == W.WD_ERR_ARG
+    rc, _ = W.wd_solve_batch([prob(0 + 1)] * 17, check=False)
+    assert rc == W.WD_ERR_ARG

@@ -215,3 +215,29 @@ def test_batch_device_buffers():
     for r in range(2):
         rel = np.linalg.norm(b[r] - oracle.apply_D(x[r], U, dims, 0.13)) / np.linalg.norm(b[r])
         assert rel <= 1.05e-10
+
+
+def test_batch_at_its_limits():
+    """16 problems (the most a batch takes) of assorted shapes, one of them
+    with 32 right-hand sides (the most a problem takes): every solution meets
+    the oracle's true residual."""
+    r = np.random.default_rng(17)
+    shapes = [(4, 4, 4, 4), (2, 4, 2, 6), (6, 4, 4, 6), (4, 2, 4, 8), (2, 2, 2, 2),
+              (4, 6, 2, 4), (8, 4, 2, 4), (2, 6, 4, 4)]
+    probs, keep = [], []
+    for j in range(16):
+        dims = shapes[j % len(shapes)]
+        nrhs = 32 if j == 5 else int(r.integers(1, 4))
+        U = fields.su3_links(dims, seed=3000 + j, workers=1)
+        b = np.ascontiguousarray(np.stack([fields.gaussian_spinor(dims, seed=4000 + 40 * j + k)
+                                           for k in range(nrhs)]))
+        x = np.zeros_like(b)
+        probs.append({"dims": dims, "kappa": 0.125, "nrhs": nrhs, "gauge": U, "b": b, "x": x})
+        keep.append((dims, U, b, x))
+    p = W.wd_solve_params_default()
+    rc, infos = W.wd_solve_batch(probs, p)
+    assert rc == W.WD_OK and len(infos) == sum(pr["nrhs"] for pr in probs)
+    for dims, U, b, x in keep:
+        for k in range(b.shape[0]):
+            res = b[k] - oracle.apply_D(x[k], U, dims, 0.125)
+            assert np.linalg.norm(res) / np.linalg.norm(b[k]) <= 1.05e-10
