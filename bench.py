@@ -821,6 +821,9 @@ def run_ours(args, rank, world, local):
                   "value": FLOPS_PER_SITE * Vh * args.steps * world / dt_graph / 1e9,
                   "unit": "Gflops", "note": "the same launches captured as one CUDA graph"},
         "gpu_launches": steps,
+        "paper_context": {"tesla_c870_gflops": 68, "gtx280_gflops": 92,
+                          "note": "the paper's FP32 Wilson-Dirac operator on G80/GT200 cards, "
+                                  "lattice volume not stated: context, not the same workload"},
         "variants": {},
     }
     for name in ("f16", "f64", "f32_tg", "f16_tg"):
