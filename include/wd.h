@@ -301,6 +301,19 @@ int wd_axpby(double a, const void *x, double b, void *y, const int dims[4],
  */
 int wd_tc_gemm_bf16(float *D, const void *A, const void *B, int M, int K, int N);
 
+/*
+ * Failure-path check of the bounded device waits (no counterpart in the
+ * paper).  Every spin-wait in the library's kernels (the tensor-core kernels'
+ * mbarrier waits) polls at most a fixed number of times; when the polls run
+ * out the kernel raises a device flag, frees what it holds and returns, and
+ * the call reports WD_ERR_TIMEOUT with the context still usable.  This entry
+ * point runs that path on purpose: one warp waits, through the same bounded
+ * helper, on an mbarrier that nothing ever completes, for at most `spins`
+ * polls (1 <= spins <= 2^24, about 100 ns each).  It returns WD_ERR_TIMEOUT
+ * (the expected answer), WD_ERR_ARG for spins out of range.  Synchronous.
+ */
+int wd_wait_selftest(long long spins);
+
 /* ------------------------------------------------------------------ */
 /* solver (paper: even-odd preconditioned CG; Fig. 2)                  */
 /* ------------------------------------------------------------------ */

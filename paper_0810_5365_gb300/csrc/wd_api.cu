@@ -311,6 +311,18 @@ int wd_tc_gemm_bf16(float* D, const void* A, const void* B, int M, int K, int N)
   return h ? WD_ERR_TIMEOUT : WD_OK;
 }
 
+int wd_wait_selftest(long long spins) {
+  if (spins < 1 || spins > (1LL << 24)) return WD_ERR_ARG;
+  cudaStream_t st = state().stream;
+  int* flag = nullptr;
+  WD_TRY(cuda_status(device_flag(&flag, st)));
+  WD_TRY(cuda_status(wait_selftest((long)spins, flag, st)));
+  int h = 0;
+  WD_TRY(cuda_status(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st)));
+  WD_TRY(cuda_status(cudaStreamSynchronize(st)));
+  return h ? WD_ERR_TIMEOUT : WD_OK;
+}
+
 void wd_nn_train_params_default(wd_nn_train_params* p) {
   if (!p) return;
   p->samples = 4096;

@@ -93,4 +93,24 @@ cudaError_t tc_gemm_bf16(const void* A, const void* B, float* D, int M, int K, i
   return cudaGetLastError();
 }
 
+// The bounded-wait failure path, exercised on purpose: one warp initialises
+// an mbarrier that nothing ever arrives on and waits for its first phase with
+// the same bounded helper as the tensor-core kernels.  When the polls run out
+// it raises the device error flag, as those kernels do, and returns normally.
+__global__ void wait_selftest_kernel(long spins, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0u, spins);
+  if (threadIdx.x == 0 && !ok) atomicExch(err, 1);
+}
+
+cudaError_t wait_selftest(long spins, int* err, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(spins, err);
+  return cudaGetLastError();
+}
+
 }  // namespace wd

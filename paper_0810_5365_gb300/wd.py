@@ -42,6 +42,7 @@ EXPORTS = [
     "wd_rotate_spinor", "wd_tc_gemm_bf16", "wd_nn_train_params_default", "wd_nn_init",
     "wd_nn_apply", "wd_nn_train", "wd_solve_fgcr", "wd_nn_layer", "wd_gaussian_spinor",
     "wd_nn_wgrad", "wd_set_autotune", "wd_mrhs_set_lanes", "wd_tune_report",
+    "wd_wait_selftest",
 ]
 
 WD_NN_PARAMS = 2304
@@ -143,6 +144,7 @@ def lib():
         "wd_dslash_mrhs": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
                                      C.c_int, dp, i4, C.c_int, C.c_int]),
         "wd_set_autotune": (C.c_int, [C.c_int]),
+        "wd_wait_selftest": (C.c_int, [C.c_longlong]),
         "wd_mrhs_set_lanes": (C.c_int, [C.c_int]),
         "wd_tune_report": (C.c_int, [C.c_char_p, C.c_size_t]),
         "wd_solve_batch": (C.c_int, [C.POINTER(wd_batch_problem), C.c_int,
@@ -271,6 +273,12 @@ def wd_dslash_mrhs(out, inp, gauge, parity, dagger, a, x, bx, nrhs, norm2, dims,
     _ck(lib().wd_dslash_mrhs(_p(out), _p(inp), _p(gauge), int(parity), int(dagger), float(a),
                              _p(x), float(bx), int(nrhs), _p(norm2), _d(dims), int(prec),
                              int(recon)), "wd_dslash_mrhs")
+
+
+def wd_wait_selftest(spins):
+    """Run the bounded-wait failure path on purpose; returns the status
+    (WD_ERR_TIMEOUT is the expected answer)."""
+    return int(lib().wd_wait_selftest(int(spins)))
 
 
 def wd_set_autotune(enable):

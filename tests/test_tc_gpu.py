@@ -34,3 +34,12 @@ def test_tc_gemm_rejects_bad_shapes():
         with pytest.raises(W.WdError) as e:
             W.wd_tc_gemm_bf16(d, a, a, M, K, N)
         assert e.value.status == W.WD_ERR_ARG
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    """The failure path of the bounded device waits, run on purpose: a wait on
+    an mbarrier that nothing completes gives up after its polls, the call
+    reports WD_ERR_TIMEOUT, and the next tensor-core launch is still exact."""
+    assert W.wd_wait_selftest(1 << 14) == W.WD_ERR_TIMEOUT
+    assert W.wd_wait_selftest(0) == W.WD_ERR_ARG
+    test_tc_gemm_matches_host(128, 48, 48)
