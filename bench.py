@@ -1,16 +1,33 @@
-"""Benchmark: even-odd Wilson dslash throughput on a 32^3x64 lattice.
+"""Benchmark: even-odd Wilson dslash throughput on a 32^3x64 lattice, and
+time-to-solution of the solvers built on it.
 
-One step = one parity-restricted hopping application (Dslash of the paper's
-section "Wilson inverter: Main features") over the V/2 = 1,048,576 sites of
-one parity, FP32 with 12-real links (the headline), alternating the output
-parity each step.  Effective Gflops use the nominal 1320 flops per site
-(reconstruction work not counted, as the paper counts its effective
-Gflops, section "Performance").  The FP16 (per-site scale) variant is timed too.
+Headline: one step = one parity-restricted hopping application (Dslash of
+the paper's section "Wilson inverter: Main features") over the
+V/2 = 1,048,576 sites of one parity, FP32 with 12-real links, alternating the
+output parity each step.  Effective Gflops use the nominal 1320 flops per
+site (reconstruction work not counted, as the paper counts its effective
+Gflops, section "Performance").
 
-Contract: one JSON line on rank 0 with metric/value/unit, roofline (HBM),
-cpu_baseline (the FP64 oracle on the host cores), e2e (through the C ABI with
-host buffers), clocks and gpu_launches.  ``--impl reference`` times the FP64
-CPU oracle on the same workload instead (bounded sample per step).
+The JSON line (rank 0) carries, besides metric/value/unit:
+  roofline      achieved GB/s against the measured copy peak (and the nominal
+                8 TB/s), with the DRAM traffic per launch from the committed
+                ncu counters while the kernel sources are unchanged;
+  graph         the same launches captured as one CUDA graph;
+  variants      FP16, FP64 and the temporal-gauge variants;
+  e2e           the headline through the C ABI with pinned host buffers and
+                the copies inside the timed region (pipelined over streams);
+  clocks        SM clocks and throttle reasons sampled during the timing;
+  cpu_baseline  the FP64 oracle on the host cores (and one thread), plus a
+                per-iteration oracle CG time on 24^3x48;
+  solve         time to a 1e-10 true residual on 24^3x48: mixed-precision CG
+                and BiCGstab against plain FP64 CG;
+  batch         batched multi-right-hand-side solves against the same solves
+                one at a time, and the autotuner's tile shapes;
+  learned_preconditioner  training, and FGCR with the network against plain
+                GCR and CG.
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(bounded sample per step).  ``--profile NAME`` runs a short fixed workload for
+an ncu capture.
 """
 from __future__ import annotations
 
