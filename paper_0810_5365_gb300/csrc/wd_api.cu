@@ -36,6 +36,22 @@ int tune_report(char* buf, size_t len);
 using namespace wd;
 
 namespace {
+// Entry points whose implementations use host containers run through this
+// guard, so that a host allocation failure becomes a status (WD_ERR_CUDA with
+// cudaErrorMemoryAllocation) instead of an exception crossing the C ABI.
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (...) {
+    state().last_cuda_error = (int)cudaErrorMemoryAllocation;
+    return WD_ERR_CUDA;
+  }
+}
+}  // namespace
+
+
+namespace {
 
 int check_dims(const int* dims) {
   if (!dims) return WD_ERR_NULL;
@@ -254,15 +270,19 @@ int wd_dslash_mrhs(void* out, const void* in, const void* gauge, int parity, int
   if (nrhs < 1 || nrhs > 32) return WD_ERR_ARG;
   if (link_bytes(prec, recon) == 0) return WD_ERR_PREC;
   if (out == in) return WD_ERR_ALIAS;
-  return cuda_status(dslash_mrhs(out, in, gauge, parity, dagger, a, x, bx, nrhs, norm2,
-                                 make_geom(dims), prec, recon, state().stream));
+  return guarded([&] {
+    return cuda_status(dslash_mrhs(out, in, gauge, parity, dagger, a, x, bx, nrhs, norm2,
+                                   make_geom(dims), prec, recon, state().stream));
+  });
 }
 
 int wd_set_autotune(int enable) { return set_autotune(enable); }
 
 int wd_mrhs_set_lanes(int lanes) { return mrhs_set_lanes(lanes); }
 
-int wd_tune_report(char* buf, size_t len) { return tune_report(buf, len); }
+int wd_tune_report(char* buf, size_t len) {
+  return guarded([&] { return tune_report(buf, len); });
+}
 
 int wd_solve_batch(const wd_batch_problem* problems, int nproblems, const wd_solve_params* params,
                    wd_solve_info* info) {
@@ -276,7 +296,7 @@ int wd_solve_batch(const wd_batch_problem* problems, int nproblems, const wd_sol
     if (problems[j].nrhs < 1 || problems[j].nrhs > 32) return WD_ERR_ARG;
     if ((const void*)problems[j].x == (const void*)problems[j].b) return WD_ERR_ALIAS;
   }
-  return solve_batch_impl(problems, nproblems, params, info);
+  return guarded([&] { return solve_batch_impl(problems, nproblems, params, info); });
 }
 
 int wd_gauge_fix_temporal(double* U_out, double* omega_out, const double* U_in,
@@ -341,7 +361,7 @@ int wd_nn_layer(void* out, const void* in, const float* weights, int cin, int co
   if (!aligned(out) || !aligned(in) || !aligned(weights) || !aligned(gauge)) return WD_ERR_ALIGN;
   if ((cin != 4 && cin != 8) || (cout != 4 && cout != 8)) return WD_ERR_ARG;
   if (out == in) return WD_ERR_ALIAS;
-  return nn_layer_impl(out, in, weights, cin, cout, gauge, dims);
+  return guarded([&] { return nn_layer_impl(out, in, weights, cin, cout, gauge, dims); });
 }
 
 int wd_nn_wgrad(float* grad, const void* in, const void* delta, int cin, int cout,
@@ -351,7 +371,7 @@ int wd_nn_wgrad(float* grad, const void* in, const void* delta, int cin, int cou
   if (!aligned(grad) || !aligned(in) || !aligned(delta) || !aligned(gauge)) return WD_ERR_ALIGN;
   if ((cin != 4 && cin != 8) || (cout != 4 && cout != 8) || (cin == 4 && cout == 4))
     return WD_ERR_ARG;
-  return nn_wgrad_impl(grad, in, delta, cin, cout, gauge, dims);
+  return guarded([&] { return nn_wgrad_impl(grad, in, delta, cin, cout, gauge, dims); });
 }
 
 int wd_gaussian_spinor(void* out, unsigned long long seed, unsigned long long stream,
@@ -365,7 +385,7 @@ int wd_gaussian_spinor(void* out, unsigned long long seed, unsigned long long st
 int wd_nn_init(float* weights, double kappa) {
   if (!weights) return WD_ERR_NULL;
   if (!aligned(weights)) return WD_ERR_ALIGN;
-  return nn_init_impl(weights, kappa);
+  return guarded([&] { return nn_init_impl(weights, kappa); });
 }
 
 int wd_nn_apply(void* out, const void* in, const float* weights, const void* gauge,
@@ -374,7 +394,7 @@ int wd_nn_apply(void* out, const void* in, const float* weights, const void* gau
   if (!out || !in || !weights || !gauge) return WD_ERR_NULL;
   if (!aligned(out) || !aligned(in) || !aligned(weights) || !aligned(gauge)) return WD_ERR_ALIGN;
   if (out == in) return WD_ERR_ALIAS;
-  return nn_apply_impl(out, in, weights, gauge, dims);
+  return guarded([&] { return nn_apply_impl(out, in, weights, gauge, dims); });
 }
 
 int wd_nn_train(float* weights, const double* gauge, double kappa, const int dims[4],
@@ -385,7 +405,7 @@ int wd_nn_train(float* weights, const double* gauge, double kappa, const int dim
   wd_nn_train_params p;
   wd_nn_train_params_default(&p);
   if (params) p = *params;
-  return nn_train_impl(weights, gauge, kappa, dims, &p, info);
+  return guarded([&] { return nn_train_impl(weights, gauge, kappa, dims, &p, info); });
 }
 
 int wd_solve_fgcr(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
@@ -397,7 +417,7 @@ int wd_solve_fgcr(double* x, const double* b, const double* gauge, double kappa,
     return WD_ERR_ALIGN;
   if (x == b) return WD_ERR_ALIAS;
   if (m < 1 || m > 16) return WD_ERR_ARG;
-  return fgcr_impl(x, b, gauge, kappa, dims, weights, params, info, m);
+  return guarded([&] { return fgcr_impl(x, b, gauge, kappa, dims, weights, params, info, m); });
 }
 
 int wd_norm2(double* result, const void* x, const int dims[4], int parity, int prec) {
