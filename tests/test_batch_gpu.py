@@ -241,3 +241,34 @@ def test_batch_at_its_limits():
         for k in range(b.shape[0]):
             res = b[k] - oracle.apply_D(x[k], U, dims, 0.125)
             assert np.linalg.norm(res) / np.linalg.norm(b[k]) <= 1.05e-10
+
+
+def test_batched_resume_from_initial_guess():
+    """A batched solve restarted from the partial solutions of a loose first
+    pass (nonzero x: the FP64 residual is formed in setup) reaches 1e-10 on
+    every right-hand side in fewer iterations than a start from zero."""
+    probs, keep = [], []
+    for j, (dims, nrhs) in enumerate([((4, 4, 4, 4), 2), ((6, 4, 4, 6), 3)]):
+        U = fields.su3_links(dims, seed=5000 + j, workers=1)
+        b = np.ascontiguousarray(np.stack([fields.gaussian_spinor(dims, seed=6000 + 10 * j + k)
+                                           for k in range(nrhs)]))
+        x = np.zeros_like(b)
+        probs.append({"dims": dims, "kappa": 0.13, "nrhs": nrhs, "gauge": U, "b": b, "x": x})
+        keep.append((dims, U, b, x))
+    p = W.wd_solve_params_default()
+    p.tol = 1e-5
+    rc, loose = W.wd_solve_batch(probs, p)
+    assert rc == W.WD_OK
+    p.tol = 1e-10
+    p.use_initial_guess = 1
+    rc, resumed = W.wd_solve_batch(probs, p)
+    assert rc == W.WD_OK
+    for dims, U, b, x in keep:
+        for k in range(b.shape[0]):
+            res = b[k] - oracle.apply_D(x[k], U, dims, 0.13)
+            assert np.linalg.norm(res) / np.linalg.norm(b[k]) <= 1.05e-10
+    zero = [dict(pr, x=np.zeros_like(pr["b"])) for pr in probs]
+    p.use_initial_guess = 0
+    rc, fresh = W.wd_solve_batch(zero, p)
+    assert rc == W.WD_OK
+    assert sum(d["iters"] for d in resumed) < sum(d["iters"] for d in fresh)
