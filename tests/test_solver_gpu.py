@@ -174,3 +174,20 @@ def test_initial_guess_resume_other_variants(solver, gf):
     fresh = W.wd_solve_ex(np.zeros_like(b), b, U, kappa, dims,
                           params(solver=solver, gauge_fix=gf))
     assert again["iters"] < fresh["iters"]
+
+
+@pytest.mark.parametrize("reliable,check", [(1, 2), (7, 3), (50, 16), (3, 1)])
+@pytest.mark.parametrize("inner", [W.WD_F32, W.WD_F16])
+def test_solver_schedule_edges(reliable, check, inner):
+    """Reliable updates every iteration or at odd intervals, and check
+    intervals that are odd, 1 or long (the graph chunk rounds to an even
+    count of at least 2): every schedule reaches the oracle's 1e-10."""
+    dims, kappa = (4, 4, 4, 8), 0.132
+    U = fields.su3_links(dims, workers=1)
+    b = fields.gaussian_spinor(dims, seed=13)
+    x = np.zeros_like(b)
+    info = W.wd_solve_ex(x, b, U, kappa, dims,
+                         params(inner_prec=inner, reliable_interval=reliable,
+                                check_interval=check))
+    assert info["status"] == W.WD_OK
+    assert true_residual(x, b, U, dims, kappa) <= 1.05e-10
