@@ -451,7 +451,10 @@ int wd_nn_layer(void *out, const void *in, const float *weights, int cin, int co
 /* Weight gradient of one layer (backpropagation):
  *     grad_d[o][i] = sum_{x, colour a} delta(x)[o][a] conj((T_d in)(x)[i][a])
  * in: cin channels, delta: cout channels (packed FP32 full layout as above);
- * grad: [9][cout][cin] complex FP32 (device).  Synchronous. */
+ * grad: [9][cout][cin] complex FP32 (device).  The contraction runs on the
+ * tensor cores (BF16 operands, FP32 accumulation); the per-CTA partial
+ * gradients are summed in a fixed order.  (cin, cout) in {(4, 8), (8, 8),
+ * (8, 4)}.  WD_ERR_TIMEOUT if a bounded device wait gave up.  Synchronous. */
 int wd_nn_wgrad(float *grad, const void *in, const void *delta, int cin, int cout,
                 const void *gauge, const int dims[4]);
 

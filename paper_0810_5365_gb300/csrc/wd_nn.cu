@@ -84,70 +84,9 @@ static cudaError_t nn_layer(int cin, int cout, const Geom& g, const void* gauge,
 
 // ---------------------------------------------------------------------------
 // weight gradient: G_d[o][i] = sum_{x, a} delta(x)[o][a] conj((T_d phi)(x)[i][a])
-// per-tile partials (fixed order) and a fixed-order sum over tiles
+// (the tensor-core kernel below writes one partial gradient per CTA; this
+// sums them in CTA order)
 // ---------------------------------------------------------------------------
-
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(NN_TILE) nn_wgrad_kernel(const NnLayerArgs A,
-                                                           const char* __restrict__ delta,
-                                                           size_t delta_half, float* partials) {
-  constexpr int NV = COUT * CIN * 2;
-  __shared__ float red[4][NV];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Geom& g = A.g;
-  const int tpp = (g.Vh + NN_TILE - 1) / NN_TILE;
-  const int p = blockIdx.x / tpp;
-  const int cb = (blockIdx.x - p * tpp) * NN_TILE + tid;
-  const bool valid = cb < g.Vh;
-  cx<float> dl[COUT * 3];
-  NnNeighbours nbs;
-  if (valid) {
-    nn_neighbours(nbs, cb, p, g);
-    nn_load<COUT>(dl, delta + p * delta_half, cb, g.Vh_pad);
-  } else {
-#pragma unroll
-    for (int k = 0; k < COUT * 3; k++) dl[k] = mk<float>(0.f, 0.f);
-  }
-  for (int d = 0; d < NN_NDIR; d++) {
-    cx<float> t[CIN * 3];
-    if (valid) {
-      nn_transport<CIN>(t, A, nbs, d, p);
-    } else {
-#pragma unroll
-      for (int k = 0; k < CIN * 3; k++) t[k] = mk<float>(0.f, 0.f);
-    }
-#pragma unroll
-    for (int o = 0; o < COUT; o++) {
-#pragma unroll
-      for (int i = 0; i < CIN; i++) {
-        // sum_a delta[o][a] * conj(t[i][a])
-        float re = 0.f, im = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-          const cx<float> x = dl[o * 3 + a], y = t[i * 3 + a];
-          re = fmaf(x.r, y.r, re);
-          re = fmaf(x.i, y.i, re);
-          im = fmaf(x.i, y.r, im);
-          im = fmaf(-x.r, y.i, im);
-        }
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-          re += __shfl_xor_sync(0xffffffffu, re, s);
-          im += __shfl_xor_sync(0xffffffffu, im, s);
-        }
-        if (lane == 0) {
-          red[warp][(o * CIN + i) * 2] = re;
-          red[warp][(o * CIN + i) * 2 + 1] = im;
-        }
-      }
-    }
-    __syncthreads();
-    for (int j = tid; j < NV; j += NN_TILE)
-      partials[((size_t)blockIdx.x * NN_NDIR + d) * NV + j] =
-          red[0][j] + red[1][j] + red[2][j] + red[3][j];
-    __syncthreads();
-  }
-}
 
 // out[j] (+)= sum_t partials[t][j], t in order
 __global__ void nn_sum_tiles(const float* __restrict__ partials, int ntiles, int n, float* out,
@@ -159,26 +98,204 @@ __global__ void nn_sum_tiles(const float* __restrict__ partials, int ntiles, int
   out[j] = accumulate ? out[j] + (float)s : (float)s;
 }
 
+// ---------------------------------------------------------------------------
+// weight gradient on the tensor cores: for all nine directions at once,
+//   G^T[d C_in + i][2o + part] = sum_{x, a} (T_d phi)[i][a] x delta-row,
+// with the real form of the complex product conj-contracted over (site,
+// colour): the A rows are the transported input channels [t_r | t_i] (9 C_in
+// of the M = 128 rows, the rest zero), the B rows are [delta_r | delta_i] for
+// Re G and [delta_i | -delta_r] for Im G (2 C_out of N = 16 rows).  K runs over
+// (part, colour, site) of 32-site blocks: 192 = 12 chunks of 16 per block.
+// Each persistent CTA accumulates its blocks in TMEM (FP32), writes its
+// partial gradient, and the partials are summed over CTAs in a fixed order.
+// ---------------------------------------------------------------------------
+
+constexpr int WG_SITES = 32;                    // sites per K block
+constexpr int WG_KCH = 2 * 3 * WG_SITES / 16;   // K chunks of 16 per block
+constexpr uint32_t WG_ACH = 128 * 16 * 2;       // one A chunk (M = 128 rows), bytes
+constexpr uint32_t WG_BCH = 16 * 16 * 2;        // one B chunk (N = 16 rows), bytes
+constexpr uint32_t WG_BUF = WG_KCH * (WG_ACH + WG_BCH);
+constexpr int WG_THREADS = 128;
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WG_THREADS) nn_wgrad_tc_kernel(const NnLayerArgs A,
+                                                                 const char* __restrict__ delta,
+                                                                 size_t delta_half, int nblocks,
+                                                                 float* partials) {
+  extern __shared__ __align__(128) unsigned char wg_smem[];  // 2 buffers of WG_BUF
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Geom& g = A.g;
+  constexpr int NV = NN_NDIR * COUT * CIN * 2;
+  // rows that are never written (A rows >= 9 CIN, B rows >= 2 COUT) stay zero
+  for (uint32_t e = tid; e < 2 * WG_BUF / 16; e += WG_THREADS)
+    reinterpret_cast<int4*>(wg_smem)[e] = make_int4(0, 0, 0, 0);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 32);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t idesc = make_idesc_bf16(128, 16);
+  const int bpp = (g.Vh + WG_SITES - 1) / WG_SITES;  // blocks per parity
+  bool ok = true;
+  uint32_t G = 0;  // blocks issued by this CTA
+
+  for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x, G++) {
+    const uint32_t buf = G & 1u;
+    unsigned char* sa = wg_smem + buf * WG_BUF;
+    unsigned char* sb = sa + WG_KCH * WG_ACH;
+    if (G >= 2) ok = mbar_wait_bounded(&bar[buf], ((G - 2) >> 1) & 1u, NN_SPIN_LIMIT) && ok;
+    const int p = blk / bpp;
+    const int cb = (blk - p * bpp) * WG_SITES + lane;
+    const bool valid = cb < g.Vh;
+    NnNeighbours nbs;
+    if (valid) nn_neighbours(nbs, cb, p, g);
+    // A: warp w transports directions w, w + 4, w + 8
+    for (int d = warp; d < NN_NDIR; d += 4) {
+      cx<float> t[CIN * 3];
+      if (valid) {
+        nn_transport<CIN>(t, A, nbs, d, p);
+      } else {
+#pragma unroll
+        for (int k = 0; k < CIN * 3; k++) t[k] = mk<float>(0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < CIN; i++) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+#pragma unroll
+          for (int part = 0; part < 2; part++) {
+            const int kp = (part * 3 + a) * WG_SITES + lane;
+            const float v = part ? t[i * 3 + a].i : t[i * 3 + a].r;
+            *(__nv_bfloat16*)(sa + (kp >> 4) * WG_ACH + kmajor_offset(d * CIN + i, kp & 15, 16)) =
+                __float2bfloat16_rn(v);
+          }
+        }
+      }
+    }
+    // B: the delta rows of these sites (warp 0)
+    if (warp == 0) {
+      cx<float> dl[COUT * 3];
+      if (valid) {
+        nn_load<COUT>(dl, delta + p * delta_half, cb, g.Vh_pad);
+      } else {
+#pragma unroll
+        for (int k = 0; k < COUT * 3; k++) dl[k] = mk<float>(0.f, 0.f);
+      }
+#pragma unroll
+      for (int o = 0; o < COUT; o++) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const cx<float> v = dl[o * 3 + a];
+          const int k0 = a * WG_SITES + lane, k1 = (3 + a) * WG_SITES + lane;
+          // Re G row: [delta_r | delta_i] ; Im G row: [delta_i | -delta_r]
+          *(__nv_bfloat16*)(sb + (k0 >> 4) * WG_BCH + kmajor_offset(2 * o, k0 & 15, 16)) =
+              __float2bfloat16_rn(v.r);
+          *(__nv_bfloat16*)(sb + (k1 >> 4) * WG_BCH + kmajor_offset(2 * o, k1 & 15, 16)) =
+              __float2bfloat16_rn(v.i);
+          *(__nv_bfloat16*)(sb + (k0 >> 4) * WG_BCH + kmajor_offset(2 * o + 1, k0 & 15, 16)) =
+              __float2bfloat16_rn(v.i);
+          *(__nv_bfloat16*)(sb + (k1 >> 4) * WG_BCH + kmajor_offset(2 * o + 1, k1 & 15, 16)) =
+              __float2bfloat16_rn(-v.r);
+        }
+      }
+    }
+    fence_smem_to_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      for (int kc = 0; kc < WG_KCH; kc++) {
+        const uint64_t ad = make_smem_desc(smem_u32(sa + kc * WG_ACH), 128, 256);
+        const uint64_t bd = make_smem_desc(smem_u32(sb + kc * WG_BCH), 128, 256);
+        tc_mma_bf16(tbase, ad, bd, idesc, (G > 0 || kc > 0) ? 1u : 0u);
+      }
+      tc_commit(&bar[buf]);
+    }
+  }
+  if (G > 0) ok = mbar_wait_bounded(&bar[(G - 1) & 1u], ((G - 1) >> 1) & 1u, NN_SPIN_LIMIT) && ok;
+  ok = __syncthreads_and(ok) != 0;
+  tc_fence_after();
+  float* mine = partials + (size_t)blockIdx.x * NV;
+  if (ok) {
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 16; c++) v[c] = 0.f;
+    if (G > 0) tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16), v);
+    // lane 32 w + lane holds row i' = d CIN + i: columns 2o + part
+    const int row = 32 * warp + lane;
+    if (row < NN_NDIR * CIN) {
+      const int d = row / CIN, i = row - d * CIN;
+#pragma unroll
+      for (int o = 0; o < COUT; o++) {
+        mine[((d * COUT + o) * CIN + i) * 2] = v[2 * o];
+        mine[((d * COUT + o) * CIN + i) * 2 + 1] = v[2 * o + 1];
+      }
+    }
+  } else {
+    if (tid == 0) atomicExch(A.err, 1);
+    if (G > 0) mbar_wait_bounded(&bar[(G - 1) & 1u], ((G - 1) >> 1) & 1u, NN_SPIN_LIMIT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 32);
+}
+
+// persistent grid of the tensor-core weight gradient: at most `cap` CTAs
+// (the caller's partial buffer), 2 per SM (two K buffers of ~110 KB)
+template <int CIN, int COUT>
+static cudaError_t launch_wgrad_tc(const NnLayerArgs& A, const char* delta, size_t dh,
+                                   float* partials, int cap, int* grid_out, cudaStream_t st) {
+  constexpr int dyn = 2 * (int)WG_BUF;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(nn_wgrad_tc_kernel<CIN, COUT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int nblocks = 2 * ((A.g.Vh + WG_SITES - 1) / WG_SITES);
+  int grid = num_sms() * 2;
+  grid = grid < nblocks ? grid : nblocks;
+  grid = grid < cap ? grid : cap;
+  if (grid < 1) grid = 1;
+  *grid_out = grid;
+  nn_wgrad_tc_kernel<CIN, COUT><<<grid, WG_THREADS, dyn, st>>>(A, delta, dh, nblocks, partials);
+  return cudaGetLastError();
+}
+
 static cudaError_t nn_wgrad(int cin, int cout, const Geom& g, const void* gauge, const void* in,
                             const void* delta, float* partials, float* grad_out, int accumulate,
-                            cudaStream_t st) {
+                            int* err, cudaStream_t st) {
   NnLayerArgs A;
   std::memset(&A, 0, sizeof(A));
   A.g = g;
   A.gauge = gauge;
   A.in = (const char*)in;
   A.in_half = nn_half_bytes(g.Vh_pad, cin);
+  A.err = err;
   const size_t dh = nn_half_bytes(g.Vh_pad, cout);
-  const int grid = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  // the partial buffer holds one gradient per 128-site tile
+  const int cap = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  int grid = 1;
+  cudaError_t e;
   if (cin == 4 && cout == 8)
-    nn_wgrad_kernel<4, 8><<<grid, NN_TILE, 0, st>>>(A, (const char*)delta, dh, partials);
+    e = launch_wgrad_tc<4, 8>(A, (const char*)delta, dh, partials, cap, &grid, st);
   else if (cin == 8 && cout == 8)
-    nn_wgrad_kernel<8, 8><<<grid, NN_TILE, 0, st>>>(A, (const char*)delta, dh, partials);
+    e = launch_wgrad_tc<8, 8>(A, (const char*)delta, dh, partials, cap, &grid, st);
   else if (cin == 8 && cout == 4)
-    nn_wgrad_kernel<8, 4><<<grid, NN_TILE, 0, st>>>(A, (const char*)delta, dh, partials);
+    e = launch_wgrad_tc<8, 4>(A, (const char*)delta, dh, partials, cap, &grid, st);
   else
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n = NN_NDIR * cout * cin * 2;
   nn_sum_tiles<<<(n + 127) / 128, 128, 0, st>>>(partials, grid, n, grad_out, accumulate);
@@ -592,9 +709,13 @@ int nn_wgrad_impl(float* grad, const void* in, const void* delta, int cin, int c
   void* part;
   const int ntile = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
   NCK(al.get(&part, (size_t)ntile * NN_NDIR * cout * cin * 2 * sizeof(float)));
-  NCK(nn_wgrad(cin, cout, g, gauge, in, delta, (float*)part, grad, 0, st));
+  int* flag = nullptr;
+  NCK(device_flag(&flag, st));
+  NCK(nn_wgrad(cin, cout, g, gauge, in, delta, (float*)part, grad, 0, flag, st));
+  int hflag = 0;
+  NCK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   NCK(cudaStreamSynchronize(st));
-  return WD_OK;
+  return hflag ? WD_ERR_TIMEOUT : WD_OK;
 }
 
 int gaussian_spinor_impl(void* out, unsigned long long seed, unsigned long long stream,
@@ -698,11 +819,14 @@ int nn_train_impl(float* w, const double* gauge, double kappa, const int dims[4]
       NCK(norm2(L + 1, x, g, WD_F32, 2, st));
       // backward: G3 (h2 -> y), delta2 = L3^+ dl, G2, delta1 = L2^+ delta2, G1
       const int acc = sbt > 0;
-      NCK(nn_wgrad(8, 4, g, gp, B.h2, dl, (float*)part, (float*)grad + nn_layer_offset(2), acc, st));
+      NCK(nn_wgrad(8, 4, g, gp, B.h2, dl, (float*)part, (float*)grad + nn_layer_offset(2), acc,
+                   flag, st));
       NCK(nn_layer(4, 8, g, gp, dl, d2, WA + nn_layer_offset(2), flag, st));
-      NCK(nn_wgrad(8, 8, g, gp, B.h1, d2, (float*)part, (float*)grad + nn_layer_offset(1), acc, st));
+      NCK(nn_wgrad(8, 8, g, gp, B.h1, d2, (float*)part, (float*)grad + nn_layer_offset(1), acc,
+                   flag, st));
       NCK(nn_layer(8, 8, g, gp, d2, d1, WA + nn_layer_offset(1), flag, st));
-      NCK(nn_wgrad(4, 8, g, gp, b, d1, (float*)part, (float*)grad + nn_layer_offset(0), acc, st));
+      NCK(nn_wgrad(4, 8, g, gp, b, d1, (float*)part, (float*)grad + nn_layer_offset(0), acc,
+                   flag, st));
     }
     const float gscale = (float)(1.0 / ((double)P.batch * 12.0 * (double)V));
     nn_adam<<<(NN_PARAMS + 255) / 256, 256, 0, st>>>(W, (const float*)grad, (float*)m, (float*)v2,

@@ -114,11 +114,14 @@ def test_layer_within_bf16_bound(dims, cin, cout):
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 5e-3
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 8), (6, 4, 2, 6), (8, 8, 8, 8)])
 @pytest.mark.parametrize("cin,cout", [(4, 8), (8, 8), (8, 4)])
-def test_weight_gradient(cin, cout):
-    dims = (4, 4, 4, 8)
+def test_weight_gradient(dims, cin, cout):
+    """The tensor-core weight gradient (BF16 operands, FP32 accumulation in
+    TMEM, fixed-order FP32 sum over CTAs) against its FP64 definition, element
+    by element within the BF16 rounding bound, on ragged 32-site blocks."""
     U = fields.su3_links(dims, workers=1)
-    r = np.random.default_rng(7 + cin + cout)
+    r = np.random.default_rng(7 + cin + cout + dims[0])
     V = fields.volume(dims)
     phi = r.normal(size=(V, cin, 3)) + 1j * r.normal(size=(V, cin, 3))
     dl = r.normal(size=(V, cout, 3)) + 1j * r.normal(size=(V, cout, 3))
@@ -128,9 +131,14 @@ def test_weight_gradient(cin, cout):
     got = grad.cpu().numpy().astype(np.float64).reshape(9, cout, cin, 2)
     got = got[..., 0] + 1j * got[..., 1]
     tr = nn.transports(dims)
-    want = np.stack([np.einsum("xoa,xia->oi", dl, np.conj(nn.transport(phi, U, dims, d, tr)))
-                     for d in range(9)])
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-5
+    ts = [nn.transport(phi, U, dims, d, tr) for d in range(9)]
+    want = np.stack([np.einsum("xoa,xia->oi", dl, np.conj(t)) for t in ts])
+    # each real product of BF16-rounded operands is off by at most 2 * 2^-8
+    # of its size; the FP32 sums add far less
+    bound = np.stack([np.einsum("xoa,xia->oi", np.abs(dl), np.abs(t)) for t in ts])
+    err = np.abs(got - want)
+    assert np.all(err <= 2 * 2.0 ** -8 * 2 * bound + 1e-4)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-2
 
 
 def test_initial_weights_are_the_hopping_series():
