@@ -642,10 +642,15 @@ def nn_section(W, torch):
 
 def profile_case(name):
     """A short fixed workload for an ncu capture (nothing timed or reported):
-    ``mrhs`` = 4 multi-RHS hopping launches (12 right-hand sides, FP32, 24^3x48);
-    ``solve_f32`` / ``solve_f16`` = 2 mixed-precision CG solves to 1e-10 on
-    24^3x48 (kappa 0.137); ``nn`` = 2 applications of the series-initialised
-    network (three tensor-core layers) on 16^3x32."""
+    ``mrhs``      4 multi-RHS hopping launches (12 right-hand sides, FP32,
+                  24^3x48);
+    ``solve_f32`` / ``solve_f16``  2 mixed-precision CG solves to 1e-10 on
+                  24^3x48 (kappa 0.137);
+    ``batch``     one batched FP32-inner solve of 12 point sources on 24^3x48;
+    ``train``     4 Adam steps of 16 samples on 16^3x32 (forward, adjoint and
+                  tensor-core weight-gradient kernels);
+    ``nn``        2 applications of the series-initialised network (three
+                  tensor-core layers) on 16^3x32."""
     import torch
     from synth import fields
     import paper_0810_5365_gb300 as W
@@ -686,6 +691,13 @@ def profile_case(name):
         p = W.wd_solve_params_default()
         p.inner_prec = W.WD_F32
         W.wd_solve_batch(probs, p)
+    elif name == "train":
+        dims = (16, 16, 16, 32)
+        Ud = torch.from_numpy(fields.su3_links(dims).view(np.float64).reshape(-1)).cuda()
+        w = torch.zeros(W.WD_NN_PARAMS, dtype=torch.float32, device="cuda")
+        p = W.wd_nn_train_params_default()
+        p.samples = 64
+        W.wd_nn_train(w, Ud, NN_KAPPA, dims, p)
     elif name == "nn":
         dims = (16, 16, 16, 32)
         Ud = torch.from_numpy(fields.su3_links(dims).view(np.float64).reshape(-1)).cuda()
@@ -905,7 +917,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--quick", action="store_true", help="FP32 dslash only")
     ap.add_argument("--no-solve", action="store_true", help="skip the 24^3x48 solver comparison")
-    ap.add_argument("--profile", choices=["mrhs", "solve_f32", "solve_f16", "batch", "nn"],
+    ap.add_argument("--profile", choices=["mrhs", "solve_f32", "solve_f16", "batch", "train", "nn"],
                     help="run a short fixed workload for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile:
