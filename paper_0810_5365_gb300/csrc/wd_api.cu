@@ -28,6 +28,7 @@ cudaError_t dslash_mrhs(void* out, const void* in, const void* gauge, int parity
 int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
                const wd_solve_params* prm, wd_solve_info* info);
 void solver_finalize();
+cudaError_t wait_selftest(long spins, int* err, cudaStream_t st);
 int set_autotune(int enable);
 int mrhs_set_lanes(int lanes);
 int tune_report(char* buf, size_t len);

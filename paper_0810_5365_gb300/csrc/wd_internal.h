@@ -129,8 +129,6 @@ cudaError_t axpby(double a, const void* x, double b, void* y, const Geom& g, int
 cudaError_t device_flag(int** flag, cudaStream_t st);
 
 // tensor-core GEMM (wd_tcgemm.cu)
-// one bounded wait on an mbarrier nothing completes (wd_tcgemm.cu)
-cudaError_t wait_selftest(long spins, int* err, cudaStream_t st);
 cudaError_t tc_gemm_bf16(const void* A, const void* B, float* D, int M, int K, int N, int* err,
                          cudaStream_t st);
 
