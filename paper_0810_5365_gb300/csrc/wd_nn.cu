@@ -115,7 +115,7 @@ constexpr int WG_KCH = 2 * 3 * WG_SITES / 16;   // K chunks of 16 per block
 constexpr uint32_t WG_ACH = 128 * 16 * 2;       // one A chunk (M = 128 rows), bytes
 constexpr uint32_t WG_BCH = 16 * 16 * 2;        // one B chunk (N = 16 rows), bytes
 constexpr uint32_t WG_BUF = WG_KCH * (WG_ACH + WG_BCH);
-constexpr int WG_THREADS = 128;
+constexpr int WG_THREADS = 256;
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(WG_THREADS) nn_wgrad_tc_kernel(const NnLayerArgs A,
@@ -146,6 +146,13 @@ __global__ void __launch_bounds__(WG_THREADS) nn_wgrad_tc_kernel(const NnLayerAr
   const uint32_t tbase = tmem_base;
   const uint32_t idesc = make_idesc_bf16(128, 16);
   const int bpp = (g.Vh + WG_SITES - 1) / WG_SITES;  // blocks per parity
+  // work split of the 8 warps: CIN = 8: warps w and w + 4 transport channels
+  // 0-3 and 4-7 of directions w, w + 4, w + 8; CIN = 4: warps 0-3 transport
+  // directions w, w + 4, w + 8 and warps 4-7 stage the delta rows
+  constexpr bool SPLIT = CIN == 8;
+  const int dw = warp & 3;
+  const int c0 = SPLIT ? 4 * (warp >> 2) : 0;
+  const bool transports = SPLIT || warp < 4;
   bool ok = true;
   uint32_t G = 0;  // blocks issued by this CTA
 
@@ -157,59 +164,74 @@ __global__ void __launch_bounds__(WG_THREADS) nn_wgrad_tc_kernel(const NnLayerAr
     const int p = blk / bpp;
     const int cb = (blk - p * bpp) * WG_SITES + lane;
     const bool valid = cb < g.Vh;
-    NnNeighbours nbs;
-    if (valid) nn_neighbours(nbs, cb, p, g);
-    // A: warp w transports directions w, w + 4, w + 8
-    for (int d = warp; d < NN_NDIR; d += 4) {
-      cx<float> t[CIN * 3];
-      if (valid) {
-        nn_transport<CIN>(t, A, nbs, d, p);
-      } else {
+    if (transports) {
+      int nb[NN_NDIR];
+      int x3 = 0;
+      if (valid) nn_nbr(nb, x3, cb, p, g);
+      for (int d = dw; d < NN_NDIR; d += 4) {
+        cx<float> t[12];
+        if (valid) {
+          nn_transport4<CIN>(t, A, d, p, cb, nb[d], x3, c0);
+        } else {
 #pragma unroll
-        for (int k = 0; k < CIN * 3; k++) t[k] = mk<float>(0.f, 0.f);
-      }
+          for (int k = 0; k < 12; k++) t[k] = mk<float>(0.f, 0.f);
+        }
 #pragma unroll
-      for (int i = 0; i < CIN; i++) {
+        for (int i = 0; i < 4; i++) {
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
+          for (int a = 0; a < 3; a++) {
 #pragma unroll
-          for (int part = 0; part < 2; part++) {
-            const int kp = (part * 3 + a) * WG_SITES + lane;
-            const float v = part ? t[i * 3 + a].i : t[i * 3 + a].r;
-            *(__nv_bfloat16*)(sa + (kp >> 4) * WG_ACH + kmajor_offset(d * CIN + i, kp & 15, 16)) =
-                __float2bfloat16_rn(v);
+            for (int part = 0; part < 2; part++) {
+              const int kp = (part * 3 + a) * WG_SITES + lane;
+              const float v = part ? t[i * 3 + a].i : t[i * 3 + a].r;
+              *(__nv_bfloat16*)(sa + (kp >> 4) * WG_ACH +
+                                kmajor_offset(d * CIN + c0 + i, kp & 15, 16)) =
+                  __float2bfloat16_rn(v);
+            }
           }
         }
       }
     }
-    // B: the delta rows of these sites (warp 0)
-    if (warp == 0) {
-      cx<float> dl[COUT * 3];
-      if (valid) {
-        nn_load<COUT>(dl, delta + p * delta_half, cb, g.Vh_pad);
-      } else {
+    // B: the delta rows of these sites, output channels spread over the warps
+    // that do not transport (CIN = 4) or over all warps (CIN = 8)
+    {
+      constexpr int NW = SPLIT ? 8 : 4;
+      const int w0 = SPLIT ? warp : warp - 4;
+      if (w0 >= 0) {
+        for (int o = w0; o < COUT; o += NW) {
+          cx<float> dl[3];
+          if (valid) {
+            const float4* src = (const float4*)(delta + p * delta_half);
+            constexpr int NG = 3 * COUT / 2;
+            // complex index o*3 + a lives in group (o*3 + a) / 2, half (o*3 + a) % 2
 #pragma unroll
-        for (int k = 0; k < COUT * 3; k++) dl[k] = mk<float>(0.f, 0.f);
-      }
+            for (int a = 0; a < 3; a++) {
+              const int ci = o * 3 + a;
+              const float4 q = __ldg(src + sbi(cb, ci >> 1, NG));
+              dl[a] = (ci & 1) ? mk<float>(q.z, q.w) : mk<float>(q.x, q.y);
+            }
+          } else {
 #pragma unroll
-      for (int o = 0; o < COUT; o++) {
+            for (int a = 0; a < 3; a++) dl[a] = mk<float>(0.f, 0.f);
+          }
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-          const cx<float> v = dl[o * 3 + a];
-          const int k0 = a * WG_SITES + lane, k1 = (3 + a) * WG_SITES + lane;
-          // Re G row: [delta_r | delta_i] ; Im G row: [delta_i | -delta_r]
-          *(__nv_bfloat16*)(sb + (k0 >> 4) * WG_BCH + kmajor_offset(2 * o, k0 & 15, 16)) =
-              __float2bfloat16_rn(v.r);
-          *(__nv_bfloat16*)(sb + (k1 >> 4) * WG_BCH + kmajor_offset(2 * o, k1 & 15, 16)) =
-              __float2bfloat16_rn(v.i);
-          *(__nv_bfloat16*)(sb + (k0 >> 4) * WG_BCH + kmajor_offset(2 * o + 1, k0 & 15, 16)) =
-              __float2bfloat16_rn(v.i);
-          *(__nv_bfloat16*)(sb + (k1 >> 4) * WG_BCH + kmajor_offset(2 * o + 1, k1 & 15, 16)) =
-              __float2bfloat16_rn(-v.r);
+          for (int a = 0; a < 3; a++) {
+            const cx<float> v = dl[a];
+            const int k0 = a * WG_SITES + lane, k1 = (3 + a) * WG_SITES + lane;
+            // Re G row: [delta_r | delta_i] ; Im G row: [delta_i | -delta_r]
+            *(__nv_bfloat16*)(sb + (k0 >> 4) * WG_BCH + kmajor_offset(2 * o, k0 & 15, 16)) =
+                __float2bfloat16_rn(v.r);
+            *(__nv_bfloat16*)(sb + (k1 >> 4) * WG_BCH + kmajor_offset(2 * o, k1 & 15, 16)) =
+                __float2bfloat16_rn(v.i);
+            *(__nv_bfloat16*)(sb + (k0 >> 4) * WG_BCH + kmajor_offset(2 * o + 1, k0 & 15, 16)) =
+                __float2bfloat16_rn(v.i);
+            *(__nv_bfloat16*)(sb + (k1 >> 4) * WG_BCH + kmajor_offset(2 * o + 1, k1 & 15, 16)) =
+                __float2bfloat16_rn(-v.r);
+          }
         }
       }
     }
-    fence_smem_to_async();
+      fence_smem_to_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -226,7 +248,7 @@ __global__ void __launch_bounds__(WG_THREADS) nn_wgrad_tc_kernel(const NnLayerAr
   ok = __syncthreads_and(ok) != 0;
   tc_fence_after();
   float* mine = partials + (size_t)blockIdx.x * NV;
-  if (ok) {
+  if (ok && warp < 4) {
     float v[16];
 #pragma unroll
     for (int c = 0; c < 16; c++) v[c] = 0.f;
@@ -241,7 +263,7 @@ __global__ void __launch_bounds__(WG_THREADS) nn_wgrad_tc_kernel(const NnLayerAr
         mine[((d * COUT + o) * CIN + i) * 2 + 1] = v[2 * o + 1];
       }
     }
-  } else {
+  } else if (!ok) {
     if (tid == 0) atomicExch(A.err, 1);
     if (G > 0) mbar_wait_bounded(&bar[(G - 1) & 1u], ((G - 1) >> 1) & 1u, NN_SPIN_LIMIT);
   }
@@ -251,7 +273,7 @@ __global__ void __launch_bounds__(WG_THREADS) nn_wgrad_tc_kernel(const NnLayerAr
 }
 
 // persistent grid of the tensor-core weight gradient: at most `cap` CTAs
-// (the caller's partial buffer), 2 per SM (two K buffers of ~110 KB)
+// (the caller's partial buffer), 2 per SM (two K buffers of 108 KB each CTA)
 template <int CIN, int COUT>
 static cudaError_t launch_wgrad_tc(const NnLayerArgs& A, const char* delta, size_t dh,
                                    float* partials, int cap, int* grid_out, cudaStream_t st) {
