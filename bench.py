@@ -13,6 +13,7 @@ The JSON line (rank 0) carries, besides metric/value/unit:
                 8 TB/s), with the DRAM traffic per launch from the committed
                 ncu counters while the kernel sources are unchanged;
   graph         the same launches captured as one CUDA graph;
+  mhat          the even-odd operator 1 - kappa^2 D_eo D_oe (the paper's Fig. 1);
   variants      FP16, FP64 and the temporal-gauge variants;
   e2e           the headline through the C ABI with pinned host buffers and
                 the copies inside the timed region (pipelined over streams);
@@ -777,6 +778,23 @@ def run_ours(args, rank, world, local):
         # the headline launches once more, captured as one CUDA graph
         g32, a32, b32, _ = gauges["f32"]
         dt_graph = time_dslash_graph(W, torch, g32, (a32, b32), dims, args.steps)
+        # the paper's Fig. 1 operator: Mhat = 1 - kappa^2 D_eo D_oe on the even
+        # sites (two parity dslashes, the second with the fused epilogue)
+        tmp_o = W.alloc_spinor(dims, W.WD_ODD, W.WD_F32)
+        out_e = W.alloc_spinor(dims, W.WD_EVEN, W.WD_F32)
+        n_mhat = max(1, args.steps // 2)
+        for _ in range(args.warmup):
+            W.wd_mhat(out_e, b32, g32, tmp_o, KAPPA, 0, dims, W.WD_F32)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_mhat):
+            W.wd_mhat(out_e, b32, g32, tmp_o, KAPPA, 0, dims, W.WD_F32)
+        e1.record(stream)
+        e1.synchronize()
+        dt_mhat = e0.elapsed_time(e1) / 1e3
+        del tmp_o, out_e
         # end to end through the C ABI with pinned host buffers: every step
         # copies its input spinor in, applies the operator and copies the
         # result out.  Three streams and two device buffer pairs let step
@@ -851,6 +869,11 @@ def run_ours(args, rank, world, local):
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                      "bytes_per_site": BYTES_PER_SITE["f32"],
                      "frac_of_nominal_8tbs": achieved / 8000.0},
+        "mhat": {"ms_per_step": 1e3 * dt_mhat / n_mhat,
+                 "value": (2 * FLOPS_PER_SITE + 48) * Vh * n_mhat * world / dt_mhat / 1e9,
+                 "unit": "Gflops", "steps": n_mhat,
+                 "note": "even-odd operator 1 - kappa^2 D_eo D_oe (the paper's Fig. 1), FP32, "
+                         "12-real links, 2 x 1320 + 48 flops per even site"},
         "graph": {"ms_per_step": 1e3 * dt_graph / args.steps,
                   "value": FLOPS_PER_SITE * Vh * args.steps * world / dt_graph / 1e9,
                   "unit": "Gflops", "note": "the same launches captured as one CUDA graph"},
@@ -880,7 +903,7 @@ def run_ours(args, rank, world, local):
                    "steps": k_e2e, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
                    "overlap": "3 streams, 2 device buffer pairs: step k+1's input copy and "
                               "step k-1's output copy run under step k's kernel"}
-    line["gpu_launches"] += k_e2e + args.steps  # e2e steps and the graph replay
+    line["gpu_launches"] += k_e2e + args.steps + 2 * n_mhat  # e2e, graph replay, Mhat
     line["clocks"] = clocks
     if not args.no_solve and not args.quick:
         line["solve"] = solve_section(W, torch)
