@@ -214,7 +214,8 @@ int wd_mhat(void *out, const void *in, const void *gauge, void *tmp, double kapp
  * (H^+ when dagger != 0).  The CTAs that cover the right-hand sides of the
  * same sites run together, so each link comes from memory once per site and
  * serves every right-hand side from cache.  The tile shape (right-hand-side
- * warps per CTA) comes from the autotuner below.  x may be NULL or alias out;
+ * warps per CTA, right-hand sides per thread) comes from the autotuner
+ * below.  x may be NULL or alias out;
  * in must not.  If norm2 != NULL (device, nrhs doubles) it receives
  * ||out_r||^2, summed in a fixed order.  1 <= nrhs <= 32.
  */
@@ -223,9 +224,12 @@ int wd_dslash_mrhs(void *out, const void *in, const void *gauge, int parity, int
                    const int dims[4], int prec, int recon);
 
 /*
- * Autotuner of the multi-right-hand-side tile shape: the right-hand-side
- * warps per CTA (1, 2, 4 or 8) of wd_dslash_mrhs and of the hopping launches
- * of wd_solve_batch (the paper has no such component).
+ * Autotuner of the multi-right-hand-side tile shape of wd_dslash_mrhs and of
+ * the hopping launches of wd_solve_batch (the paper has no such component).
+ * A shape code is w (1, 2, 4 or 8 right-hand-side warps per CTA, one
+ * right-hand side per thread) or, for FP32 only, 16 + w (w = 1, 2 or 4 warps,
+ * two right-hand sides per thread: each link is loaded and rebuilt once for
+ * both).  Every shape gives bit-identical results.
  *
  * enable = 1 (the default): a batch shape (precision, link format, dagger,
  * fused norm, tile count, largest nrhs, problem count) met for the first time
@@ -239,8 +243,9 @@ int wd_dslash_mrhs(void *out, const void *in, const void *gauge, int parity, int
  */
 int wd_set_autotune(int enable);
 
-/* Force one tile shape for every multi-RHS launch (lanes = 1, 2, 4 or 8), or
- * go back to the tuned/default shapes (lanes = 0).  WD_ERR_ARG otherwise. */
+/* Force one tile shape for every multi-RHS launch (lanes = a shape code:
+ * 1, 2, 4, 8, 17, 18 or 20; FP64 and FP16 launches run 16 + w as w), or go
+ * back to the tuned/default shapes (lanes = 0).  WD_ERR_ARG otherwise. */
 int wd_mrhs_set_lanes(int lanes);
 
 /* Text table of the tuned shapes, one line per batch shape with the

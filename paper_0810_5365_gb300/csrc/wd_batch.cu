@@ -108,10 +108,12 @@ static cudaError_t launch_mrhs_raw(int prec, const MrhsBatch& bt, int recon, boo
 // Autotuner of the multi-right-hand-side tile shape.  A batch shape (precision,
 // link format, dagger, fused norm, tile count, largest nrhs, problem count)
 // met for the first time outside stream capture is timed with every shape
-// (1, 2, 4, 8 right-hand-side warps per CTA): one warm-up and three timed
-// launches each, CUDA events on the launching stream, outputs (and norms)
-// redirected to a temporary buffer so that no caller data is written.  The
-// fastest shape is kept for the life of the process.
+// (1, 2, 4, 8 right-hand-side warps per CTA with one right-hand side per
+// thread; for FP32 also 1, 2, 4 warps with two right-hand sides per thread,
+// shape codes MRHS_PAIR + warps): one warm-up and three timed launches each,
+// CUDA events on the launching stream, outputs (and norms) redirected to a
+// temporary buffer so that no caller data is written.  The fastest shape is
+// kept for the life of the process.
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -127,12 +129,19 @@ struct MrhsKey {
   }
 };
 
+constexpr int NSHAPES = 7;
+constexpr int SHAPE_CHOICES[NSHAPES] = {1, 2, 4, 8, MRHS_PAIR + 1, MRHS_PAIR + 2, MRHS_PAIR + 4};
+
 struct MrhsTuned {
-  int lanes;
-  float us[4];  // per candidate, 0 when not timed
+  int lanes;         // the chosen shape code
+  float us[NSHAPES];  // per candidate, 0 when not timed
 };
 
-constexpr int LANE_CHOICES[4] = {1, 2, 4, 8};
+bool valid_shape(int shape) {
+  for (int c = 0; c < NSHAPES; c++)
+    if (SHAPE_CHOICES[c] == shape) return true;
+  return false;
+}
 
 std::map<MrhsKey, MrhsTuned>& tune_table() {
   static std::map<MrhsKey, MrhsTuned> t;
@@ -152,7 +161,10 @@ MrhsKey make_key(int prec, const MrhsBatch& bt, int recon, bool dagger, bool nor
 cudaError_t mrhs_lanes(int prec, const MrhsBatch& bt, int recon, bool dagger, const int* active,
                        RedScratch rs, bool norm, cudaStream_t st, int* lanes) {
   if (g_force_lanes) {
-    *lanes = g_force_lanes;
+    // the pair shapes exist for FP32 only; other precisions take the
+    // one-per-thread shape with the same warps
+    *lanes = (g_force_lanes & MRHS_PAIR) && prec != WD_F32 ? g_force_lanes - MRHS_PAIR
+                                                            : g_force_lanes;
     return cudaSuccess;
   }
   const MrhsKey key = make_key(prec, bt, recon, dagger, norm);
@@ -184,12 +196,13 @@ cudaError_t mrhs_lanes(int prec, const MrhsBatch& bt, int recon, bool dagger, co
   }
   double* nt = norm ? (double*)(buf + 256) : nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  MrhsTuned best{MRHS_LANES, {0.f, 0.f, 0.f, 0.f}};
+  MrhsTuned best{MRHS_LANES, {}};
   float best_us = 0.f;
   e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  for (int c = 0; c < 4 && e == cudaSuccess; c++) {
-    const int L = LANE_CHOICES[c];
+  for (int c = 0; c < NSHAPES && e == cudaSuccess; c++) {
+    const int L = SHAPE_CHOICES[c];
+    if ((L & MRHS_PAIR) && prec != WD_F32) continue;
     e = launch_mrhs_raw(prec, t, recon, dagger, active, rs, nt, L, st);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     for (int k = 0; k < 3 && e == cudaSuccess; k++)
@@ -233,7 +246,7 @@ int set_autotune(int enable) {
 }
 
 int mrhs_set_lanes(int lanes) {
-  if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return WD_ERR_ARG;
+  if (lanes != 0 && !valid_shape(lanes)) return WD_ERR_ARG;
   g_force_lanes = lanes;
   return WD_OK;
 }
@@ -247,9 +260,10 @@ int tune_report(char* buf, size_t len) {
     char line[256];
     std::snprintf(line, sizeof(line),
                   "mrhs prec=%d recon=%d dagger=%d norm=%d tiles=%d maxrhs=%d problems=%d "
-                  "us[1,2,4,8]=%.1f,%.1f,%.1f,%.1f lanes=%d\n",
+                  "us[1,2,4,8,p1,p2,p4]=%.1f,%.1f,%.1f,%.1f,%.1f,%.1f,%.1f shape=%s%d\n",
                   k.prec, k.recon, k.dagger, k.norm, k.ntiles, k.maxr, k.nprob, v.us[0], v.us[1],
-                  v.us[2], v.us[3], v.lanes);
+                  v.us[2], v.us[3], v.us[4], v.us[5], v.us[6], (v.lanes & MRHS_PAIR) ? "p" : "",
+                  v.lanes & ~MRHS_PAIR);
     const size_t n = std::strlen(line);
     if (buf && used + n + 1 <= len) {
       std::memcpy(buf + used, line, n + 1);

@@ -166,6 +166,183 @@ __global__ void __launch_bounds__(MRHS_SUB* LANES, (MrhsMinBlocks<P, NORM, LANES
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 with two right-hand sides per thread.  The link of each hop is loaded
+// and its third row rebuilt once, then multiplies the half spinors of both
+// right-hand sides, so the L1 requests per right-hand-side site drop from
+// 8 * 48 + 8 * 96 + 96 to 8 * 24 + 8 * 96 + 96 bytes and the link
+// instructions are halved.  The price is registers: two accumulators.  Thread
+// (x, y) of block b computes right-hand sides 2 (L (b % G) + y) and the next
+// one, G = ceil(max nrhs / 2L).  When the second right-hand side does not
+// exist or is masked off, the thread still computes it on the first one's
+// field (branch-free, so both hops' loads can be in flight together) and
+// discards it.
+// ---------------------------------------------------------------------------
+constexpr int MRHS_PAIR = 16;  // shape code bit: two right-hand sides per thread
+
+#ifndef WD_MRHS2_MINB4
+#define WD_MRHS2_MINB4 4  // CTAs per SM at 4 warps the pair kernel is budgeted for
+#endif
+template <int LANES>
+struct Mrhs2MinBlocks {
+  static constexpr int raw = WD_MRHS2_MINB4 * 4 / LANES;
+  static constexpr int value = raw < 1 ? 1 : (raw > 32 ? 32 : raw);
+};
+
+template <int RC, int MU, int S, bool FWD>
+__device__ __forceinline__ void hop_pair_f32(cx<float> (&a0)[12], cx<float> (&a1)[12],
+                                             const void* __restrict__ in0,
+                                             const void* __restrict__ in1,
+                                             const void* __restrict__ gauge, int nb, int region,
+                                             int lcb, bool flip, int VP) {
+  cx<float> u[9];
+  load_link<WD_F32, RC, float>(u, gauge, region, lcb, VP);
+  cx<float> h0[6], h1[6];
+  load_project<WD_F32, MU, S, float>(h0, in0, nb, VP);
+  load_project<WD_F32, MU, S, float>(h1, in1, nb, VP);
+  cx<float> t[6];
+#if WD_F32X2
+  su3_mul_f32x2<FWD>(u, h0, t);
+#else
+#error "the pair kernel uses the packed FP32 link product"
+#endif
+  if constexpr (MU == 3) {
+    expand_add<MU, S, false>(a0, t, flip ? -1.f : 1.f);
+  } else {
+    expand_add<MU, S, true>(a0, t, 1.f);
+  }
+  su3_mul_f32x2<FWD>(u, h1, t);
+  if constexpr (MU == 3) {
+    expand_add<MU, S, false>(a1, t, flip ? -1.f : 1.f);
+  } else {
+    expand_add<MU, S, true>(a1, t, 1.f);
+  }
+}
+
+// out = a H in + bx x + cy y for one right-hand side of one site (F32)
+__device__ __forceinline__ void mrhs_epilogue_f32(cx<float> (&acc)[12], const MrhsProblem& pr,
+                                                  int r, int cb, int VP) {
+  const float ca = (float)pr.a;
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
+  if (pr.x) {
+    cx<float> v[12];
+    load_spinor_rw<WD_F32, float>(v, (const char*)pr.x + (size_t)r * pr.s_x, cb, VP);
+    const float cbx = (float)pr.bx;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      acc[k].r = fmaf(cbx, v[k].r, acc[k].r);
+      acc[k].i = fmaf(cbx, v[k].i, acc[k].i);
+    }
+  }
+  if (pr.y) {
+    cx<float> v[12];
+    load_spinor_rw<WD_F32, float>(v, (const char*)pr.y + (size_t)r * pr.s_y, cb, VP);
+    const float ccy = (float)pr.cy;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      acc[k].r = fmaf(ccy, v[k].r, acc[k].r);
+      acc[k].i = fmaf(ccy, v[k].i, acc[k].i);
+    }
+  }
+  store_spinor<WD_F32, float>((char*)pr.out + (size_t)r * pr.s_out, cb, VP, acc);
+}
+
+template <int RC, bool DAG, bool NORM, int LANES>
+__global__ void __launch_bounds__(MRHS_SUB* LANES, (Mrhs2MinBlocks<LANES>::value))
+    mrhs_pair_kernel(const __grid_constant__ MrhsBatch bt, int groups,
+                     const int* __restrict__ active, RedScratch rs) {
+  const int tx = threadIdx.x, ry = threadIdx.y;
+  constexpr int SF = DAG ? -1 : 1;
+  constexpr int SB_ = -SF;
+  constexpr int SUBS = MRHS_BS / MRHS_SUB;
+  const int nprob = bt.nprob;
+  const int sub = blockIdx.x / groups;
+  const int r0 = 2 * ((blockIdx.x - sub * groups) * LANES + ry), r1 = r0 + 1;
+  const int tile = sub / SUBS, q = sub - tile * SUBS;
+  int j = 0;
+  while (j + 1 < nprob && tile >= bt.p[j + 1].tile0) j++;
+  const MrhsProblem& pr = bt.p[j];
+  const int cb = (tile - pr.tile0) * MRHS_BS + q * MRHS_SUB + tx;
+  const bool act0 = r0 < pr.nrhs && (active == nullptr || active[pr.rhs0 + r0] != 0);
+  const bool act1 = r1 < pr.nrhs && (active == nullptr || active[pr.rhs0 + r1] != 0);
+  double nrm0 = 0.0, nrm1 = 0.0;
+  if ((act0 || act1) && cb < pr.g.Vh) {
+    const Geom& g = pr.g;
+    const int p = pr.parity, qq = 1 - p, VP = g.Vh_pad;
+    int x0, x1, x2, x3;
+    cb_coords(cb, p, g, x0, x1, x2, x3);
+    const int row = cb - (x0 >> 1);
+    const int f0 = row + ((x0 + 1 == g.L[0] ? 0 : x0 + 1) >> 1);
+    const int b0 = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
+    const int f1 = x1 == g.L[1] - 1 ? cb - (g.L[1] - 1) * g.S1 : cb + g.S1;
+    const int b1 = x1 == 0 ? cb + (g.L[1] - 1) * g.S1 : cb - g.S1;
+    const int f2 = x2 == g.L[2] - 1 ? cb - (g.L[2] - 1) * g.S2 : cb + g.S2;
+    const int b2 = x2 == 0 ? cb + (g.L[2] - 1) * g.S2 : cb - g.S2;
+    const int f3 = x3 == g.L[3] - 1 ? cb - (g.L[3] - 1) * g.S3 : cb + g.S3;
+    const int b3 = x3 == 0 ? cb + (g.L[3] - 1) * g.S3 : cb - g.S3;
+    const bool fflip = x3 == g.L[3] - 1;
+    const bool bflip = x3 == 0;
+    // an absent or masked right-hand side is computed on the other one's
+    // field and discarded
+    const int ra = act0 ? r0 : r1, rb = act1 ? r1 : r0;
+    const void* in0 = (const char*)pr.in + (size_t)ra * pr.s_in;
+    const void* in1 = (const char*)pr.in + (size_t)rb * pr.s_in;
+    const void* ga = pr.gauge;
+    cx<float> a0[12], a1[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) a0[k] = a1[k] = mk<float>(0.f, 0.f);
+    hop_pair_f32<RC, 0, SF, true>(a0, a1, in0, in1, ga, f0, 0 + p, cb, false, VP);
+    hop_pair_f32<RC, 0, SB_, false>(a0, a1, in0, in1, ga, b0, 0 + qq, b0, false, VP);
+    hop_pair_f32<RC, 1, SF, true>(a0, a1, in0, in1, ga, f1, 2 + p, cb, false, VP);
+    hop_pair_f32<RC, 1, SB_, false>(a0, a1, in0, in1, ga, b1, 2 + qq, b1, false, VP);
+    hop_pair_f32<RC, 2, SF, true>(a0, a1, in0, in1, ga, f2, 4 + p, cb, false, VP);
+    hop_pair_f32<RC, 2, SB_, false>(a0, a1, in0, in1, ga, b2, 4 + qq, b2, false, VP);
+    hop_pair_f32<RC, 3, SF, true>(a0, a1, in0, in1, ga, f3, 6 + p, cb, fflip, VP);
+    hop_pair_f32<RC, 3, SB_, false>(a0, a1, in0, in1, ga, b3, 6 + qq, b3, bflip, VP);
+    if (act0) {
+      mrhs_epilogue_f32(a0, pr, r0, cb, VP);
+      if constexpr (NORM) nrm0 = site_norm2(a0);
+    }
+    if (act1) {
+      mrhs_epilogue_f32(a1, pr, r1, cb, VP);
+      if constexpr (NORM) nrm1 = site_norm2(a1);
+    }
+  }
+  if constexpr (NORM) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nrm0 += __shfl_xor_sync(0xffffffffu, nrm0, o);
+      nrm1 += __shfl_xor_sync(0xffffffffu, nrm1, o);
+    }
+    if (tx == 0 && act0) rs.partials[(size_t)r0 * (bt.ntiles * SUBS) + sub] = nrm0;
+    if (tx == 0 && act1) rs.partials[(size_t)r1 * (bt.ntiles * SUBS) + sub] = nrm1;
+  }
+}
+
+template <int RC, bool DG, bool NM, int L>
+cudaError_t launch_mrhs_pair_one(const MrhsBatch& bt, const int* active, RedScratch rs,
+                                 cudaStream_t st) {
+  int maxr = 1;
+  for (int j = 0; j < bt.nprob; j++) maxr = bt.p[j].nrhs > maxr ? bt.p[j].nrhs : maxr;
+  const int groups = (maxr + 2 * L - 1) / (2 * L);
+  const long long nblk = (long long)bt.ntiles * (MRHS_BS / MRHS_SUB) * groups;
+  mrhs_pair_kernel<RC, DG, NM, L><<<(unsigned)nblk, dim3(MRHS_SUB, L), 0, st>>>(bt, groups,
+                                                                              active, rs);
+  return cudaGetLastError();
+}
+
+template <int RC, bool DG, bool NM>
+cudaError_t launch_mrhs_pair(const MrhsBatch& bt, const int* active, RedScratch rs, int lanes,
+                             cudaStream_t st) {
+  switch (lanes) {
+    case 1: return launch_mrhs_pair_one<RC, DG, NM, 1>(bt, active, rs, st);
+    case 2: return launch_mrhs_pair_one<RC, DG, NM, 2>(bt, active, rs, st);
+    case 4: return launch_mrhs_pair_one<RC, DG, NM, 4>(bt, active, rs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <int P, int RC, bool DG, bool NM, int L>
 cudaError_t launch_mrhs_one(const MrhsBatch& bt, const int* active, RedScratch rs,
                             cudaStream_t st) {
@@ -181,6 +358,11 @@ cudaError_t launch_mrhs_one(const MrhsBatch& bt, const int* active, RedScratch r
 template <int P, int RC, bool DG, bool NM>
 cudaError_t launch_mrhs_lanes(const MrhsBatch& bt, const int* active, RedScratch rs, int lanes,
                               cudaStream_t st) {
+  if (lanes & MRHS_PAIR) {
+    if constexpr (P == WD_F32) return launch_mrhs_pair<RC, DG, NM>(bt, active, rs,
+                                                                    lanes - MRHS_PAIR, st);
+    return cudaErrorInvalidValue;
+  }
   switch (lanes) {
     case 1: return launch_mrhs_one<P, RC, DG, NM, 1>(bt, active, rs, st);
     case 2: return launch_mrhs_one<P, RC, DG, NM, 2>(bt, active, rs, st);

@@ -288,8 +288,9 @@ def wd_set_autotune(enable):
 
 
 def wd_mrhs_set_lanes(lanes):
-    """Force the multi-RHS tile shape (1, 2, 4, 8 right-hand sides per CTA) or
-    return to the tuned shapes (0)."""
+    """Force the multi-RHS tile shape or return to the tuned shapes (0).  Shape
+    codes: 1, 2, 4, 8 right-hand-side warps per CTA with one right-hand side
+    per thread; 17, 18, 20 = 16 + warps with two per thread (FP32)."""
     _ck(lib().wd_mrhs_set_lanes(int(lanes)), "wd_mrhs_set_lanes")
 
 

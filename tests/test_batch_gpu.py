@@ -71,13 +71,20 @@ def _mrhs_run(dims, prec, recon, nrhs, dagger=0):
     return out, nrm, h, U, srcs, xs
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 8])
-@pytest.mark.parametrize("prec,recon", [(W.WD_F64, 18), (W.WD_F32, 12), (W.WD_F16, 12)])
+PAIR = 16  # shape code: two right-hand sides per thread (FP32)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 8, PAIR + 1, PAIR + 2, PAIR + 4])
+@pytest.mark.parametrize("prec,recon", [(W.WD_F64, 18), (W.WD_F32, 12), (W.WD_F32, 18),
+                                        (W.WD_F16, 12)])
 def test_mrhs_every_tile_shape(lanes, prec, recon):
     """Every tile shape the autotuner may choose gives bit-identical fields and
-    norms to the default shape (each thread computes one right-hand side of one
-    site the same way), and both match the oracle; 6x4x4x6 has a ragged last
-    tile and nrhs = 7 leaves idle lanes for lanes = 2, 8."""
+    norms to the default shape (every right-hand side of every site goes
+    through the same operations in the same order, whether a thread holds one
+    right-hand side or two), and both match the oracle; 6x4x4x6 has a ragged
+    last tile and nrhs = 7 leaves idle lanes for lanes = 2, 8 and a thread
+    whose second right-hand side does not exist for the pair shapes (FP64 and
+    FP16 run the pair codes as the one-per-thread shape with as many warps)."""
     dims, nrhs = (6, 4, 4, 6), 7
     try:
         W.wd_mrhs_set_lanes(4)
@@ -97,14 +104,35 @@ def test_mrhs_every_tile_shape(lanes, prec, recon):
 
 
 def test_mrhs_set_lanes_rejects_other_shapes():
-    with pytest.raises(W.WdError):
-        W.wd_mrhs_set_lanes(3)
+    for bad in (3, PAIR, PAIR + 8):
+        with pytest.raises(W.WdError):
+            W.wd_mrhs_set_lanes(bad)
+
+
+def test_batched_solve_pair_shape_is_bit_identical():
+    """A batched solve whose hopping launches hold two right-hand sides per
+    thread gives the same solutions, bit for bit, and the same iteration
+    counts as one right-hand side per thread.  The batch's right-hand sides
+    converge at different iterations, so the convergence mask switches off
+    one member of a thread's pair while the other goes on."""
+    try:
+        W.wd_mrhs_set_lanes(2)
+        rc1, i1, k1 = _batch(W.WD_F32)
+        W.wd_mrhs_set_lanes(PAIR + 2)
+        rc2, i2, k2 = _batch(W.WD_F32)
+    finally:
+        W.wd_mrhs_set_lanes(0)
+    assert rc1 == rc2 == W.WD_OK
+    assert len({d["iters"] for d in i1}) > 1
+    assert [d["iters"] for d in i1] == [d["iters"] for d in i2]
+    for (_, _, _, x1), (_, _, _, x2) in zip(k1, k2):
+        assert np.array_equal(x1, x2)
 
 
 def test_autotuner_times_every_shape_and_leaves_outputs_alone():
-    """A new batch shape is timed with all four tile shapes on temporary
+    """A new FP32 batch shape is timed with all seven tile shapes on temporary
     outputs: the caller's output equals the untuned (default-shape) result
-    exactly, and the report lists the shape with four timings and a choice."""
+    exactly, and the report lists the shape with seven timings and a choice."""
     dims, prec, nrhs = (8, 4, 6, 10), W.WD_F32, 6
     prev = W.wd_set_autotune(0)
     try:
@@ -126,10 +154,11 @@ def test_autotuner_times_every_shape_and_leaves_outputs_alone():
     mine = [l for l in text.splitlines()
             if f"tiles={tiles} " in l and f"maxrhs={nrhs} " in l and "norm=1" in l]
     assert len(mine) == 1, text
-    us = [float(v) for v in mine[0].split("us[1,2,4,8]=")[1].split()[0].split(",")]
-    assert all(v > 0 for v in us)
-    lanes = int(mine[0].split("lanes=")[1])
-    assert lanes in (1, 2, 4, 8) and us[[1, 2, 4, 8].index(lanes)] == min(us)
+    us = [float(v) for v in mine[0].split("us[1,2,4,8,p1,p2,p4]=")[1].split()[0].split(",")]
+    assert len(us) == 7 and all(v > 0 for v in us)
+    shape = mine[0].split("shape=")[1].strip()
+    names = ["1", "2", "4", "8", "p1", "p2", "p4"]
+    assert shape in names and us[names.index(shape)] == min(us)
 
 
 def test_mrhs_agrees_with_single_rhs_kernel():
