@@ -70,6 +70,17 @@ enum { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2 };
  * kernels then treat U_t(x) as the identity on every slice but t = L3-1 and
  * neither load nor apply it. */
 enum { WD_TEMPORAL_GAUGE = 0x100 };
+
+/* OR into the `recon` argument of wd_dslash_ex: FP16 hopping in which each
+ * warp stages the spinors of its +-z and +-t neighbours (four whole 32-site
+ * blocks of the other parity) in shared memory with bulk asynchronous copies
+ * (the TMA engine) while it computes its x and y hops.  Results are
+ * bit-identical to the unstaged kernel.  Requires prec = WD_F16, recon = 12,
+ * no temporal gauge, norm2 == NULL and L0*L1/2 a multiple of 32; WD_ERR_ARG
+ * otherwise.  The wait for the copies is bounded; should it give up, the
+ * kernel writes NaN to the sites of that warp (so any later norm, solve or
+ * check of the output fails) instead of hanging. */
+enum { WD_STAGE_NEIGHBOURS = 0x200 };
 enum { WD_EVEN = 0, WD_ODD = 1, WD_FULL = -1 };
 
 enum {

@@ -32,6 +32,10 @@ cudaError_t wait_selftest(long spins, int* err, cudaStream_t st);
 int set_autotune(int enable);
 int mrhs_set_lanes(int lanes);
 int tune_report(char* buf, size_t len);
+cudaError_t launch_dslash_f16_staged(const DslashArgs& a, int recon, bool dagger, int* flag,
+                                     cudaStream_t st);
+cudaError_t sticky_flag(int** flag);
+void sticky_flag_free();
 }  // namespace wd
 
 using namespace wd;
@@ -122,6 +126,7 @@ void wd_finalize(void) {
   if (s.partials) cudaFree(s.partials);
   if (s.counter) cudaFree(s.counter);
   if (s.dev_flag) cudaFree(s.dev_flag);
+  sticky_flag_free();
   s.partials = nullptr;
   s.counter = nullptr;
   s.dev_flag = nullptr;
@@ -186,7 +191,8 @@ int wd_dslash_ex(void* out, const void* in, const void* gauge, int parity, int d
                  const void* x, double bx, const void* y, double cy, double* norm2,
                  const int dims[4], int prec, int recon) {
   const int tg = (recon & WD_TEMPORAL_GAUGE_BIT) != 0;
-  recon &= ~WD_TEMPORAL_GAUGE_BIT;
+  const int staged = (recon & WD_STAGE_NEIGHBOURS) != 0;
+  recon &= ~(WD_TEMPORAL_GAUGE_BIT | WD_STAGE_NEIGHBOURS);
   WD_TRY(check_dims(dims));
   WD_TRY(check_prec(prec));
   if (!out || !in || !gauge) return WD_ERR_NULL;
@@ -215,6 +221,13 @@ int wd_dslash_ex(void* out, const void* in, const void* gauge, int parity, int d
   d.g = g;
   d.parity = parity;
   d.tg = tg;
+  if (staged) {
+    if (prec != WD_F16 || recon != 12 || tg || norm2 || (g.S2 & 31) != 0) return WD_ERR_ARG;
+    int* flag = nullptr;
+    cudaError_t e = sticky_flag(&flag);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(launch_dslash_f16_staged(d, recon, dagger != 0, flag, state().stream));
+  }
   return cuda_status(launch_dslash(prec, d, recon, dagger != 0, state().stream));
 }
 

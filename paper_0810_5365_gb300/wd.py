@@ -15,6 +15,7 @@ from .build import LIB
 
 WD_F64, WD_F32, WD_F16 = 0, 1, 2
 WD_TEMPORAL_GAUGE = 0x100
+WD_STAGE_NEIGHBOURS = 0x200
 WD_SOLVER_CG, WD_SOLVER_BICGSTAB = 0, 1
 WD_EVEN, WD_ODD, WD_FULL = 0, 1, -1
 
