@@ -77,9 +77,10 @@ enum { WD_TEMPORAL_GAUGE = 0x100 };
  * (the TMA engine) while it computes its x and y hops.  Results are
  * bit-identical to the unstaged kernel.  Requires prec = WD_F16, recon = 12,
  * no temporal gauge, norm2 == NULL and L0*L1/2 a multiple of 32; WD_ERR_ARG
- * otherwise.  The wait for the copies is bounded; should it give up, the
- * kernel writes NaN to the sites of that warp (so any later norm, solve or
- * check of the output fails) instead of hanging. */
+ * otherwise.  The wait for the copies is bounded (wd_set_wait_limit); should
+ * it give up, the kernel writes NaN to the sites of that warp (so any later
+ * norm, solve or check of the output fails) instead of hanging, and raises
+ * the device's fault flag, which wd_async_status reports. */
 enum { WD_STAGE_NEIGHBOURS = 0x200 };
 enum { WD_EVEN = 0, WD_ODD = 1, WD_FULL = -1 };
 
@@ -181,7 +182,10 @@ int wd_dslash_ex(void *out, const void *in, const void *gauge, int parity, int d
 /*
  * wd_dslash_ex_noalloc: wd_dslash_ex (same arguments, same results) for
  * callers that cannot let the library allocate device memory.  The paper has
- * no counterpart; this is an interface addition.
+ * no counterpart; this is an interface addition.  recon takes the same flag
+ * bits as in wd_dslash_ex (| WD_TEMPORAL_GAUGE, | WD_STAGE_NEIGHBOURS, with
+ * the same restrictions); the staged kernel reduces nothing and so uses no
+ * scratch at all.
  *
  * Who needs it: code that records its launches into a CUDA graph by stream
  * capture (allocating during a capture is not allowed), applications whose
@@ -329,6 +333,26 @@ int wd_tc_gemm_bf16(float *D, const void *A, const void *B, int M, int K, int N)
  * (the expected answer), WD_ERR_ARG for spins out of range.  Synchronous.
  */
 int wd_wait_selftest(long long spins);
+
+/*
+ * Bounded waits of the asynchronous kernels (no counterpart in the paper).
+ * The staged hopping kernel (WD_STAGE_NEIGHBOURS) waits for its bulk copies
+ * at most `polls` times (about 100 ns each; default 2^22) before it gives
+ * up, poisons its sites with NaN and raises the device's fault flag.
+ * 0 <= polls <= 2^26 (else WD_ERR_ARG); polls = 0 gives up at once, which
+ * exercises the failure path without any fault.  Applies to the following
+ * launches from this process.
+ */
+int wd_set_wait_limit(long long polls);
+
+/*
+ * Status of the asynchronous bounded waits on the current device: waits for
+ * the work queued on the set stream, then returns WD_ERR_TIMEOUT if a launch
+ * gave up waiting since the last call (and clears the flag), else WD_OK.
+ * A raised flag means every launch since the previous call is untrustworthy.
+ * Allocates nothing.
+ */
+int wd_async_status(void);
 
 /* ------------------------------------------------------------------ */
 /* solver (paper: even-odd preconditioned CG; Fig. 2)                  */

@@ -32,10 +32,6 @@ cudaError_t wait_selftest(long spins, int* err, cudaStream_t st);
 int set_autotune(int enable);
 int mrhs_set_lanes(int lanes);
 int tune_report(char* buf, size_t len);
-cudaError_t launch_dslash_f16_staged(const DslashArgs& a, int recon, bool dagger, int* flag,
-                                     cudaStream_t st);
-cudaError_t sticky_flag(int** flag);
-void sticky_flag_free();
 }  // namespace wd
 
 using namespace wd;
@@ -126,7 +122,6 @@ void wd_finalize(void) {
   if (s.partials) cudaFree(s.partials);
   if (s.counter) cudaFree(s.counter);
   if (s.dev_flag) cudaFree(s.dev_flag);
-  sticky_flag_free();
   s.partials = nullptr;
   s.counter = nullptr;
   s.dev_flag = nullptr;
@@ -223,10 +218,8 @@ int wd_dslash_ex(void* out, const void* in, const void* gauge, int parity, int d
   d.tg = tg;
   if (staged) {
     if (prec != WD_F16 || recon != 12 || tg || norm2 || (g.S2 & 31) != 0) return WD_ERR_ARG;
-    int* flag = nullptr;
-    cudaError_t e = sticky_flag(&flag);
-    if (e != cudaSuccess) return cuda_status(e);
-    return cuda_status(launch_dslash_f16_staged(d, recon, dagger != 0, flag, state().stream));
+    return cuda_status(launch_dslash_f16_staged(d, recon, dagger != 0, state().wait_limit,
+                                                state().stream));
   }
   return cuda_status(launch_dslash(prec, d, recon, dagger != 0, state().stream));
 }
@@ -343,6 +336,18 @@ int wd_tc_gemm_bf16(float* D, const void* A, const void* B, int M, int K, int N)
   WD_TRY(cuda_status(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st)));
   WD_TRY(cuda_status(cudaStreamSynchronize(st)));
   return h ? WD_ERR_TIMEOUT : WD_OK;
+}
+
+int wd_set_wait_limit(long long polls) {
+  if (polls < 0 || polls > (1LL << 26)) return WD_ERR_ARG;
+  state().wait_limit = (long)polls;
+  return WD_OK;
+}
+
+int wd_async_status(void) {
+  int fault = 0;
+  WD_TRY(cuda_status(stage_fault_take(&fault, state().stream)));
+  return fault ? WD_ERR_TIMEOUT : WD_OK;
 }
 
 int wd_wait_selftest(long long spins) {

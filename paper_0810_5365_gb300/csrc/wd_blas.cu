@@ -68,34 +68,6 @@ cudaError_t device_flag(int** flag, cudaStream_t st) {
   return cudaMemsetAsync(s.dev_flag, 0, sizeof(int), st);
 }
 
-// A device int, zeroed once when it is first allocated, for asynchronous
-// kernels whose bounded waits may give up (they also poison their output);
-// it is never reset by the library.
-namespace {
-int* g_sticky = nullptr;
-}
-
-cudaError_t sticky_flag(int** flag) {
-  if (!g_sticky) {
-    int* f = nullptr;
-    cudaError_t e = cudaMalloc(&f, 256);
-    if (e != cudaSuccess) return e;
-    e = cudaMemset(f, 0, 256);
-    if (e != cudaSuccess) {
-      cudaFree(f);
-      return e;
-    }
-    g_sticky = f;
-  }
-  *flag = g_sticky;
-  return cudaSuccess;
-}
-
-void sticky_flag_free() {
-  if (g_sticky) cudaFree(g_sticky);
-  g_sticky = nullptr;
-}
-
 RedScratch scratch() {
   RedScratch r;
   r.partials = state().partials;

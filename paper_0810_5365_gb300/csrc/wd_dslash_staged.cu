@@ -15,9 +15,14 @@
 // are used once per application and are loaded directly.
 //
 // Each warp's mbarrier is used once (phase 0).  The wait is bounded: if it
-// gives up, the kernel sets the sticky *flag, waits once more (bounded) for
-// its copies and writes NaN to that warp's sites, so that the failure shows
-// in any later norm, solve or check of the output.
+// gives up after `spin_limit` polls, the kernel raises the device's fault
+// flag, drains its copies with a second, much longer bounded wait and writes
+// NaN to that warp's sites, so that the failure shows in any later norm,
+// solve or check of the output.  A raised flag marks the whole launch (and
+// any launch since the flag was last read) as untrustworthy, not only the
+// poisoned sites: should even the drain wait give up, the warp exits with a
+// copy possibly still writing into shared memory that the next CTA on that
+// SM may own.
 #include "wd_dslash.cuh"
 #include "wd_tc.cuh"
 
@@ -42,7 +47,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 constexpr int STG_WARPS = 4;           // CTA = 4 site blocks = 128 sites
 constexpr uint32_t STG_SPAN = 1536;    // bytes of one FP16 site block (3 x 32 x 16)
 constexpr uint32_t STG_SCALE = 128;    // bytes of its 32 site scales
-constexpr long STG_SPIN_LIMIT = 1L << 22;
+// polls of the drain wait after a timeout: about 7 s at some 100 ns per poll,
+// far beyond any copy of 6.5 KB
+constexpr long STG_DRAIN_LIMIT = 1L << 26;
+
+// Fault flag of the asynchronous bounded waits, one per device (a __device__
+// variable exists once in every GPU context that loads the library), raised
+// by a timed-out staged launch and read and cleared by stage_fault_take().
+__device__ int g_stage_fault;
 
 struct __align__(16) StageWarp {
   int4 sp[4][3][32];  // [z+, z-, t+, t-][plane][lane]
@@ -59,7 +71,7 @@ __device__ __forceinline__ void fetch_link_f16(RawF16& r, const void* __restrict
 
 template <bool DAG>
 __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>::value)
-    dslash_f16_staged_kernel(const DslashArgs a, int* flag) {
+    dslash_f16_staged_kernel(const DslashArgs a, long spin_limit) {
   __shared__ StageWarp stage[STG_WARPS];
   __shared__ uint64_t bar[STG_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -123,7 +135,7 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
     compute_f16<1, SB_, false>(acc, r3, false);
     fetch_link_f16(r3, a.gauge, 6 + q, b3, VP);
     // far hops from shared memory
-    if (mbar_wait_bounded(&bar[warp], 0, STG_SPIN_LIMIT)) {
+    if (mbar_wait_bounded(&bar[warp], 0, spin_limit)) {
 #pragma unroll
       for (int k = 0; k < 3; k++) {
         r0.s[k] = s.sp[0][k][lane];
@@ -143,10 +155,10 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
       compute_f16<3, SF, true>(acc, r2, fflip);
       compute_f16<3, SB_, false>(acc, r3, bflip);
     } else {
-      if (lane == 0) atomicExch(flag, 1);
-      // the copies may still be in flight: give them one more bounded wait
-      // before the CTA's shared memory is released
-      mbar_wait_bounded(&bar[warp], 0, STG_SPIN_LIMIT);
+      if (lane == 0) atomicExch(&g_stage_fault, 1);
+      // the copies may still be in flight: drain them (bounded, long) before
+      // the CTA's shared memory is released
+      mbar_wait_bounded(&bar[warp], 0, STG_DRAIN_LIMIT);
       // the output of these sites is poisoned (NaN), so that the failure
       // reaches any later norm, solve or check of the result
 #pragma unroll
@@ -182,22 +194,30 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
 
 }  // namespace
 
+namespace {
+constexpr int kMaxDevices = 64;
+bool g_carveout_set[kMaxDevices] = {false};
+}  // namespace
+
 // The staged kernel covers FP16 fields with 12-real links, no temporal gauge
 // and no fused reduction, on lattices whose (z, t) slices hold a multiple of
-// 32 sites of one parity; cudaErrorNotSupported otherwise.
-cudaError_t launch_dslash_f16_staged(const DslashArgs& a, int recon, bool dagger, int* flag,
+// 32 sites of one parity; cudaErrorNotSupported otherwise.  spin_limit: polls
+// of the bounded wait for the copies (0 gives up at once).  Allocates nothing.
+cudaError_t launch_dslash_f16_staged(const DslashArgs& a, int recon, bool dagger, long spin_limit,
                                      cudaStream_t st) {
   const Geom& g = a.g;
-  if (recon != 12 || a.tg || a.norm_out || (g.S2 & 31) != 0 || flag == nullptr)
+  if (recon != 12 || a.tg || a.norm_out || (g.S2 & 31) != 0 || spin_limit < 0)
     return cudaErrorNotSupported;
   const int nblk = g.Vh / 32;
   dim3 grid((nblk + STG_WARPS - 1) / STG_WARPS), block(STG_WARPS * 32);
-  static bool carveout = false;
-  if (!carveout) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  // the carveout is a per-device function attribute: set it once per device
+  if (dev >= 0 && dev < kMaxDevices && !g_carveout_set[dev]) {
     // shared memory for the register budget's CTAs per SM and no more: the
     // rest of the unified L1 keeps serving the near neighbours and links
-    int dev = 0, smem_sm = 0;
-    cudaGetDevice(&dev);
+    int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     const long need = (long)DslashMinBlocks<WD_F16, false>::value *
                       (long)(sizeof(StageWarp) * STG_WARPS + 64);
@@ -208,13 +228,31 @@ cudaError_t launch_dslash_f16_staged(const DslashArgs& a, int recon, bool dagger
     cudaFuncSetAttribute(dslash_f16_staged_kernel<true>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaGetLastError();
-    carveout = true;
+    g_carveout_set[dev] = true;
   }
   if (dagger)
-    dslash_f16_staged_kernel<true><<<grid, block, 0, st>>>(a, flag);
+    dslash_f16_staged_kernel<true><<<grid, block, 0, st>>>(a, spin_limit);
   else
-    dslash_f16_staged_kernel<false><<<grid, block, 0, st>>>(a, flag);
+    dslash_f16_staged_kernel<false><<<grid, block, 0, st>>>(a, spin_limit);
   return cudaGetLastError();
+}
+
+// Read and clear the current device's fault flag after the work queued on
+// `st` has finished (synchronises st).  *fault = 1 if a staged launch gave up
+// waiting since the flag was last cleared.  Allocates nothing.
+cudaError_t stage_fault_take(int* fault, cudaStream_t st) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&h, g_stage_fault, sizeof(int), 0,
+                                            cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && h) {
+    static const int zero = 0;
+    e = cudaMemcpyToSymbolAsync(g_stage_fault, &zero, sizeof(int), 0, cudaMemcpyHostToDevice,
+                                st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  *fault = h;
+  return e;
 }
 
 }  // namespace wd

@@ -70,6 +70,15 @@ cudaError_t launch_dslash_f64(const DslashArgs& a, int recon, bool dagger, cudaS
 cudaError_t launch_dslash_f32(const DslashArgs& a, int recon, bool dagger, cudaStream_t st);
 cudaError_t launch_dslash_f16(const DslashArgs& a, int recon, bool dagger, cudaStream_t st);
 
+// FP16 hopping with the +-z, +-t neighbours staged in shared memory by bulk
+// copies (wd_dslash_staged.cu); spin_limit bounds the wait for the copies.
+// A launch whose wait gave up raises the device's fault flag, which
+// stage_fault_take reads and clears (after synchronising st).  Neither
+// allocates.
+cudaError_t launch_dslash_f16_staged(const DslashArgs& a, int recon, bool dagger,
+                                     long spin_limit, cudaStream_t st);
+cudaError_t stage_fault_take(int* fault, cudaStream_t st);
+
 inline cudaError_t launch_dslash(int prec, const DslashArgs& a, int recon, bool dagger,
                                  cudaStream_t st) {
   switch (prec) {
@@ -94,6 +103,8 @@ struct State {
   size_t partials_cap = 0;  // doubles
   int num_sms = 0;
   int* dev_flag = nullptr;  // device int: set by kernels whose bounded waits gave up
+  // polls of the first bounded wait of the asynchronous kernels (wd_set_wait_limit)
+  long wait_limit = 1L << 22;
 };
 
 State& state();

@@ -41,6 +41,10 @@ extern "C" int wd_dslash_ex_noalloc(void* out, const void* in, const void* gauge
                                     const void* y, double cy, double* norm2, const int dims[4],
                                     int prec, int recon) {
   // ---- validation, all on the host, before any CUDA call ----
+  // the flag bits of wd_dslash_ex: temporal-gauge links, staged neighbours
+  const int tg = (recon & WD_TEMPORAL_GAUGE_BIT) != 0;
+  const int staged = (recon & WD_STAGE_NEIGHBOURS) != 0;
+  recon &= ~(WD_TEMPORAL_GAUGE_BIT | WD_STAGE_NEIGHBOURS);
   if (!dims) return WD_ERR_NULL;
   long long V = 1;
   for (int i = 0; i < 4; i++) {
@@ -59,6 +63,32 @@ extern "C" int wd_dslash_ex_noalloc(void* out, const void* in, const void* gauge
   const Geom g = make_geom(dims);
   const long long ctas = (g.Vh + DSLASH_BS - 1) / DSLASH_BS;
   if (ctas > kMaxPartials) return WD_ERR_SCRATCH;
+  if (staged && (prec != WD_F16 || recon != 12 || tg || norm2 || (g.S2 & 31) != 0))
+    return WD_ERR_ARG;
+  cudaStream_t st = state().stream;
+  if (staged) {
+    // no reduction, hence no scratch: the staged kernel's fault flag is a
+    // __device__ variable of the library as well
+    DslashArgs d;
+    d.out = out;
+    d.in = in;
+    d.gauge = gauge;
+    d.x = x;
+    d.y = y;
+    d.a = a;
+    d.bx = bx;
+    d.cy = cy;
+    d.norm_out = nullptr;
+    d.rs = RedScratch{};
+    d.g = g;
+    d.parity = parity;
+    cudaError_t es = launch_dslash_f16_staged(d, recon, dagger != 0, state().wait_limit, st);
+    if (es != cudaSuccess) {
+      state().last_cuda_error = (int)es;
+      return WD_ERR_CUDA;
+    }
+    return WD_OK;
+  }
 
   // ---- once per device: the device address of the fixed scratch ----
   int dev = 0;
@@ -80,7 +110,6 @@ extern "C" int wd_dslash_ex_noalloc(void* out, const void* in, const void* gauge
   RedScratch rs;
   rs.partials = g_scratch_addr[dev];
   rs.counter = reinterpret_cast<unsigned*>(g_scratch_addr[dev] + kMaxPartials);
-  cudaStream_t st = state().stream;
   if (norm2) {
     // the counter must start at zero; the array keeps whatever the last call left
     e = cudaMemsetAsync(rs.counter, 0, sizeof(unsigned), st);
@@ -102,6 +131,7 @@ extern "C" int wd_dslash_ex_noalloc(void* out, const void* in, const void* gauge
   d.rs = rs;
   d.g = g;
   d.parity = parity;
+  d.tg = tg;
   e = launch_dslash(prec, d, recon, dagger != 0, st);
   if (e != cudaSuccess) {
     state().last_cuda_error = (int)e;

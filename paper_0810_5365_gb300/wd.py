@@ -43,7 +43,7 @@ EXPORTS = [
     "wd_rotate_spinor", "wd_tc_gemm_bf16", "wd_nn_train_params_default", "wd_nn_init",
     "wd_nn_apply", "wd_nn_train", "wd_solve_fgcr", "wd_nn_layer", "wd_gaussian_spinor",
     "wd_nn_wgrad", "wd_set_autotune", "wd_mrhs_set_lanes", "wd_tune_report",
-    "wd_wait_selftest",
+    "wd_wait_selftest", "wd_set_wait_limit", "wd_async_status",
 ]
 
 WD_NN_PARAMS = 2304
@@ -146,6 +146,8 @@ def lib():
                                      C.c_int, dp, i4, C.c_int, C.c_int]),
         "wd_set_autotune": (C.c_int, [C.c_int]),
         "wd_wait_selftest": (C.c_int, [C.c_longlong]),
+        "wd_set_wait_limit": (C.c_int, [C.c_longlong]),
+        "wd_async_status": (C.c_int, []),
         "wd_mrhs_set_lanes": (C.c_int, [C.c_int]),
         "wd_tune_report": (C.c_int, [C.c_char_p, C.c_size_t]),
         "wd_solve_batch": (C.c_int, [C.POINTER(wd_batch_problem), C.c_int,
@@ -280,6 +282,20 @@ def wd_wait_selftest(spins):
     """Run the bounded-wait failure path on purpose; returns the status
     (WD_ERR_TIMEOUT is the expected answer)."""
     return int(lib().wd_wait_selftest(int(spins)))
+
+
+def wd_set_wait_limit(polls):
+    """Polls of the bounded wait of the asynchronous (staged) kernels."""
+    _ck(lib().wd_set_wait_limit(int(polls)), "wd_set_wait_limit")
+
+
+def wd_async_status():
+    """WD_OK, or WD_ERR_TIMEOUT if an asynchronous launch gave up waiting since
+    the last call (the flag is cleared); waits for the set stream."""
+    rc = int(lib().wd_async_status())
+    if rc not in (WD_OK, WD_ERR_TIMEOUT):
+        raise WdError(rc, "wd_async_status")
+    return rc
 
 
 def wd_set_autotune(enable):

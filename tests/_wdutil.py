@@ -56,3 +56,21 @@ def rel_l2(a, b):
 def rel_max(a, b):
     """largest elementwise error relative to the largest reference magnitude"""
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def temporal_gauge_links(U, dims):
+    """Links in temporal gauge, made on the host from the definition:
+    omega(x, 0) = 1, omega(x, t+1) = omega(x, t) U_t(x, t) and
+    U'_mu(x) = omega(x) U_mu(x) omega(x+mu)^+, with U'_t set to the exact
+    identity off the last time slice (the form the hopping kernels assume
+    under WD_TEMPORAL_GAUGE).  Returns (U', omega)."""
+    from tests.test_oracle_pins import gauge_rotate
+    V = int(np.prod(dims))
+    S = int(dims[0]) * int(dims[1]) * int(dims[2])
+    om = np.zeros((V, 3, 3), dtype=np.complex128)
+    om[:S] = np.eye(3)
+    for t in range(int(dims[3]) - 1):
+        om[(t + 1) * S:(t + 2) * S] = om[t * S:(t + 1) * S] @ U[3][t * S:(t + 1) * S]
+    Up = gauge_rotate(U, om, dims)
+    Up[3][: (int(dims[3]) - 1) * S] = np.eye(3)
+    return Up, om

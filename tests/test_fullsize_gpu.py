@@ -8,7 +8,10 @@ bench.py times, on outputs the oracle computes site by site.
 * the mixed-precision solve on 24^3x48 (FP16 inner CG at kappa = 0.137,
   FP16 inner BiCGstab in temporal gauge at kappa = 0.130), judged by the
   oracle's own true residual over the whole lattice;
-* the 12-right-hand-side multi-RHS dslash on 24^3x48, sampled per RHS.
+* the 12-right-hand-side multi-RHS dslash on 24^3x48, sampled per RHS;
+* the FP16 kernel with staged z and t neighbours on 32^3x64, bit for bit
+  against the unstaged FP16 kernel (both parities, H and H^+), which covers
+  the z and t wrap blocks at full size.
 """
 import numpy as np
 import pytest
@@ -43,6 +46,23 @@ def _even_samples(dims, n, seed):
 @pytest.fixture(scope="module")
 def headline_fields():
     return fields.su3_links(HEADLINE), fields.gaussian_spinor(HEADLINE)
+
+
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_headline_staged_f16_bit_exact(headline_fields, dagger):
+    U, psi = headline_fields
+    g = pack_gauge(U, HEADLINE, W.WD_F16, 12)
+    for p in (W.WD_EVEN, W.WD_ODD):
+        a = pack_spinor(fields.to_half(psi, HEADLINE, 1 - p), HEADLINE, 1 - p, W.WD_F16)
+        ref = W.alloc_spinor(HEADLINE, p, W.WD_F16)
+        out = W.alloc_spinor(HEADLINE, p, W.WD_F16)
+        W.wd_dslash_ex(ref, a, g, p, dagger, -KAPPA, None, 0.0, None, 0.0, None, HEADLINE,
+                       W.WD_F16, 12)
+        W.wd_dslash_ex(out, a, g, p, dagger, -KAPPA, None, 0.0, None, 0.0, None, HEADLINE,
+                       W.WD_F16, 12 | W.WD_STAGE_NEIGHBOURS)
+        torch.cuda.synchronize()
+        assert W.wd_async_status() == W.WD_OK
+        assert torch.equal(out, ref), (p, dagger)
 
 
 @pytest.mark.parametrize("prec,recon", [(W.WD_F32, 12), (W.WD_F16, 12), (W.WD_F64, 18)])

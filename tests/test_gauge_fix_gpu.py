@@ -18,6 +18,7 @@ from synth import fields
 from tests._wdutil import (PREC_TOL, dev, host, pack_gauge, pack_spinor, rel_l2, rel_max,
                            unpack_spinor)
 from tests.test_oracle_pins import gauge_rotate
+from tests._wdutil import temporal_gauge_links
 
 pytestmark = pytest.mark.gpu
 
@@ -59,8 +60,9 @@ def test_temporal_gauge_transformation(dims):
 @pytest.mark.parametrize("prec,recon", [(W.WD_F64, 18), (W.WD_F32, 12), (W.WD_F16, 12)])
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_temporal_gauge_dslash(dims, prec, recon, dagger):
+    # the oracle's links come from the host definition, not from the GPU
     U = fields.su3_links(dims, workers=1)
-    Up, _ = fix(U, dims)
+    Up, _ = temporal_gauge_links(U, dims)
     psi = fields.gaussian_spinor(dims)
     g = pack_gauge(Up, dims, prec, recon)
     for p in (0, 1):
@@ -78,7 +80,7 @@ def test_temporal_gauge_dslash(dims, prec, recon, dagger):
 def test_temporal_gauge_covariance_full_operator():
     dims, kappa = (4, 4, 4, 8), 0.12
     U = fields.su3_links(dims, workers=1)
-    Up, om = fix(U, dims)
+    Up, om = temporal_gauge_links(U, dims)
     psi = fields.gaussian_spinor(dims)
     g = pack_gauge(Up, dims, W.WD_F64, 18)
     rot = np.einsum("xab,xsb->xsa", om, psi)

@@ -81,3 +81,41 @@ def test_staged_rejects_what_it_does_not_cover(case):
     recon = STAGED | (W.WD_TEMPORAL_GAUGE if case == "gauge" else 0)
     with pytest.raises(W.WdError):
         W.wd_dslash_ex(out, inp, g, 0, 0, 1.0, None, 0.0, None, 0.0, nrm, dims, prec, recon)
+
+
+def test_staged_wait_timeout_is_reported_and_recoverable():
+    """The failure path of the staged kernel's bounded wait, run on purpose
+    and without any fault: with a wait limit of 0 polls every warp gives up
+    at once, drains its copies with the long second wait, writes NaN and
+    raises the device flag; wd_async_status reports WD_ERR_TIMEOUT once and
+    clears it, and the next launch with the default limit is exact."""
+    dims = (8, 8, 6, 4)
+    U = fields.su3_links(dims, workers=1)
+    psi = fields.gaussian_spinor(dims)
+    g = pack_gauge(U, dims, F16, 12)
+    src = oracle.restrict(psi, dims, 1)
+    inp = pack_spinor(src, dims, 1, F16)
+    ref = W.alloc_spinor(dims, 0, F16)
+    W.wd_dslash_ex(ref, inp, g, 0, 0, 1.0, None, 0.0, None, 0.0, None, dims, F16, 12)
+    want = unpack_spinor(ref, dims, 0, F16)
+    assert W.wd_async_status() == W.WD_OK
+    out = W.alloc_spinor(dims, 0, F16)
+    try:
+        W.wd_set_wait_limit(0)
+        W.wd_dslash_ex(out, inp, g, 0, 0, 1.0, None, 0.0, None, 0.0, None, dims, F16, STAGED)
+        assert W.wd_async_status() == W.WD_ERR_TIMEOUT
+    finally:
+        W.wd_set_wait_limit(1 << 22)
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(unpack_spinor(out, dims, 0, F16).real))
+    assert W.wd_async_status() == W.WD_OK  # cleared on read
+    W.wd_dslash_ex(out, inp, g, 0, 0, 1.0, None, 0.0, None, 0.0, None, dims, F16, STAGED)
+    assert W.wd_async_status() == W.WD_OK
+    assert np.array_equal(unpack_spinor(out, dims, 0, F16), want)
+
+
+def test_wait_limit_range():
+    with pytest.raises(W.WdError):
+        W.wd_set_wait_limit(-1)
+    with pytest.raises(W.WdError):
+        W.wd_set_wait_limit((1 << 26) + 1)

@@ -58,3 +58,64 @@ def test_noalloc_matches_wd_dslash_ex_on_two_calls(prec, recon):
             assert rel_l2(got, want) <= tol, (call, rel_l2(got, want))
             assert rel_max(got, want) <= 4 * tol, (call, rel_max(got, want))
             assert abs(n.item() - nref.item()) <= 1e-12 * nref.item(), (call, n.item(), nref.item())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,recon", [(W.WD_F64, 18), (W.WD_F32, 12), (W.WD_F16, 12)])
+def test_noalloc_temporal_gauge_links(prec, recon):
+    """recon | WD_TEMPORAL_GAUGE, as wd_dslash_ex takes it: the same field and
+    norm as wd_dslash_ex, and the oracle's hop on the temporal-gauge links
+    (made on the host from their definition), on two calls in a row."""
+    from tests._wdutil import temporal_gauge_links
+    import oracle
+
+    dims = (6, 4, 4, 8)
+    U = fields.su3_links(dims, workers=1)
+    Up, _ = temporal_gauge_links(U, dims)
+    psi = fields.gaussian_spinor(dims)
+    g = pack_gauge(Up, dims, prec, recon)
+    flags = recon | W.WD_TEMPORAL_GAUGE
+    for p in (W.WD_EVEN, W.WD_ODD):
+        src = fields.to_half(psi, dims, 1 - p)
+        inp = pack_spinor(src, dims, 1 - p, prec)
+        ref = W.alloc_spinor(dims, p, prec)
+        nref = torch.zeros(1, dtype=torch.float64, device="cuda")
+        W.wd_dslash_ex(ref, inp, g, p, 1, 1.0, None, 0.0, None, 0.0, nref, dims, prec, flags)
+        want = oracle.hop_block(p, src, Up, dims, dagger=True)
+        for call in range(2):
+            out = W.alloc_spinor(dims, p, prec)
+            n = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+            W.wd_dslash_ex_noalloc(out, inp, g, p, 1, 1.0, None, 0.0, None, 0.0, n, dims, prec,
+                                   flags)
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref), (p, call)
+            assert n.item() == nref.item(), (p, call)
+            got = unpack_spinor(out, dims, p, prec)
+            assert rel_l2(got, want) <= PREC_TOL[prec], (p, call)
+            assert rel_max(got, want) <= 4 * PREC_TOL[prec], (p, call)
+
+
+@pytest.mark.gpu
+def test_noalloc_staged_neighbours():
+    """12 | WD_STAGE_NEIGHBOURS through the allocation-free entry point: bit
+    for bit the unstaged FP16 field, with no fault raised; and the flag
+    combinations that wd_dslash_ex refuses are refused here too."""
+    dims = (8, 8, 6, 4)
+    U = fields.su3_links(dims, workers=1)
+    g = pack_gauge(U, dims, W.WD_F16, 12)
+    inp = pack_spinor(fields.to_half(fields.gaussian_spinor(dims), dims, 1), dims, 1, W.WD_F16)
+    ref = W.alloc_spinor(dims, 0, W.WD_F16)
+    W.wd_dslash_ex(ref, inp, g, 0, 0, -0.13, None, 0.0, None, 0.0, None, dims, W.WD_F16, 12)
+    for call in range(2):
+        out = W.alloc_spinor(dims, 0, W.WD_F16)
+        W.wd_dslash_ex_noalloc(out, inp, g, 0, 0, -0.13, None, 0.0, None, 0.0, None, dims,
+                               W.WD_F16, 12 | W.WD_STAGE_NEIGHBOURS)
+        assert W.wd_async_status() == W.WD_OK
+        assert torch.equal(out, ref), call
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for recon, norm in [(12 | W.WD_STAGE_NEIGHBOURS, nrm),
+                        (12 | W.WD_STAGE_NEIGHBOURS | W.WD_TEMPORAL_GAUGE, None)]:
+        with pytest.raises(W.WdError) as e:
+            W.wd_dslash_ex_noalloc(out, inp, g, 0, 0, 1.0, None, 0.0, None, 0.0, norm, dims,
+                                   W.WD_F16, recon)
+        assert e.value.status == W.WD_ERR_ARG
