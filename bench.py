@@ -19,14 +19,16 @@ The JSON line (rank 0) carries, besides metric/value/unit:
   e2e           the headline through the C ABI with pinned host buffers and
                 the copies inside the timed region (pipelined over streams);
   clocks        SM clocks and throttle reasons sampled during the timing;
-  cpu_baseline  the FP64 oracle on the host cores (and one thread), plus a
-                per-iteration oracle CG time on 24^3x48;
+  summary       the figures of the sections below in a few short keys;
+  cpu_baseline  the FP64 oracle on the host cores (and one thread), plus the
+                oracle's plain FP64 CG to 1e-10 on 24^3x48, timed whole;
   solve         time to a 1e-10 true residual on 24^3x48: mixed-precision CG
                 and BiCGstab against plain FP64 CG;
   batch         batched multi-right-hand-side solves against the same solves
                 one at a time, and the autotuner's tile shapes;
-  learned_preconditioner  training, and FGCR with the network against plain
-                GCR and CG.
+  learned_preconditioner  training at kappa = 0.137, and flexible CG with the
+                preconditioner N N^+ (trained network, untrained series, none)
+                against plain FP64 CG and mixed CG on 16^3x32 and 32^3x64.
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead
 (bounded sample per step).  ``--profile NAME`` runs a short fixed workload for
 an ncu capture.
@@ -218,19 +220,55 @@ def cpu_baseline(U, psi, dims, budget_s=12.0):
     return out
 
 
-def oracle_cg_estimate(budget_iters=4):
-    """Plain FP64 CG of the oracle on the 24^3x48 solve problem, estimated:
-    the time of a few iterations (two D applications each, all host cores)
-    times the iteration count the GPU's plain FP64 CG needs."""
+def oracle_cg_full(maxiter=4000):
+    """Plain FP64 CG of the oracle (CG on D^+ D of the full lattice, two D
+    applications per iteration, all host cores) on the 24^3x48 solve problem
+    of the GPU's solve comparison, run to a 1e-10 true residual and timed."""
     import oracle
     from synth import fields
     oracle.set_threads(os.cpu_count() or 1)
     U = fields.su3_links(SOLVE_DIMS)
     b = fields.gaussian_spinor(SOLVE_DIMS, seed=2025)
     t0 = time.perf_counter()
-    _, its, _, _ = oracle.cgnr(b, U, SOLVE_DIMS, SOLVE_KAPPA, 1e-10, budget_iters)
+    _, its, rel, ok = oracle.cgnr(b, U, SOLVE_DIMS, SOLVE_KAPPA, 1e-10, maxiter)
     dt = time.perf_counter() - t0
-    return dt / max(its, 1)
+    return {"wall_s": dt, "iterations": its, "true_residual": rel, "converged": bool(ok),
+            "cores": oracle.get_threads(), "kind": "measured",
+            "problem": "24^3x48, kappa 0.137, complex Gaussian b (seed 2025), tol 1e-10"}
+
+
+def compact_summary(line):
+    """The figures of the sub-sections in a few short keys, so that they sit
+    near the start of the JSON line."""
+    sm = {"dslash_f32_frac": round(line["roofline"]["frac"], 3),
+          "variants_frac": {k: round(v["frac"], 3) for k, v in line["variants"].items()},
+          "variants_us": {k: round(v["ms_per_step"] * 1e3, 1) for k, v in line["variants"].items()}}
+    if "solve" in line:
+        sm["solve_24x48_s_iters_speedup"] = {
+            k: [round(v["wall_s"], 4), v["iters"], round(v.get("speedup_vs_f64", 1.0), 2)]
+            for k, v in line["solve"].items() if k != "config"}
+    if "batch" in line:
+        bt = line["batch"]
+        sm["batch_s_vs_sequential_vs_f64"] = {
+            f"{k}_{inner}": [round(v["batched"][inner]["wall_s"], 4),
+                             round(v["batched"][inner]["speedup_vs_sequential_same_inner"], 2),
+                             round(v["batched"][inner]["speedup_vs_plain_f64"], 2)]
+            for k, v in bt.items() if isinstance(v, dict) and "batched" in v
+            for inner in v["batched"]}
+        if "mrhs_dslash" in bt:
+            sm["mrhs_dslash_12rhs_24x48"] = {"us": round(bt["mrhs_dslash"]["us_per_launch"], 1),
+                                             "gbs": round(bt["mrhs_dslash"]["gbs"], 0)}
+    if "learned_preconditioner" in line:
+        lp = line["learned_preconditioner"]
+        sm["learned_k137_s_iters"] = {
+            d: {k: [round(v["wall_s"], 4), v["iters"]] for k, v in r.items()}
+            for d, r in lp.items() if d not in ("training", "config")}
+        sm["learned_training"] = {k: lp["training"][k] for k in ("loss_first", "loss_last",
+                                                                 "wall_s")}
+    if "cpu_baseline" in line and "oracle_cg_24x24x24x48" in line["cpu_baseline"]:
+        oc = line["cpu_baseline"]["oracle_cg_24x24x24x48"]
+        sm["oracle_cg_24x48_s_iters"] = [round(oc["wall_s"], 1), oc["iterations"]]
+    return sm
 
 
 def headline_config(dims, world):
@@ -561,22 +599,20 @@ def batch_section(W, torch):
     return out
 
 
-NN_KAPPA = 0.1300     # below the critical region of these links (restarted GCR converges)
-NN_GCR_M = 16        # Krylov vectors kept between FP64 restarts
-NN_MAXITER = 3000    # cap for the (F)GCR runs (a non-converged run reports its status)
+NN_KAPPA = 0.1370     # BASELINE config 5: beyond the critical region of these links
 
 
-def nn_section(W, torch):
-    """Learned gauge-covariant preconditioner in flexible GCR: train on
-    16^3x32 (4096 on-GPU pairs (D x, x), Adam, starting from the hopping
+def nn_section(W, torch, U_big):
+    """Learned gauge-covariant preconditioner at kappa = 0.137 (beyond the
+    critical region of these links, where restarted GCR on D stagnates): train
+    on 16^3x32 (4096 on-GPU pairs (D x, x), Adam, starting from the hopping
     series 1 + kH + k^2H^2 + k^3H^3), then time-to-1e-10 on 16^3x32 and 32^3x64
-    (the network is local and gauge covariant, so the weights trained on the
-    small lattice serve the large one) against plain GCR, the untrained series
-    and plain FP64 CG (and the mixed-precision CG) on the same GPU.
-    kappa = 0.130: on these synthetic links the spectrum of D encloses the
-    origin from about kappa = 0.13 on, where every restarted minimal-residual
-    method stagnates (FP64 GCR(16) on the CPU included) while CG on the normal
-    equations still converges."""
+    of flexible CG on D^+ D with the preconditioner N N^+ for the trained
+    network, the untrained series and no network (plain CGNR), against plain
+    FP64 even-odd CG and the mixed-precision even-odd CG on the same GPU.  The
+    network is local and gauge covariant, so the weights trained on the small
+    lattice serve the large one.  Every time is one solve after a short
+    warm-up solve; the true residual is the solver's FP64 one."""
     from synth import fields
     out = {}
     train_dims = (16, 16, 16, 32)
@@ -595,26 +631,26 @@ def nn_section(W, torch):
     out["training"] = tinfo
     series = torch.zeros_like(w)
     W.wd_nn_init(series, NN_KAPPA)
-    for dims, seed in ((train_dims, 1234), ((32, 32, 32, 64), 1234)):
-        Uh = U if dims == train_dims else fields.su3_links(dims, seed=seed)
+    for dims in (train_dims, (32, 32, 32, 64)):
+        Uh = U if dims == train_dims else U_big
         Ug = torch.from_numpy(Uh.view(np.float64).reshape(-1)).cuda()
         b = torch.from_numpy(fields.gaussian_spinor(dims, seed=2026).view(np.float64)
                              .reshape(-1)).cuda()
         x = torch.zeros_like(b)
         res = {}
-        warm = W.wd_solve_params_default()
-        warm.maxiter = 20
-        for name, wts in (("fgcr_trained", w), ("fgcr_series", series), ("gcr_plain", None)):
-            W.wd_solve_fgcr(x, b, Ug, NN_KAPPA, dims, wts, NN_GCR_M, warm, check=False)  # warm-up
+        for name, wts in (("fcg_trained", w), ("fcg_series", series), ("cgnr_plain", None)):
+            q = W.wd_solve_params_default()
+            q.maxiter = 5
+            W.wd_solve_fcg(x, b, Ug, NN_KAPPA, dims, wts, q, check=False)  # warm-up
             x.zero_()
             q = W.wd_solve_params_default()
-            q.maxiter = NN_MAXITER
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            info = W.wd_solve_fgcr(x, b, Ug, NN_KAPPA, dims, wts, NN_GCR_M, q, check=False)
+            info = W.wd_solve_fcg(x, b, Ug, NN_KAPPA, dims, wts, q, check=False)
             torch.cuda.synchronize()
             res[name] = {"wall_s": time.perf_counter() - t0, "iters": info["iters"],
-                         "restarts": info["reliable_updates"], "status": info["status"],
+                         "reliable_updates": info["reliable_updates"], "status": info["status"],
+                         "fallback_iters": info["fallback_iters"],
                          "true_residual": info["true_residual"]}
         for name, inner in (("cg_plain_f64", W.WD_F64), ("cg_mixed_f16", W.WD_F16)):
             q = W.wd_solve_params_default()
@@ -629,7 +665,7 @@ def nn_section(W, torch):
             torch.cuda.synchronize()
             res[name] = {"wall_s": time.perf_counter() - t0, "iters": info["iters"],
                          "status": info["status"], "true_residual": info["true_residual"]}
-        for name in ("fgcr_trained", "fgcr_series", "gcr_plain", "cg_mixed_f16"):
+        for name in ("fcg_trained", "fcg_series", "cgnr_plain", "cg_mixed_f16"):
             res[name]["speedup_vs_plain_f64_cg"] = (res["cg_plain_f64"]["wall_s"]
                                                     / res[name]["wall_s"])
         out["x".join(map(str, dims))] = res
@@ -637,8 +673,9 @@ def nn_section(W, torch):
         torch.cuda.empty_cache()
     out["config"] = {"kappa": NN_KAPPA, "network": "3 layers, 12->24->24->12 complex channels, "
                      "nearest-neighbour gauge-covariant, BF16 tensor-core contraction (tcgen05), "
-                     "FP32 accumulation", "gcr_restart": NN_GCR_M,
-                     "gcr_maxiter": NN_MAXITER, "tol": 1e-10}
+                     "FP32 accumulation", "solver": "flexible CG on D^+ D, preconditioner N N^+, "
+                     "FP32 vectors, FP64 reliable updates every 50 iterations; plain CG fallback",
+                     "tol": 1e-10}
     return out
 
 
@@ -936,21 +973,27 @@ def run_ours(args, rank, world, local):
         torch.cuda.empty_cache()
         line["batch"] = batch_section(W, torch)
         torch.cuda.empty_cache()
-        line["learned_preconditioner"] = nn_section(W, torch)
+        line["learned_preconditioner"] = nn_section(W, torch, U)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(U, psi, dims)
-        if "solve" in line:
-            # plain FP64 CG of the oracle (full system, 2 D applications per
-            # iteration), per iteration, and scaled to the iteration count of
-            # the GPU's plain FP64 CG at the same kappa: an estimate
-            spi = oracle_cg_estimate()
-            its = line["solve"]["f64"]["iters"]
-            line["cpu_baseline"]["oracle_cg_24x24x24x48"] = {
-                "s_per_iteration": spi, "estimated_s": spi * its, "iterations_assumed": its,
-                "kind": "estimate: oracle CGNR time per iteration x GPU plain FP64 CG "
-                        "iterations", "gpu_plain_f64_cg_s": line["solve"]["f64"]["wall_s"]}
+        if "solve" in line and not args.no_oracle_cg:
+            # the oracle's plain FP64 CG to 1e-10 on the solve problem, timed
+            # whole (about 100 s on 16 host cores), beside the GPU's solves
+            oc = oracle_cg_full()
+            oc["gpu_plain_f64_cg_s"] = line["solve"]["f64"]["wall_s"]
+            oc["gpu_mixed_f16_cg_s"] = line["solve"]["f16"]["wall_s"]
+            oc["gpu_plain_f64_speedup"] = oc["wall_s"] / oc["gpu_plain_f64_cg_s"]
+            oc["gpu_mixed_f16_speedup"] = oc["wall_s"] / oc["gpu_mixed_f16_cg_s"]
+            line["cpu_baseline"]["oracle_cg_24x24x24x48"] = oc
     if rank == 0:
+        # the compact summary right after the config, ahead of the long sections
+        head = {}
+        for k, v in line.items():
+            head[k] = v
+            if k == "config":
+                head["summary"] = compact_summary(line)
+        line = head
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -966,6 +1009,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--quick", action="store_true", help="FP32 dslash only")
     ap.add_argument("--no-solve", action="store_true", help="skip the 24^3x48 solver comparison")
+    ap.add_argument("--no-oracle-cg", action="store_true",
+                    help="skip the oracle's full FP64 CG timing (about 100 s of host time)")
     ap.add_argument("--profile", choices=["mrhs", "solve_f32", "solve_f16", "batch", "train", "nn",
                                           "staged"],
                     help="run a short fixed workload for an ncu capture and exit")

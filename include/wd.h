@@ -387,6 +387,8 @@ typedef struct {
     double iterate_seconds;  /* inner iterations (graph launches + checks) */
     double reliable_seconds; /* FP64 reliable updates inside the loop */
     double final_seconds;    /* odd-site reconstruction, true residual, unpack */
+    int fallback_iters;      /* wd_solve_fcg: iterations of the plain-CG fallback
+                                (0 when the preconditioned solve converged) */
 } wd_solve_info;
 
 /* Fill p with the defaults above (inner_prec WD_F32, recon 12 / 18). */
@@ -526,6 +528,29 @@ int wd_nn_train(float *weights, const double *gauge, double kappa, const int dim
 int wd_solve_fgcr(double *x, const double *b, const double *gauge, double kappa,
                   const int dims[4], const float *weights, int m,
                   const wd_solve_params *params, wd_solve_info *info);
+
+/*
+ * Flexible CG on the normal equations D^+ D x = D^+ b of the full lattice,
+ * preconditioned by N N^+ with N the network above (weights NULL: plain
+ * CGNR).  N N^+ is Hermitian positive definite, so the method converges where
+ * GCR on D stalls (kappa beyond the critical region of the links, where the
+ * spectrum of D surrounds the origin).  FP32 vectors and operator, BF16
+ * network arithmetic; the small variation of N's rounding between
+ * applications is absorbed by the flexible (Polak-Ribiere) beta.  FP64
+ * reliable updates every params->reliable_interval iterations and whenever
+ * the FP32 residual looks converged (x accumulated and r = b - D x recomputed
+ * in FP64; the search direction restarts).  Stops on ||b - D x|| / ||b|| <=
+ * params->tol in FP64.  Plain CG is the fallback: should the preconditioned
+ * iteration stop short (params->maxiter, a non-finite residual, a network
+ * wait that timed out) the even-odd mixed-precision CG of wd_solve_ex
+ * continues from its iterate (info->fallback_iters > 0).  The paper's solver
+ * is the unpreconditioned even-odd CG; this is an addition.  x, b, gauge:
+ * canonical FP64, host or device.  info->reliable_updates counts the FP64
+ * residual recomputations.
+ */
+int wd_solve_fcg(double *x, const double *b, const double *gauge, double kappa,
+                 const int dims[4], const float *weights, const wd_solve_params *params,
+                 wd_solve_info *info);
 
 #ifdef __cplusplus
 }

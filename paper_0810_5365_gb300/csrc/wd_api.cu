@@ -20,6 +20,8 @@ int nn_train_impl(float* w, const double* gauge, double kappa, const int dims[4]
 int fgcr_impl(double* x, const double* bsrc, const double* gauge, double kappa,
               const int dims[4], const float* wts, const wd_solve_params* prm,
               wd_solve_info* info, int m);
+int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, const int dims[4],
+             const float* wts, const wd_solve_params* prm, wd_solve_info* info);
 int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_params* prm,
                      wd_solve_info* infos);
 cudaError_t dslash_mrhs(void* out, const void* in, const void* gauge, int parity, int dagger,
@@ -437,6 +439,16 @@ int wd_solve_fgcr(double* x, const double* b, const double* gauge, double kappa,
   if (x == b) return WD_ERR_ALIAS;
   if (m < 1 || m > 16) return WD_ERR_ARG;
   return guarded([&] { return fgcr_impl(x, b, gauge, kappa, dims, weights, params, info, m); });
+}
+
+int wd_solve_fcg(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
+                 const float* weights, const wd_solve_params* params, wd_solve_info* info) {
+  WD_TRY(check_dims(dims));
+  if (!x || !b || !gauge) return WD_ERR_NULL;
+  if (!aligned(x) || !aligned(b) || !aligned(gauge) || (weights && !aligned(weights)))
+    return WD_ERR_ALIGN;
+  if (x == b) return WD_ERR_ALIAS;
+  return guarded([&] { return fcg_impl(x, b, gauge, kappa, dims, weights, params, info); });
 }
 
 int wd_norm2(double* result, const void* x, const int dims[4], int parity, int prec) {

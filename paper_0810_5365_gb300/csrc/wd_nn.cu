@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "wd_nn.cuh"
@@ -620,6 +621,96 @@ __global__ void accumulate_full_kernel(char* x64, char* xs, Geom g, size_t h64, 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// flexible CG on the normal equations D^+ D x = D^+ b with the preconditioner
+// N N^+ (N the network): packed FP32 full fields, scalars on the device.
+// rho[kp] = <s, z> of the current iteration, rho[1-kp] that of the next one;
+// qq[0..1] = ||D p||^2 on the even / odd half.
+// ---------------------------------------------------------------------------
+
+struct FcgScalars {
+  double rho[2];
+  double zeta;    // <s_old, z_new>: the Polak-Ribiere correction of beta
+  double qq[2];
+  double rr;      // ||r||^2, r = b - D x (sloppy)
+  double r64;     // ||b - D x64||^2 (FP64)
+  double bn;      // ||b||^2
+};
+
+// x += alpha p ; r -= alpha q ; rr = ||r||^2 ; alpha = rho[kp] / ||q||^2
+__global__ void __launch_bounds__(256) fcg_update_xr(char* x, char* r, const char* p,
+                                                     const char* q, FcgScalars* sc, int kp,
+                                                     Geom g, size_t half, RedScratch rs) {
+  const float a = (float)(sc->rho[kp] / (sc->qq[0] + sc->qq[1]));
+  double acc[1] = {0.0};
+  const long long n = 2LL * g.Vh;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
+    cx<float> xv[12], rv[12], pv[12], qv[12];
+    load_spinor_rw<WD_F32, float>(xv, x + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(rv, r + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(pv, p + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(qv, q + h * half, cb, g.Vh_pad);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      xv[k].r = fmaf(a, pv[k].r, xv[k].r);
+      xv[k].i = fmaf(a, pv[k].i, xv[k].i);
+      rv[k].r = fmaf(-a, qv[k].r, rv[k].r);
+      rv[k].i = fmaf(-a, qv[k].i, rv[k].i);
+    }
+    store_spinor<WD_F32, float>(x + h * half, cb, g.Vh_pad, xv);
+    store_spinor<WD_F32, float>(r + h * half, cb, g.Vh_pad, rv);
+    acc[0] += site_norm2(rv);
+  }
+  double tot[1];
+  if (grid_reduce<1, 256>(acc, rs, tot) && threadIdx.x == 0) sc->rr = tot[0];
+}
+
+// rho[slot] = Re <s, z> ; zeta = Re <s_old, z> (s_old may be null: zeta = 0)
+__global__ void __launch_bounds__(256) fcg_dots(const char* s, const char* s_old, const char* z,
+                                                FcgScalars* sc, int slot, Geom g, size_t half,
+                                                RedScratch rs) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  const long long n = 2LL * g.Vh;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
+    cx<float> sv[12], zv[12];
+    load_spinor_rw<WD_F32, float>(sv, s + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(zv, z + h * half, cb, g.Vh_pad);
+    site_cdot(sv, zv, acc[0], acc[1]);
+    if (s_old) {
+      load_spinor_rw<WD_F32, float>(sv, s_old + h * half, cb, g.Vh_pad);
+      double im = 0.0;
+      site_cdot(sv, zv, acc[2], im);
+    }
+  }
+  double tot[3];
+  if (grid_reduce<3, 256>(acc, rs, tot) && threadIdx.x == 0) {
+    sc->rho[slot] = tot[0];
+    sc->zeta = tot[2];
+  }
+}
+
+// p = z + beta p, beta = (rho[1-kp] - zeta) / rho[kp]  (restart: p = z)
+__global__ void __launch_bounds__(256) fcg_update_p(char* p, const char* z, const FcgScalars* sc,
+                                                    int kp, int restart, Geom g, size_t half) {
+  const float beta = restart ? 0.f : (float)((sc->rho[1 - kp] - sc->zeta) / sc->rho[kp]);
+  const long long n = 2LL * g.Vh;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
+    cx<float> pv[12], zv[12];
+    load_spinor_rw<WD_F32, float>(pv, p + h * half, cb, g.Vh_pad);
+    load_spinor_rw<WD_F32, float>(zv, z + h * half, cb, g.Vh_pad);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      pv[k].r = restart ? zv[k].r : fmaf(beta, pv[k].r, zv[k].r);
+      pv[k].i = restart ? zv[k].i : fmaf(beta, pv[k].i, zv[k].i);
+    }
+    store_spinor<WD_F32, float>(p + h * half, cb, g.Vh_pad, pv);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1032,6 +1123,230 @@ int fgcr_impl(double* x, const double* bsrc, const double* gauge, double kappa,
     info->reliable_updates = restarts;
     info->status = status;
     info->true_residual = rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
+               const wd_solve_params* prm, wd_solve_info* info);
+
+// Flexible CG on the normal equations D^+ D x = D^+ b, preconditioned by
+// N N^+ (N the network; w == nullptr: plain CGNR), with FP32 vectors and
+// operator, FP64 reliable updates (x accumulated and r = b - D x recomputed in
+// FP64 every `reliable_interval` iterations and whenever the FP32 residual
+// looks converged; the search direction restarts there).  N N^+ is Hermitian
+// and positive definite, so CG applies; its BF16 arithmetic perturbs it a
+// little from one application to the next, which the Polak-Ribiere form of
+// beta = <z_new, s_new - s_old> / <z_old, s_old> absorbs (flexible CG,
+// Notay, SIAM J. Sci. Comput. 22, 2000).  If this does not reach the
+// tolerance (maxiter, a non-finite residual, a network wait that timed out),
+// the plain mixed-precision even-odd CG continues from the best iterate.
+int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, const int dims[4],
+             const float* wts, const wd_solve_params* prm, wd_solve_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  wd_solve_params P;
+  wd_solve_params_default(&P);
+  if (prm) P = *prm;
+  if (P.reliable_interval < 1 || P.maxiter < 1) return WD_ERR_ARG;
+  const Geom g = make_geom(dims);
+  cudaStream_t st = state().stream;
+  int status = WD_ERR_NOCONV, iters = 0, restarts = 0;
+  double rel = 0.0;
+  {
+    Alloc al;
+    const size_t V = 2 * (size_t)g.Vh;
+    const size_t h32 = spinor_half_bytes(g, WD_F32), h64 = spinor_half_bytes(g, WD_F64);
+    void *g32, *g64;
+    NCK(al.get(&g32, gauge_bytes(g, WD_F32, 12)));
+    NCK(al.get(&g64, gauge_bytes(g, WD_F64, 18)));
+    const double* gd = gauge;
+    if (!on_device(gauge)) {
+      void* v;
+      NCK(al.get(&v, 4 * V * 18 * sizeof(double)));
+      NCK(cudaMemcpyAsync(v, gauge, 4 * V * 18 * sizeof(double), cudaMemcpyHostToDevice, st));
+      gd = (const double*)v;
+    }
+    NCK(pack_gauge(g32, gd, g, WD_F32, 12, st));
+    NCK(pack_gauge(g64, gd, g, WD_F64, 18, st));
+    const double* bd = bsrc;
+    double* canon = nullptr;
+    {
+      void* v;
+      NCK(al.get(&v, V * 24 * sizeof(double)));
+      canon = (double*)v;
+    }
+    if (!on_device(bsrc)) {
+      NCK(cudaMemcpyAsync(canon, bsrc, V * 24 * sizeof(double), cudaMemcpyHostToDevice, st));
+      bd = canon;
+    }
+    void *b64, *x64, *r64, *r, *xs, *p, *q, *sA, *sB, *w, *z, *scal, *wa = nullptr;
+    NCK(al.get(&b64, 2 * h64));
+    NCK(al.get(&x64, 2 * h64));
+    NCK(al.get(&r64, 2 * h64));
+    NCK(al.get(&r, 2 * h32));
+    NCK(al.get(&xs, 2 * h32));
+    NCK(al.get(&p, 2 * h32));
+    NCK(al.get(&q, 2 * h32));
+    NCK(al.get(&sA, 2 * h32));
+    NCK(al.get(&sB, 2 * h32));
+    NCK(al.get(&w, 2 * h32));
+    NCK(al.get(&z, 2 * h32));
+    NCK(al.get(&scal, sizeof(FcgScalars)));
+    FcgScalars* S = (FcgScalars*)scal;
+    NnBuffers B;
+    B.bytes8 = 2 * nn_half_bytes(g.Vh_pad, 8);
+    if (wts) {
+      NCK(al.get(&B.h1, B.bytes8));
+      NCK(al.get(&B.h2, B.bytes8));
+      NCK(al.get(&wa, NN_PARAMS * sizeof(float)));
+      // N^+ = L1^+ L2^+ L3^+: the adjoint layers in reverse order have the
+      // shapes of the forward layers (4 -> 8, 8 -> 8, 8 -> 4)
+      float* WA = (float*)wa;
+      nn_adjoint_weights<<<8, 256, 0, st>>>(wts + nn_layer_offset(2), WA + nn_layer_offset(0), 8, 4);
+      nn_adjoint_weights<<<8, 256, 0, st>>>(wts + nn_layer_offset(1), WA + nn_layer_offset(1), 8, 8);
+      nn_adjoint_weights<<<8, 256, 0, st>>>(wts + nn_layer_offset(0), WA + nn_layer_offset(2), 4, 8);
+      NCK(cudaGetLastError());
+    }
+    int* flag = nullptr;
+    NCK(device_flag(&flag, st));
+    NCK(ensure_scratch((size_t)num_sms() * 8 * 4 + 2 * (size_t)((g.Vh + 127) / 128) + 1024));
+    NCK(cudaMemsetAsync(scal, 0, sizeof(FcgScalars), st));
+    NCK(pack_spinor(b64, bd, g, WD_FULL, WD_F64, st));
+    NCK(norm2(&S->bn, b64, g, WD_F64, 2, st));
+    NCK(cudaMemsetAsync(x64, 0, 2 * h64, st));
+    NCK(cudaMemsetAsync(xs, 0, 2 * h32, st));
+    const int grid = blas_grid(V, 256);
+    RedScratch rs = scratch();
+    FcgScalars hs;
+    auto rd = [&]() -> cudaError_t {
+      cudaError_t e = cudaMemcpyAsync(&hs, S, sizeof(hs), cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return e;
+      return cudaStreamSynchronize(st);
+    };
+    // z = N N^+ s (or z = s without a network)
+    auto precond = [&](void* zo, const void* si) -> cudaError_t {
+      if (!wts) return cudaMemcpyAsync(zo, si, 2 * h32, cudaMemcpyDeviceToDevice, st);
+      cudaError_t e = nn_forward(g, g32, (const float*)wa, si, w, B, flag, st);
+      if (e != cudaSuccess) return e;
+      return nn_forward(g, g32, wts, w, zo, B, flag, st);
+    };
+    // q = D p with ||q||^2 per half
+    auto apply_D = [&](void* out, const void* in) -> cudaError_t {
+      for (int par = 0; par < 2; par++) {
+        DslashArgs d;
+        d.out = (char*)out + par * h32;
+        d.in = (const char*)in + (1 - par) * h32;
+        d.gauge = g32;
+        d.a = -kappa;
+        d.x = (const char*)in + par * h32;
+        d.bx = 1.0;
+        d.y = nullptr;
+        d.cy = 0.0;
+        d.norm_out = &S->qq[par];
+        d.rs = rs;
+        d.g = g;
+        d.parity = par;
+        cudaError_t e = launch_dslash(WD_F32, d, 12, false, st);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    };
+    void* s_cur = sA;
+    void* s_old = sB;
+    int kp = 0;
+    // r64 = b - D x64 (FP64), r = r64, s = D^+ r, z = N N^+ s, p = z
+    auto restart = [&]() -> cudaError_t {
+      cudaError_t e = full_op(WD_F64, 18, g64, r64, x64, kappa, g, st, b64);
+      if (e == cudaSuccess) e = norm2(&S->r64, r64, g, WD_F64, 2, st);
+      if (e == cudaSuccess) e = convert_spinor(r, WD_F32, r64, WD_F64, g, 2, st);
+      if (e == cudaSuccess) e = full_op(WD_F32, 12, g32, s_cur, r, kappa, g, st, nullptr, true);
+      if (e == cudaSuccess) e = precond(z, s_cur);
+      if (e != cudaSuccess) return e;
+      fcg_dots<<<grid, 256, 0, st>>>((const char*)s_cur, nullptr, (const char*)z, S, kp, g, h32, rs);
+      fcg_update_p<<<grid, 256, 0, st>>>((char*)p, (const char*)z, S, kp, 1, g, h32);
+      return cudaGetLastError();
+    };
+    NCK(restart());
+    NCK(rd());
+    const double bnorm = std::sqrt(hs.bn);
+    const double target = P.tol * bnorm * 0.9;
+    rel = bnorm > 0 ? std::sqrt(hs.r64) / bnorm : 0.0;
+    bool done = !(bnorm > 0) || std::sqrt(hs.r64) <= target;
+    int since = 0;
+    while (!done && iters < P.maxiter) {
+      NCK(apply_D(q, p));
+      fcg_update_xr<<<grid, 256, 0, st>>>((char*)xs, (char*)r, (const char*)p, (const char*)q, S,
+                                         kp, g, h32, rs);
+      NCK(cudaGetLastError());
+      iters++;
+      since++;
+      NCK(rd());
+      const double rn = std::sqrt(hs.rr);
+      if (!std::isfinite(rn)) {
+        status = WD_ERR_NONFINITE;
+        break;
+      }
+      if (rn <= target || since >= P.reliable_interval) {
+        accumulate_full_kernel<<<grid, 256, 0, st>>>((char*)x64, (char*)xs, g, h64, h32);
+        NCK(cudaGetLastError());
+        NCK(restart());
+        NCK(rd());
+        restarts++;
+        since = 0;
+        const double r64v = std::sqrt(hs.r64);
+        rel = r64v / bnorm;
+        if (!std::isfinite(r64v)) {
+          status = WD_ERR_NONFINITE;
+          break;
+        }
+        if (r64v <= target) done = true;
+        continue;
+      }
+      std::swap(s_cur, s_old);
+      NCK(full_op(WD_F32, 12, g32, s_cur, r, kappa, g, st, nullptr, true));
+      NCK(precond(z, s_cur));
+      fcg_dots<<<grid, 256, 0, st>>>((const char*)s_cur, (const char*)s_old, (const char*)z, S,
+                                    1 - kp, g, h32, rs);
+      fcg_update_p<<<grid, 256, 0, st>>>((char*)p, (const char*)z, S, kp, 0, g, h32);
+      NCK(cudaGetLastError());
+      kp ^= 1;
+    }
+    if (done) status = WD_OK;
+    // the best iterate: x64 (xs was folded in at the last reliable update;
+    // fold whatever accumulated since)
+    accumulate_full_kernel<<<grid, 256, 0, st>>>((char*)x64, (char*)xs, g, h64, h32);
+    NCK(cudaGetLastError());
+    const bool xdev = on_device(x);
+    double* xd = xdev ? x : canon;
+    NCK(unpack_spinor(xd, x64, g, WD_FULL, WD_F64, st));
+    if (!xdev) NCK(cudaMemcpyAsync(x, xd, V * 24 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int hflag = 0;
+    NCK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NCK(cudaStreamSynchronize(st));
+    if (hflag) status = WD_ERR_TIMEOUT;
+    if (status == WD_OK && !(rel <= P.tol)) status = WD_ERR_NOCONV;
+  }
+  int fb_iters = 0;
+  if (status != WD_OK) {
+    // plain CG, the fallback: the even-odd mixed-precision solver from x
+    wd_solve_params Q = P;
+    Q.use_initial_guess = 1;
+    Q.solver = WD_SOLVER_CG;
+    Q.maxiter = 100000;
+    wd_solve_info fi;
+    std::memset(&fi, 0, sizeof(fi));
+    status = solve_impl(x, bsrc, gauge, kappa, dims, &Q, &fi);
+    fb_iters = fi.iters;
+    rel = fi.true_residual;
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = iters + fb_iters;
+    info->reliable_updates = restarts;
+    info->status = status;
+    info->true_residual = rel;
+    info->fallback_iters = fb_iters;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return status;

@@ -43,7 +43,7 @@ EXPORTS = [
     "wd_rotate_spinor", "wd_tc_gemm_bf16", "wd_nn_train_params_default", "wd_nn_init",
     "wd_nn_apply", "wd_nn_train", "wd_solve_fgcr", "wd_nn_layer", "wd_gaussian_spinor",
     "wd_nn_wgrad", "wd_set_autotune", "wd_mrhs_set_lanes", "wd_tune_report",
-    "wd_wait_selftest", "wd_set_wait_limit", "wd_async_status",
+    "wd_wait_selftest", "wd_set_wait_limit", "wd_async_status", "wd_solve_fcg",
 ]
 
 WD_NN_PARAMS = 2304
@@ -89,7 +89,7 @@ class wd_solve_info(C.Structure):
                 ("true_residual", C.c_double), ("seconds", C.c_double),
                 ("dslash_calls", C.c_double), ("setup_seconds", C.c_double),
                 ("iterate_seconds", C.c_double), ("reliable_seconds", C.c_double),
-                ("final_seconds", C.c_double)]
+                ("final_seconds", C.c_double), ("fallback_iters", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -142,6 +142,8 @@ def lib():
         "wd_solve_fgcr": (C.c_int, [dp, dp, dp, C.c_double, i4, dp, C.c_int,
                                     C.POINTER(wd_solve_params), C.POINTER(wd_solve_info)]),
         "wd_rotate_spinor": (C.c_int, [dp, dp, dp, i4, C.c_int]),
+        "wd_solve_fcg": (C.c_int, [dp, dp, dp, C.c_double, i4, dp,
+                                   C.POINTER(wd_solve_params), C.POINTER(wd_solve_info)]),
         "wd_dslash_mrhs": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
                                      C.c_int, dp, i4, C.c_int, C.c_int]),
         "wd_set_autotune": (C.c_int, [C.c_int]),
@@ -399,6 +401,20 @@ def wd_solve_fgcr(x, b, gauge, kappa, dims, weights=None, m=10, params=None, che
     out["status"] = rc
     if check:
         _ck(rc, "wd_solve_fgcr")
+    return out
+
+
+def wd_solve_fcg(x, b, gauge, kappa, dims, weights=None, params=None, check=True):
+    """Flexible CG on D^+ D x = D^+ b preconditioned by N N^+ (weights None:
+    plain CGNR); plain even-odd CG is the fallback.  Returns the info dict."""
+    info = wd_solve_info()
+    p = params if params is not None else wd_solve_params_default()
+    rc = lib().wd_solve_fcg(_p(x), _p(b), _p(gauge), float(kappa), _d(dims), _p(weights),
+                            C.byref(p), C.byref(info))
+    out = info.as_dict()
+    out["status"] = rc
+    if check:
+        _ck(rc, "wd_solve_fcg")
     return out
 
 
