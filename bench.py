@@ -252,7 +252,8 @@ def compact_summary(line):
         sm["batch_s_vs_sequential_vs_f64"] = {
             f"{k}_{inner}": [round(v["batched"][inner]["wall_s"], 4),
                              round(v["batched"][inner]["speedup_vs_sequential_same_inner"], 2),
-                             round(v["batched"][inner]["speedup_vs_plain_f64"], 2)]
+                             round(v["batched"][inner]["speedup_vs_plain_f64"], 2),
+                             round(v["batched"][inner]["persistent_launch_wall_s"], 4)]
             for k, v in bt.items() if isinstance(v, dict) and "batched" in v
             for inner in v["batched"]}
         if "mrhs_dslash" in bt:
@@ -503,18 +504,31 @@ def batch_section(W, torch):
         for label, inner in (("f32", W.WD_F32), ("f16", W.WD_F16)):
             p = W.wd_solve_params_default()
             p.inner_prec = inner
-            W.wd_solve_batch(probs, p, check=False)  # warm-up
-            for pr in probs:
-                pr["x"].zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rc, infos = W.wd_solve_batch(probs, p, check=False)
-            torch.cuda.synchronize()
-            batched[label] = {"status": rc, "wall_s": time.perf_counter() - t0,
-                              "iters": [d["iters"] for d in infos],
-                              "max_true_residual": max(d["true_residual"] for d in infos)}
-            for pr in probs:
-                pr["x"].zero_()
+            per_mode = {}
+            # mode 0: one launch per step, a graph of check_interval iterations
+            # (the default); mode 1: one persistent launch per iteration
+            for mode in (0, 1):
+                prev = W.wd_set_batch_mode(mode)
+                try:
+                    W.wd_solve_batch(probs, p, check=False)  # warm-up
+                    for pr in probs:
+                        pr["x"].zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    rc, infos = W.wd_solve_batch(probs, p, check=False)
+                    torch.cuda.synchronize()
+                    per_mode[mode] = {"status": rc, "wall_s": time.perf_counter() - t0,
+                                      "iters": [d["iters"] for d in infos],
+                                      "max_true_residual": max(d["true_residual"]
+                                                               for d in infos)}
+                finally:
+                    W.wd_set_batch_mode(prev)
+                for pr in probs:
+                    pr["x"].zero_()
+            batched[label] = per_mode[0]
+            batched[label]["persistent_launch_wall_s"] = per_mode[1]["wall_s"]
+            batched[label]["persistent_launch_status"] = per_mode[1]["status"]
+            batched[label]["persistent_launch_iters"] = per_mode[1]["iters"]
         seq = {}
         for label, inner in (("single_rhs_f32", W.WD_F32), ("single_rhs_f16", W.WD_F16),
                              ("plain_f64", W.WD_F64)):
@@ -685,7 +699,9 @@ def profile_case(name):
                   24^3x48);
     ``solve_f32`` / ``solve_f16``  2 mixed-precision CG solves to 1e-10 on
                   24^3x48 (kappa 0.137);
-    ``batch``     one batched FP32-inner solve of 12 point sources on 24^3x48;
+    ``batch``     one batched FP32-inner solve of 12 point sources on 24^3x48
+                  (one launch per step);
+    ``batch_persistent``  the same with one persistent launch per iteration;
     ``train``     4 Adam steps of 16 samples on 16^3x32 (forward, adjoint and
                   tensor-core weight-gradient kernels);
     ``nn``        2 applications of the series-initialised network (three
@@ -746,6 +762,18 @@ def profile_case(name):
                   "x": torch.zeros_like(b)}]
         p = W.wd_solve_params_default()
         p.inner_prec = W.WD_F32
+        W.wd_solve_batch(probs, p)
+    elif name == "batch_persistent":
+        # the same solve with one persistent launch per iteration
+        dims = (24, 24, 24, 48)
+        Ud = torch.from_numpy(fields.su3_links(dims).view(np.float64).reshape(-1)).cuda()
+        bs = [fields.point_source(dims, 0, r // 3, r % 3) for r in range(12)]
+        b = torch.from_numpy(np.ascontiguousarray(np.stack(bs)).view(np.float64)).cuda()
+        probs = [{"dims": dims, "kappa": BATCH_KAPPA, "nrhs": 12, "gauge": Ud, "b": b,
+                  "x": torch.zeros_like(b)}]
+        p = W.wd_solve_params_default()
+        p.inner_prec = W.WD_F32
+        W.wd_set_batch_mode(1)
         W.wd_solve_batch(probs, p)
     elif name == "train":
         dims = (16, 16, 16, 32)
@@ -1011,7 +1039,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the 24^3x48 solver comparison")
     ap.add_argument("--no-oracle-cg", action="store_true",
                     help="skip the oracle's full FP64 CG timing (about 100 s of host time)")
-    ap.add_argument("--profile", choices=["mrhs", "solve_f32", "solve_f16", "batch", "train", "nn",
+    ap.add_argument("--profile", choices=["mrhs", "solve_f32", "solve_f16", "batch",
+                                          "batch_persistent", "train", "nn",
                                           "staged"],
                     help="run a short fixed workload for an ncu capture and exit")
     args = ap.parse_args()

@@ -338,7 +338,9 @@ int wd_wait_selftest(long long spins);
  * Bounded waits of the asynchronous kernels (no counterpart in the paper).
  * The staged hopping kernel (WD_STAGE_NEIGHBOURS) waits for its bulk copies
  * at most `polls` times (about 100 ns each; default 2^22) before it gives
- * up, poisons its sites with NaN and raises the device's fault flag.
+ * up, poisons its sites with NaN and raises the device's fault flag; each
+ * grid-barrier wait of the persistent batched iteration (wd_set_batch_mode)
+ * polls at most `polls` times before the solve gives up with WD_ERR_TIMEOUT.
  * 0 <= polls <= 2^26 (else WD_ERR_ARG); polls = 0 gives up at once, which
  * exercises the failure path without any fault.  Applies to the following
  * launches from this process.
@@ -426,6 +428,25 @@ int wd_solve_ex(double *x, const double *b, const double *gauge, double kappa,
  * Returns WD_OK if every right-hand side converged, else the first failing
  * status (the per-right-hand-side statuses are in info).
  */
+/*
+ * Execution of the batched iterations (no counterpart in the paper).
+ * mode = 0 (the default): one launch per step of the iteration (the four
+ * hopping steps, the vector updates and the per-right-hand-side sums), with
+ * the tile shapes of the autotuner.  mode = 1: every CG iteration of
+ * wd_solve_batch is ONE persistent cooperative launch over all problems and
+ * right-hand sides (one CTA per SM; the steps are phases separated by grid
+ * barriers), for FP32 and FP16 inner iterations with 12-real links; other
+ * inner formats run mode 0.  Every grid-barrier wait is bounded
+ * (wd_set_wait_limit): a wait that runs out ends the solve with
+ * WD_ERR_TIMEOUT and the context usable.  Both modes capture check_interval
+ * iterations as a CUDA graph and give the same iterates up to the summation
+ * order of the norms; on GB300 mode 0 is the faster (the hardware scheduler
+ * balances the many small CTAs of each step; each phase of the persistent
+ * launch waits at a grid barrier for its slowest warp).  Returns the previous
+ * mode, or -WD_ERR_ARG for a mode other than 0 or 1.
+ */
+int wd_set_batch_mode(int mode);
+
 typedef struct {
     int dims[4];
     double kappa;

@@ -32,6 +32,7 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
 void solver_finalize();
 cudaError_t wait_selftest(long spins, int* err, cudaStream_t st);
 int set_autotune(int enable);
+int set_batch_mode(int mode);
 int mrhs_set_lanes(int lanes);
 int tune_report(char* buf, size_t len);
 }  // namespace wd
@@ -286,6 +287,11 @@ int wd_dslash_mrhs(void* out, const void* in, const void* gauge, int parity, int
 }
 
 int wd_set_autotune(int enable) { return set_autotune(enable); }
+
+int wd_set_batch_mode(int mode) {
+  if (mode != 0 && mode != 1) return -WD_ERR_ARG;
+  return set_batch_mode(mode);
+}
 
 int wd_mrhs_set_lanes(int lanes) { return mrhs_set_lanes(lanes); }
 

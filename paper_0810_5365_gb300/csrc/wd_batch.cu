@@ -420,6 +420,315 @@ __global__ void __launch_bounds__(MRHS_BS) batch_convert(const __grid_constant__
 #undef WD_TILE_LOOP
 
 // ---------------------------------------------------------------------------
+// One persistent launch per batched CG iteration.
+//
+// The steps of an iteration (the four multi-right-hand-side hopping steps,
+// the two vector updates and the per-right-hand-side reductions) run as
+// phases of one cooperative kernel whose CTAs are all resident, separated by
+// grid barriers.  Work items are (32-site sub-tile, right-hand side), one
+// warp each, in the order of the multi-RHS kernel (the right-hand sides of a
+// sub-tile are adjacent, so a link comes from memory once for all of them).
+// Reductions are deterministic: each warp sums its items' values per
+// right-hand side in item order, each CTA sums its warps in order, and the
+// CTA partials ([rhs][CTA]) are summed in CTA order by one warp per
+// right-hand side.  Every barrier wait is bounded: a CTA whose wait runs out
+// raises the error word and leaves; the others see it at their next wait and
+// leave too, and the host reports WD_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+
+// Warps per CTA, one CTA per SM, so that few CTAs meet at each grid barrier
+// and each CTA can sum the per-CTA partials of a norm by itself: 24 for FP16
+// (80 registers) and 20 for FP32, whose hopping code inside the kernel's
+// item loop needs 96 registers to stay (nearly) free of spills.
+template <int P>
+struct PiWarps {
+  static constexpr int value = P == WD_F32 ? 20 : 24;
+};
+
+struct IterPlan {
+  MrhsBatch oe_p, eo_q, oe_r_dag, eo_s_dag;  // ts = H p ; q = p - k^2 H ts ; and the H^+ pair
+  BlasBatch upd_r, upd_xp;                   // r -= alpha q ; x += alpha p, p = s + beta p
+  int nr;                                    // right-hand sides in the batch
+  int maxr;                                  // largest nrhs of a problem
+};
+
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  int err;    // set by a CTA whose bounded wait ran out
+  int pad;
+};
+
+// The plan of the running batched solve.  Constant memory, like the batch
+// descriptors of the per-step kernels (kernel parameters): read-only to the
+// kernel, so its fields are reloaded at will instead of held in registers.
+// One plan per process: batched solves do not overlap (the library is used
+// from one host thread, and wd_solve_batch returns after its solve).
+__constant__ IterPlan c_pi_plan;
+
+struct IterArgs {
+  const int* active;
+  const double* gk;   // gamma of this iteration (per rhs)
+  double* gk1;        // gamma of the next iteration (written by CTA 0)
+  double* qq;         // ||q||^2 (written by CTA 0)
+  double* rr;         // ||r||^2 (written by CTA 0)
+  double* partA;      // CTA partials [rhs][CTA]: ||q||^2, then ||s||^2
+  double* partB;      // CTA partials of ||r||^2
+  GridBarrier* bar;
+  long spin_limit;
+};
+
+// all CTAs arrive before any leaves; false (and the CTA should return) if
+// this CTA's bounded wait ran out or another CTA's did
+__device__ __forceinline__ bool grid_barrier(GridBarrier* b, long limit) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = &b->gen;
+    volatile int* verr = &b->err;
+    const unsigned g0 = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&b->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      long spins = 0;
+      while (*vgen == g0) {
+        if (*verr) {
+          ok = 0;
+          break;
+        }
+        if (spins++ >= limit) {
+          atomicExch(&b->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    if (*verr) ok = 0;
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <typename B>
+__device__ __forceinline__ int batch_problem(const B& bt, int tile) {
+  int j = 0;
+  while (j + 1 < bt.nprob && tile >= bt.p[j + 1].tile0) j++;
+  return j;
+}
+
+// The work items of a phase are (32-site sub-tile, right-hand side slot
+// r < maxr), the slots of a sub-tile consecutive; item i goes to global warp
+// i mod (CTAs x warps), so a CTA's warps share the links of a sub-tile.
+struct PiItem {
+  int j;     // problem
+  int r;     // right-hand side within the problem
+  int cb;    // checkerboard site of this lane
+  bool act;  // an active right-hand side of this problem at a real site
+};
+
+template <typename B>
+__device__ __forceinline__ PiItem pi_item(const B& bt, int it, int maxr, const int* active) {
+  constexpr int SUBS = MRHS_BS / MRHS_SUB;
+  PiItem w;
+  const int sub = it / maxr;
+  w.r = it - sub * maxr;
+  const int tile = sub / SUBS, q = sub - tile * SUBS;
+  w.j = batch_problem(bt, tile);
+  const auto& pr = bt.p[w.j];
+  w.cb = (tile - pr.tile0) * MRHS_BS + q * MRHS_SUB + (int)threadIdx.x;
+  w.act = w.r < pr.nrhs && active[pr.rhs0 + w.r] != 0;
+  return w;
+}
+
+// the warps' per-right-hand-side accumulators (shared memory, [warp][rhs])
+// -> the CTA's partials [rhs][CTA], warps summed in order; accumulators reset
+template <int NW>
+__device__ __forceinline__ void flush_partials(double* acc, int nr, double* part) {
+  __syncthreads();
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  for (int g = t; g < nr; g += NW * 32) {
+    double v = 0.0;
+    for (int w = 0; w < NW; w++) {
+      v += acc[w * nr + g];
+      acc[w * nr + g] = 0.0;
+    }
+    part[(size_t)g * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// red[g] = sum over CTAs of part[g][CTA] in CTA order, computed by every CTA
+// for itself (one warp per right-hand side), so all CTAs hold the same value
+// without another grid barrier; CTA 0 also stores it in out[g].
+template <int NW>
+__device__ __forceinline__ void reduce_partials(const double* part, int nr, const int* active,
+                                                double* red, double* out) {
+  const int lane = threadIdx.x;
+  for (int g = threadIdx.y; g < nr; g += NW) {
+    if (active[g] == 0) continue;
+    double v = 0.0;
+    for (int c = lane; c < (int)gridDim.x; c += 32) v += __ldcg(part + (size_t)g * gridDim.x + c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      red[g] = v;
+      if (blockIdx.x == 0) out[g] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// one hopping phase over all items; NORM: ||out||^2 per rhs into acc
+// COH: the input field was written earlier in this launch (coherent loads;
+// the first step's input p is rewritten only after three grid barriers, so
+// the read-only path serves it)
+template <int P, int RC, bool DAG, bool NORM, int NW, bool COH>
+__device__ __forceinline__ void pi_dslash_phase(const MrhsBatch& bt, int maxr, const int* active,
+                                                double* acc, int nr) {
+  constexpr int SUBS = MRHS_BS / MRHS_SUB;
+  const int items = bt.ntiles * SUBS * maxr;
+  const int stride = gridDim.x * NW;
+  for (int it = blockIdx.x * NW + threadIdx.y; it < items; it += stride) {
+    const PiItem w = pi_item(bt, it, maxr, active);
+    const MrhsProblem& pr = bt.p[w.j];
+    double nrm = 0.0;
+    if (w.act && w.cb < pr.g.Vh) nrm = mrhs_site<P, RC, DAG, NORM, COH>(pr, w.cb, w.r);
+    if constexpr (NORM) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+      if (threadIdx.x == 0 && w.act) acc[threadIdx.y * nr + pr.rhs0 + w.r] += nrm;
+    }
+  }
+}
+
+// r -= alpha q with ||r||^2 per rhs into acc (f0 = r, f1 = q); qq: the
+// CTA's copy of the reduced ||q||^2
+template <int P, int NW>
+__device__ __forceinline__ void pi_update_r(const BlasBatch& bt, int maxr, const int* active,
+                                            const double* gk, const double* qq, double* acc,
+                                            int nr) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  constexpr int SUBS = MRHS_BS / MRHS_SUB;
+  const int items = bt.ntiles * SUBS * maxr;
+  const int stride = gridDim.x * NW;
+  for (int it = blockIdx.x * NW + threadIdx.y; it < items; it += stride) {
+    const PiItem w = pi_item(bt, it, maxr, active);
+    const BlasProblem& pr = bt.p[w.j];
+    const int gi = pr.rhs0 + w.r;
+    double t = 0.0;
+    if (w.act && w.cb < pr.g.Vh) {
+      const int VP = pr.g.Vh_pad, cb = w.cb;
+      const R alpha = (R)(gk[gi] / qq[gi]);
+      char* fr = pr.f[0] + w.r * pr.s[0];
+      const char* fq = pr.f[1] + w.r * pr.s[1];
+      cx<R> a[12], b[12];
+      load_spinor_rw<P, R>(a, fr, cb, VP);
+      load_spinor_rw<P, R>(b, fq, cb, VP);
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        a[k].r = fma(-alpha, b[k].r, a[k].r);
+        a[k].i = fma(-alpha, b[k].i, a[k].i);
+      }
+      store_spinor<P, R>(fr, cb, VP, a);
+      t = site_norm2(a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0 && w.act) acc[threadIdx.y * nr + gi] += t;
+  }
+}
+
+// x += alpha p ; p = s + beta p  (f0 = x [PX], f1 = p, f2 = s); qq, gk1:
+// the CTA's copies of the reduced scalars
+template <int P, int PX, int NW>
+__device__ __forceinline__ void pi_update_xp(const BlasBatch& bt, int maxr, const int* active,
+                                             const double* gk, const double* gk1,
+                                             const double* qq) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  using RX = typename std::conditional<PX == WD_F64, double, float>::type;
+  constexpr int SUBS = MRHS_BS / MRHS_SUB;
+  const int items = bt.ntiles * SUBS * maxr;
+  const int stride = gridDim.x * NW;
+  for (int it = blockIdx.x * NW + threadIdx.y; it < items; it += stride) {
+    const PiItem w = pi_item(bt, it, maxr, active);
+    const BlasProblem& pr = bt.p[w.j];
+    if (!(w.act && w.cb < pr.g.Vh)) continue;
+    const int gi = pr.rhs0 + w.r, VP = pr.g.Vh_pad, cb = w.cb;
+    const RX alpha = (RX)(gk[gi] / qq[gi]);
+    const R beta = (R)(gk1[gi] / gk[gi]);
+    char* fx = pr.f[0] + w.r * pr.s[0];
+    char* fp = pr.f[1] + w.r * pr.s[1];
+    const char* fs = pr.f[2] + w.r * pr.s[2];
+    cx<R> pv[12], sv[12];
+    cx<RX> xv[12];
+    load_spinor_rw<P, R>(pv, fp, cb, VP);
+    load_spinor_rw<P, R>(sv, fs, cb, VP);
+    load_spinor_rw<PX, RX>(xv, fx, cb, VP);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      xv[k].r = fma(alpha, (RX)pv[k].r, xv[k].r);
+      xv[k].i = fma(alpha, (RX)pv[k].i, xv[k].i);
+      pv[k].r = fma(beta, pv[k].r, sv[k].r);
+      pv[k].i = fma(beta, pv[k].i, sv[k].i);
+    }
+    store_spinor<PX, RX>(fx, cb, VP, xv);
+    store_spinor<P, R>(fp, cb, VP, pv);
+  }
+}
+
+// Dynamic shared memory of the persistent kernel: the warps' accumulators
+// [NW][nr] and the CTA's reduced scalars qq, gamma_next, rr [3][nr].
+__host__ __device__ constexpr size_t pi_smem_doubles(int nw, int nr) {
+  return (size_t)(nw + 3) * nr;
+}
+
+// One CGLS iteration of every active right-hand side of the batch (the
+// algorithm of batch_iteration_t, one launch, five grid barriers).
+template <int P, int PX, int RC>
+__global__ void __launch_bounds__(PiWarps<P>::value * 32, 1)
+    batch_iteration_kernel(const IterArgs A) {
+  constexpr int NW = PiWarps<P>::value;
+  extern __shared__ double pi_smem[];
+  const IterPlan& pl = c_pi_plan;
+  const int nr = pl.nr, maxr = pl.maxr;
+  double* acc = pi_smem;
+  double* s_qq = pi_smem + (size_t)NW * nr;
+  double* s_g1 = s_qq + nr;
+  double* s_rr = s_g1 + nr;
+  for (int t = threadIdx.y * 32 + threadIdx.x; t < NW * nr; t += NW * 32)
+    acc[t] = 0.0;
+  __syncthreads();
+  // q = Mhat p with ||q||^2
+  pi_dslash_phase<P, RC, false, false, NW, false>(pl.oe_p, maxr, A.active, acc, nr);
+  if (!grid_barrier(A.bar, A.spin_limit)) return;
+  pi_dslash_phase<P, RC, false, true, NW, true>(pl.eo_q, maxr, A.active, acc, nr);
+  flush_partials<NW>(acc, nr, A.partA);
+  if (!grid_barrier(A.bar, A.spin_limit)) return;
+  // r -= alpha q with ||r||^2
+  reduce_partials<NW>(A.partA, nr, A.active, s_qq, A.qq);
+  pi_update_r<P, NW>(pl.upd_r, maxr, A.active, A.gk, s_qq, acc, nr);
+  flush_partials<NW>(acc, nr, A.partB);
+  if (!grid_barrier(A.bar, A.spin_limit)) return;
+  // s = Mhat^+ r with ||s||^2
+  pi_dslash_phase<P, RC, true, false, NW, true>(pl.oe_r_dag, maxr, A.active, acc, nr);
+  if (!grid_barrier(A.bar, A.spin_limit)) return;
+  pi_dslash_phase<P, RC, true, true, NW, true>(pl.eo_s_dag, maxr, A.active, acc, nr);
+  flush_partials<NW>(acc, nr, A.partA);
+  if (!grid_barrier(A.bar, A.spin_limit)) return;
+  // x += alpha p ; p = s + beta p
+  reduce_partials<NW>(A.partA, nr, A.active, s_g1, A.gk1);
+  reduce_partials<NW>(A.partB, nr, A.active, s_rr, A.rr);
+  pi_update_xp<P, PX, NW>(pl.upd_xp, maxr, A.active, A.gk, s_g1, s_qq);
+}
+
+// ---------------------------------------------------------------------------
 // the batched solver
 // ---------------------------------------------------------------------------
 
@@ -440,7 +749,9 @@ struct BatchProblemWs {
   char* q = nullptr;
   char* r = nullptr;
   char* s = nullptr;
-  char* ts = nullptr;    // nrhs sloppy odd
+  char* ts = nullptr;    // nrhs sloppy odd (H p)
+  char* ts2 = nullptr;   // nrhs sloppy odd (H^+ r): a buffer of its own, so that no field
+                         // is read at neighbours, rewritten and read again in one iteration
   char* xs = nullptr;    // nrhs sloppy-x even
   double* canon = nullptr;  // staging for host b / x (nrhs full canonical)
   double* canon_gauge = nullptr;
@@ -562,8 +873,8 @@ void build_plan(BatchCtx& c, Plan& pl) {
     // sloppy operator: ts = H_oe p ; q = p - k^2 H_eo ts ; and the dagger pair on r -> s
     pl.d_oe_p.p[j] = mproblem(w, WD_ODD, w.gs, 1.0, w.ts, hs, w.p, hs, nullptr, 0, 0, nullptr, 0, 0);
     pl.d_eo_q.p[j] = mproblem(w, WD_EVEN, w.gs, -k2, w.q, hs, w.ts, hs, w.p, hs, 1.0, nullptr, 0, 0);
-    pl.d_oe_r_dag.p[j] = mproblem(w, WD_ODD, w.gs, 1.0, w.ts, hs, w.r, hs, nullptr, 0, 0, nullptr, 0, 0);
-    pl.d_eo_s_dag.p[j] = mproblem(w, WD_EVEN, w.gs, -k2, w.s, hs, w.ts, hs, w.r, hs, 1.0, nullptr, 0, 0);
+    pl.d_oe_r_dag.p[j] = mproblem(w, WD_ODD, w.gs, 1.0, w.ts2, hs, w.r, hs, nullptr, 0, 0, nullptr, 0, 0);
+    pl.d_eo_s_dag.p[j] = mproblem(w, WD_EVEN, w.gs, -k2, w.s, hs, w.ts2, hs, w.r, hs, 1.0, nullptr, 0, 0);
     // FP64: t64 = H_oe x_e ; r64 = k^2 H_eo t64 - x_e + bhat
     pl.r_t64.p[j] = mproblem(w, WD_ODD, w.g64, 1.0, w.t64, h64, w.x64, f64, nullptr, 0, 0, nullptr, 0, 0);
     pl.r_r64.p[j] = mproblem(w, WD_EVEN, w.g64, k2, w.r64, h64, w.t64, h64, w.x64, f64, -1.0, w.bhat, h64, 1.0);
@@ -613,6 +924,119 @@ cudaError_t batch_iteration(BatchCtx& c, const Plan& pl, int kp, cudaStream_t st
     case WD_F16: return batch_iteration_t<WD_F16, WD_F32>(c, pl, kp, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// ---- the persistent iteration launch ----
+
+// 0 (default): a launch per step; 1: one persistent launch per iteration.
+// On GB300 the per-step launches are measured faster (12 right-hand sides
+// on 24^3x48: 1.53 against 1.83 ms per FP32 iteration, 1.23 against 1.46 ms
+// FP16): the hardware block scheduler balances the many small CTAs of each
+// step, while the phases of the persistent kernel each end at a grid
+// barrier that waits for its slowest warp.
+int g_batch_mode = 0;
+
+struct Persist {
+  bool on = false;
+  GridBarrier* bar = nullptr;
+  double* partA = nullptr;
+  double* partB = nullptr;
+  int grid = 0;
+  size_t smem = 0;
+};
+
+template <int P, int PX>
+cudaError_t pi_launch(const Persist& ps, const BatchCtx& c, int kp, cudaStream_t st) {
+  IterArgs A;
+  A.active = c.active;
+  A.gk = c.sc.gamma[kp];
+  A.gk1 = c.sc.gamma[1 - kp];
+  A.qq = c.sc.qq;
+  A.rr = c.sc.rr;
+  A.partA = ps.partA;
+  A.partB = ps.partB;
+  A.bar = ps.bar;
+  A.spin_limit = state().wait_limit;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ps.grid);
+  cfg.blockDim = dim3(32, PiWarps<P>::value);
+  cfg.dynamicSmemBytes = ps.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_iteration_kernel<P, PX, 12>, A);
+}
+
+cudaError_t persist_launch(const Persist& ps, const BatchCtx& c, int kp, cudaStream_t st) {
+  switch (c.sprec) {
+    case WD_F32: return pi_launch<WD_F32, WD_F32>(ps, c, kp, st);
+    case WD_F16: return pi_launch<WD_F16, WD_F32>(ps, c, kp, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// the grid of the cooperative launch: every CTA the SMs hold at once
+template <int P, int PX>
+cudaError_t pi_grid(size_t smem, int* grid) {
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, batch_iteration_kernel<P, PX, 12>, PiWarps<P>::value * 32, smem);
+  if (e != cudaSuccess) return e;
+  *grid = nb * num_sms();
+  return cudaSuccess;
+}
+
+// set up the persistent path when the inner precision and link format have
+// an instantiation; ps.on stays false otherwise (the per-step graph is used)
+cudaError_t persist_setup(Persist& ps, BatchCtx& c, const Plan& pl, cudaStream_t st) {
+  ps.on = false;
+  if (g_batch_mode != 1 || c.srecon != 12 || (c.sprec != WD_F32 && c.sprec != WD_F16))
+    return cudaSuccess;
+  int dev = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e != cudaSuccess || !coop) return e;
+  ps.smem = pi_smem_doubles(c.sprec == WD_F32 ? PiWarps<WD_F32>::value : PiWarps<WD_F16>::value,
+                            c.nr) * sizeof(double);
+  {
+    cudaError_t ea = c.sprec == WD_F32
+        ? cudaFuncSetAttribute(batch_iteration_kernel<WD_F32, WD_F32, 12>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps.smem)
+        : cudaFuncSetAttribute(batch_iteration_kernel<WD_F16, WD_F32, 12>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps.smem);
+    if (ea != cudaSuccess) return ea;
+  }
+  e = c.sprec == WD_F32 ? pi_grid<WD_F32, WD_F32>(ps.smem, &ps.grid)
+                        : pi_grid<WD_F16, WD_F32>(ps.smem, &ps.grid);
+  if (e != cudaSuccess || ps.grid < 1) return e;
+  IterPlan h;
+  std::memset(&h, 0, sizeof(h));
+  h.oe_p = pl.d_oe_p;
+  h.eo_q = pl.d_eo_q;
+  h.oe_r_dag = pl.d_oe_r_dag;
+  h.eo_s_dag = pl.d_eo_s_dag;
+  h.upd_r = pl.upd_r;
+  h.upd_xp = pl.upd_xp;
+  h.nr = c.nr;
+  h.maxr = 1;
+  for (auto& w : c.pw) h.maxr = w.nrhs > h.maxr ? w.nrhs : h.maxr;
+  void* v;
+  if ((e = dalloc(c, &v, sizeof(GridBarrier)))) return e;
+  ps.bar = (GridBarrier*)v;
+  if ((e = dalloc(c, &v, (size_t)c.nr * ps.grid * sizeof(double)))) return e;
+  ps.partA = (double*)v;
+  if ((e = dalloc(c, &v, (size_t)c.nr * ps.grid * sizeof(double)))) return e;
+  ps.partB = (double*)v;
+  if ((e = cudaMemcpyToSymbolAsync(c_pi_plan, &h, sizeof(h), 0, cudaMemcpyHostToDevice, st)))
+    return e;
+  if ((e = cudaMemsetAsync(ps.bar, 0, sizeof(GridBarrier), st))) return e;
+  // a plan on the host stack: wait for the copy before it goes out of scope
+  if ((e = cudaStreamSynchronize(st))) return e;
+  ps.on = true;
+  return cudaSuccess;
 }
 
 template <int PD, int PS>
@@ -749,6 +1173,7 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
     WD_BCK(dalloc(c, &v, n * hs)); w.r = (char*)v;
     WD_BCK(dalloc(c, &v, n * hs)); w.s = (char*)v;
     WD_BCK(dalloc(c, &v, n * hs)); w.ts = (char*)v;
+    WD_BCK(dalloc(c, &v, n * hs)); w.ts2 = (char*)v;
     WD_BCK(dalloc(c, &v, n * hx)); w.xs = (char*)v;
   }
   {
@@ -850,10 +1275,15 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
   const double t_setup = secs(t0);
 
   // ---- the iteration graph ----
+  Persist ps;
+  WD_BCK(persist_setup(ps, c, pl, st));
+  auto iteration = [&](int kp, cudaStream_t s) -> cudaError_t {
+    return ps.on ? persist_launch(ps, c, kp, s) : batch_iteration(c, pl, kp, s);
+  };
   cudaGraphExec_t exec = nullptr;
   if (P.use_graph && nact > 0) {
     // the inner launch shapes, tuned before they are frozen into the graph
-    {
+    if (!ps.on) {
       RedScratch rs = scratch();
       WD_BCK(tune_mrhs(c.sprec, pl.d_oe_p, c.srecon, false, c.active, rs, false, st));
       WD_BCK(tune_mrhs(c.sprec, pl.d_eo_q, c.srecon, false, c.active, rs, true, st));
@@ -864,7 +1294,7 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
     WD_BCK(cudaStreamBeginCapture(c.cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaSuccess;
     const double calls = c.dslash_calls;
-    for (int k = 0; k < chunk && ce == cudaSuccess; k++) ce = batch_iteration(c, pl, k & 1, c.cap);
+    for (int k = 0; k < chunk && ce == cudaSuccess; k++) ce = iteration(k & 1, c.cap);
     c.dslash_calls = calls;
     cudaError_t ee = cudaStreamEndCapture(c.cap, &graph);
     if (ce != cudaSuccess || ee != cudaSuccess) {
@@ -893,10 +1323,17 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
       c.dslash_calls += 4.0 * chunk;
     } else {
       e = cudaSuccess;
-      for (int k = 0; k < chunk && e == cudaSuccess; k++) e = batch_iteration(c, pl, k & 1, st);
+      for (int k = 0; k < chunk && e == cudaSuccess; k++) e = iteration(k & 1, st);
     }
     if (e == cudaSuccess) e = read_scal();
     if (e != cudaSuccess) { state().last_cuda_error = (int)e; err = WD_ERR_CUDA; break; }
+    if (ps.on) {
+      // a grid barrier whose bounded wait ran out ends the solve
+      GridBarrier hb;
+      e = cudaMemcpy(&hb, ps.bar, sizeof(hb), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) { state().last_cuda_error = (int)e; err = WD_ERR_CUDA; break; }
+      if (hb.err) { err = WD_ERR_TIMEOUT; break; }
+    }
     it += chunk;
     bool any_done = false;
     for (int g = 0; g < nr; g++) {
@@ -1002,6 +1439,12 @@ int solve_batch_impl(const wd_batch_problem* probs, int nprob, const wd_solve_pa
   }
   free_ctx(c);
   return worst;
+}
+
+int set_batch_mode(int mode) {
+  const int prev = g_batch_mode;
+  g_batch_mode = mode;
+  return prev;
 }
 
 // single problem, many right-hand sides: one hopping application

@@ -197,31 +197,43 @@ inline size_t spinor_half_bytes(const Geom& g, int prec) {
   return round_up((size_t)g.Vh_pad * per, 256);
 }
 
+// A load of an input field.  COH = false: the read-only data path (the field
+// is not written while the kernel runs).  COH = true: an ordinary coherent
+// load, for a kernel that reads fields written earlier in the same launch by
+// other CTAs (after a grid barrier).
+template <bool COH, typename T>
+__device__ __forceinline__ T ldin(const T* p) {
+  if constexpr (COH)
+    return __ldca(p);
+  else
+    return __ldg(p);
+}
+
 // Load the 12 complex components of site cb as type R.
-template <int P, typename R>
+template <int P, typename R, bool COH = false>
 __device__ __forceinline__ void load_spinor(cx<R> (&s)[12], const void* base, int cb, int Vh_pad) {
   if constexpr (P == WD_F64) {
     const double2* p = (const double2*)base;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      double2 v = __ldg(p + sbi(cb, k, 12));
+      double2 v = ldin<COH>(p + sbi(cb, k, 12));
       s[k] = mk<R>((R)v.x, (R)v.y);
     }
   } else if constexpr (P == WD_F32) {
     const float4* p = (const float4*)base;
 #pragma unroll
     for (int k = 0; k < 6; k++) {
-      float4 v = __ldg(p + sbi(cb, k, 6));
+      float4 v = ldin<COH>(p + sbi(cb, k, 6));
       s[2 * k] = mk<R>((R)v.x, (R)v.y);
       s[2 * k + 1] = mk<R>((R)v.z, (R)v.w);
     }
   } else {
     const int4* p = (const int4*)base;
     const float* sc = (const float*)((const char*)base + (size_t)Vh_pad * 48);
-    float scale = __ldg(sc + cb);
+    float scale = ldin<COH>(sc + cb);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      int4 v = __ldg(p + sbi(cb, k, 3));
+      int4 v = ldin<COH>(p + sbi(cb, k, 3));
       const __half2* h = reinterpret_cast<const __half2*>(&v);
 #pragma unroll
       for (int j = 0; j < 4; j++) {

@@ -168,7 +168,7 @@ __device__ __forceinline__ void su3_mul_f32x2(const cx<float> (&u)[9], const cx<
 
 // Load the neighbour spinor and project it: h receives the half spinor, the
 // return value the factor still to apply (the FP16 site scale, else 1).
-template <int P, int MU, int S, typename R>
+template <int P, int MU, int S, typename R, bool COH = false>
 __device__ __forceinline__ R load_project(cx<R> (&h)[6], const void* __restrict__ in, int nb,
                                           int Vh_pad) {
   if constexpr (P == WD_F16) {
@@ -177,12 +177,12 @@ __device__ __forceinline__ R load_project(cx<R> (&h)[6], const void* __restrict_
     __half2 v[12];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      int4 w = __ldg(p + sbi(nb, k, 3));
+      int4 w = ldin<COH>(p + sbi(nb, k, 3));
       const __half2* q = reinterpret_cast<const __half2*>(&w);
 #pragma unroll
       for (int j = 0; j < 4; j++) v[4 * k + j] = q[j];
     }
-    const float scale = __ldg(scp + nb);
+    const float scale = ldin<COH>(scp + nb);
     __half2 hh[6];
     project_h2<MU, S>(v, hh);
 #pragma unroll
@@ -193,7 +193,7 @@ __device__ __forceinline__ R load_project(cx<R> (&h)[6], const void* __restrict_
     return scale;
   } else {
     cx<R> psi[12];
-    load_spinor<P, R>(psi, in, nb, Vh_pad);
+    load_spinor<P, R, COH>(psi, in, nb, Vh_pad);
     project<MU, S>(psi, h);
     return (R)1;
   }
@@ -204,12 +204,12 @@ __device__ __forceinline__ R load_project(cx<R> (&h)[6], const void* __restrict_
 // boundary (applied as a sign at accumulation).
 // unit: the link is the identity (temporal gauge, time hop off the boundary
 // slice): neither loaded nor multiplied.
-template <int P, int RC, int MU, int S, bool FWD, typename R>
+template <int P, int RC, int MU, int S, bool FWD, typename R, bool COH = false>
 __device__ __forceinline__ void hop(cx<R> (&acc)[12], const void* __restrict__ in,
                                     const void* __restrict__ gauge, int nb, int region, int lcb,
                                     bool flip, int Vh_pad, bool unit = false) {
   cx<R> h[6];
-  R sc = load_project<P, MU, S, R>(h, in, nb, Vh_pad);
+  R sc = load_project<P, MU, S, R, COH>(h, in, nb, Vh_pad);
   cx<R> t[6];
   if (MU == 3 && unit) {
 #pragma unroll
@@ -264,14 +264,15 @@ struct RawF16 {
   int2 lb;     // link U11 U12
 };
 
+template <bool COH = false>
 __device__ __forceinline__ RawF16 fetch_f16(const void* __restrict__ in,
                                             const void* __restrict__ gauge, int nb, int region,
                                             int lcb, int VP, bool unit = false) {
   RawF16 r;
   const int4* p = (const int4*)in;
 #pragma unroll
-  for (int k = 0; k < 3; k++) r.s[k] = __ldg(p + sbi(nb, k, 3));
-  r.sc = __ldg((const float*)((const char*)in + (size_t)VP * 48) + nb);
+  for (int k = 0; k < 3; k++) r.s[k] = ldin<COH>(p + sbi(nb, k, 3));
+  r.sc = ldin<COH>((const float*)((const char*)in + (size_t)VP * 48) + nb);
   if (!unit) {
     r.la = __ldg((const int4*)gauge + (size_t)region * VP + lcb);
     r.lb = __ldg((const int2*)((const char*)gauge + (size_t)8 * VP * 16) + (size_t)region * VP + lcb);
@@ -374,13 +375,13 @@ __device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& 
 // The eight hops of one FP16 site: the loads of the next hops are issued
 // before the current one is computed (WD_F16_PREFETCH hops in flight).
 // funit/bunit: the forward/backward time link is the identity (temporal gauge).
-template <int SF, int SB_>
+template <int SF, int SB_, bool COH = false>
 __device__ __forceinline__ void hops_f16(cx<float> (&acc)[12], const void* __restrict__ in,
                                          const void* __restrict__ ga, int p, int cb, int f0,
                                          int b0, int f1, int b1, int f2, int b2, int f3, int b3,
                                          bool fflip, bool bflip, bool funit, bool bunit, int VP) {
   const int q = 1 - p;
-#define WD_F(nb, reg, lcb) fetch_f16(in, ga, nb, reg, lcb, VP)
+#define WD_F(nb, reg, lcb) fetch_f16<COH>(in, ga, nb, reg, lcb, VP)
 #if WD_F16_PREFETCH >= 2
   RawF16 r0 = WD_F(f0, 0 + p, cb), r1 = WD_F(b0, 0 + q, b0);
   RawF16 r2 = WD_F(f1, 2 + p, cb);
@@ -391,9 +392,9 @@ __device__ __forceinline__ void hops_f16(cx<float> (&acc)[12], const void* __res
   compute_f16<1, SF, true>(acc, r2, false);
   r1 = WD_F(b2, 4 + q, b2);
   compute_f16<1, SB_, false>(acc, r3, false);
-  r2 = fetch_f16(in, ga, f3, 6 + p, cb, VP, funit);
+  r2 = fetch_f16<COH>(in, ga, f3, 6 + p, cb, VP, funit);
   compute_f16<2, SF, true>(acc, r0, false);
-  r3 = fetch_f16(in, ga, b3, 6 + q, b3, VP, bunit);
+  r3 = fetch_f16<COH>(in, ga, b3, 6 + q, b3, VP, bunit);
   compute_f16<2, SB_, false>(acc, r1, false);
   compute_f16<3, SF, true>(acc, r2, fflip, funit);
   compute_f16<3, SB_, false>(acc, r3, bflip, bunit);
@@ -409,9 +410,9 @@ __device__ __forceinline__ void hops_f16(cx<float> (&acc)[12], const void* __res
   compute_f16<1, SB_, false>(acc, r1, false);
   r1 = WD_F(b2, 4 + q, b2);
   compute_f16<2, SF, true>(acc, r0, false);
-  r0 = fetch_f16(in, ga, f3, 6 + p, cb, VP, funit);
+  r0 = fetch_f16<COH>(in, ga, f3, 6 + p, cb, VP, funit);
   compute_f16<2, SB_, false>(acc, r1, false);
-  r1 = fetch_f16(in, ga, b3, 6 + q, b3, VP, bunit);
+  r1 = fetch_f16<COH>(in, ga, b3, 6 + q, b3, VP, bunit);
   compute_f16<3, SF, true>(acc, r0, fflip, funit);
   compute_f16<3, SB_, false>(acc, r1, bflip, bunit);
 #endif

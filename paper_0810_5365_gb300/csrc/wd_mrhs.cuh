@@ -73,14 +73,85 @@ struct MrhsMinBlocks {
   static constexpr int value = raw < 1 ? 1 : (raw > 32 ? 32 : raw);
 };
 
+// One right-hand side r of one site cb of problem pr: out = a H in + bx x +
+// cy y, returning ||out||^2 at this site when NORM (else 0).  COH: the input
+// field is read with coherent loads (it was written earlier in the launch).
+template <int P, int RC, bool DAG, bool NORM, bool COH = false>
+__device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r) {
+  using R = typename std::conditional<P == WD_F64, double, float>::type;
+  constexpr int SF = DAG ? -1 : 1;
+  constexpr int SB_ = -SF;
+  const Geom& g = pr.g;
+  const int p = pr.parity, qq = 1 - p, VP = g.Vh_pad;
+  int x0, x1, x2, x3;
+  cb_coords(cb, p, g, x0, x1, x2, x3);
+  const int row = cb - (x0 >> 1);
+  const int f0 = row + ((x0 + 1 == g.L[0] ? 0 : x0 + 1) >> 1);
+  const int b0 = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
+  const int f1 = x1 == g.L[1] - 1 ? cb - (g.L[1] - 1) * g.S1 : cb + g.S1;
+  const int b1 = x1 == 0 ? cb + (g.L[1] - 1) * g.S1 : cb - g.S1;
+  const int f2 = x2 == g.L[2] - 1 ? cb - (g.L[2] - 1) * g.S2 : cb + g.S2;
+  const int b2 = x2 == 0 ? cb + (g.L[2] - 1) * g.S2 : cb - g.S2;
+  const int f3 = x3 == g.L[3] - 1 ? cb - (g.L[3] - 1) * g.S3 : cb + g.S3;
+  const int b3 = x3 == 0 ? cb + (g.L[3] - 1) * g.S3 : cb - g.S3;
+  const bool fflip = x3 == g.L[3] - 1;
+  const bool bflip = x3 == 0;
+  const void* in = (const char*)pr.in + (size_t)r * pr.s_in;
+  const void* ga = pr.gauge;
+  cx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
+  if constexpr (P == WD_F16) {
+    hops_f16<SF, SB_, COH>(acc, in, ga, p, cb, f0, b0, f1, b1, f2, b2, f3, b3, fflip, bflip,
+                           false, false, VP);
+  } else {
+    hop<P, RC, 0, SF, true, R, COH>(acc, in, ga, f0, 0 + p, cb, false, VP);
+    hop<P, RC, 0, SB_, false, R, COH>(acc, in, ga, b0, 0 + qq, b0, false, VP);
+    hop<P, RC, 1, SF, true, R, COH>(acc, in, ga, f1, 2 + p, cb, false, VP);
+    hop<P, RC, 1, SB_, false, R, COH>(acc, in, ga, b1, 2 + qq, b1, false, VP);
+    hop<P, RC, 2, SF, true, R, COH>(acc, in, ga, f2, 4 + p, cb, false, VP);
+    hop<P, RC, 2, SB_, false, R, COH>(acc, in, ga, b2, 4 + qq, b2, false, VP);
+    hop<P, RC, 3, SF, true, R, COH>(acc, in, ga, f3, 6 + p, cb, fflip, VP);
+    hop<P, RC, 3, SB_, false, R, COH>(acc, in, ga, b3, 6 + qq, b3, bflip, VP);
+  }
+  const R ca = (R)pr.a;
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
+  if (pr.x) {
+    cx<R> v[12];
+    load_spinor_rw<P, R>(v, (const char*)pr.x + (size_t)r * pr.s_x, cb, VP);
+    const R cbx = (R)pr.bx;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      acc[k].r = fma(cbx, v[k].r, acc[k].r);
+      acc[k].i = fma(cbx, v[k].i, acc[k].i);
+    }
+  }
+  if (pr.y) {
+    cx<R> v[12];
+    load_spinor_rw<P, R>(v, (const char*)pr.y + (size_t)r * pr.s_y, cb, VP);
+    const R ccy = (R)pr.cy;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      acc[k].r = fma(ccy, v[k].r, acc[k].r);
+      acc[k].i = fma(ccy, v[k].i, acc[k].i);
+    }
+  }
+  void* out = (char*)pr.out + (size_t)r * pr.s_out;
+  store_spinor<P, R>(out, cb, VP, acc);
+  double nrm = 0.0;
+  if constexpr (NORM) {
+    if constexpr (P == WD_F16) load_spinor_rw<P, R>(acc, out, cb, VP);
+    nrm = site_norm2(acc);
+  }
+  return nrm;
+}
+
 template <int P, int RC, bool DAG, bool NORM, int LANES>
 __global__ void __launch_bounds__(MRHS_SUB* LANES, (MrhsMinBlocks<P, NORM, LANES>::value))
     mrhs_dslash_kernel(const __grid_constant__ MrhsBatch bt, int groups,
                        const int* __restrict__ active, RedScratch rs) {
-  using R = typename std::conditional<P == WD_F64, double, float>::type;
   const int tx = threadIdx.x, ry = threadIdx.y;
-  constexpr int SF = DAG ? -1 : 1;
-  constexpr int SB_ = -SF;
   constexpr int SUBS = MRHS_BS / MRHS_SUB;  // sub-tiles per tile
   const int nprob = bt.nprob;
   const int sub = blockIdx.x / groups;
@@ -92,70 +163,7 @@ __global__ void __launch_bounds__(MRHS_SUB* LANES, (MrhsMinBlocks<P, NORM, LANES
   const int cb = (tile - pr.tile0) * MRHS_BS + q * MRHS_SUB + tx;
   const bool act = r < pr.nrhs && (active == nullptr || active[pr.rhs0 + r] != 0);
   double nrm = 0.0;
-  if (act && cb < pr.g.Vh) {
-    const Geom& g = pr.g;
-    const int p = pr.parity, qq = 1 - p, VP = g.Vh_pad;
-    int x0, x1, x2, x3;
-    cb_coords(cb, p, g, x0, x1, x2, x3);
-    const int row = cb - (x0 >> 1);
-    const int f0 = row + ((x0 + 1 == g.L[0] ? 0 : x0 + 1) >> 1);
-    const int b0 = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
-    const int f1 = x1 == g.L[1] - 1 ? cb - (g.L[1] - 1) * g.S1 : cb + g.S1;
-    const int b1 = x1 == 0 ? cb + (g.L[1] - 1) * g.S1 : cb - g.S1;
-    const int f2 = x2 == g.L[2] - 1 ? cb - (g.L[2] - 1) * g.S2 : cb + g.S2;
-    const int b2 = x2 == 0 ? cb + (g.L[2] - 1) * g.S2 : cb - g.S2;
-    const int f3 = x3 == g.L[3] - 1 ? cb - (g.L[3] - 1) * g.S3 : cb + g.S3;
-    const int b3 = x3 == 0 ? cb + (g.L[3] - 1) * g.S3 : cb - g.S3;
-    const bool fflip = x3 == g.L[3] - 1;
-    const bool bflip = x3 == 0;
-    const void* in = (const char*)pr.in + (size_t)r * pr.s_in;
-    const void* ga = pr.gauge;
-    cx<R> acc[12];
-#pragma unroll
-    for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
-    if constexpr (P == WD_F16) {
-      hops_f16<SF, SB_>(acc, in, ga, p, cb, f0, b0, f1, b1, f2, b2, f3, b3, fflip, bflip,
-                        false, false, VP);
-    } else {
-      hop<P, RC, 0, SF, true>(acc, in, ga, f0, 0 + p, cb, false, VP);
-      hop<P, RC, 0, SB_, false>(acc, in, ga, b0, 0 + qq, b0, false, VP);
-      hop<P, RC, 1, SF, true>(acc, in, ga, f1, 2 + p, cb, false, VP);
-      hop<P, RC, 1, SB_, false>(acc, in, ga, b1, 2 + qq, b1, false, VP);
-      hop<P, RC, 2, SF, true>(acc, in, ga, f2, 4 + p, cb, false, VP);
-      hop<P, RC, 2, SB_, false>(acc, in, ga, b2, 4 + qq, b2, false, VP);
-      hop<P, RC, 3, SF, true>(acc, in, ga, f3, 6 + p, cb, fflip, VP);
-      hop<P, RC, 3, SB_, false>(acc, in, ga, b3, 6 + qq, b3, bflip, VP);
-    }
-    const R ca = (R)pr.a;
-#pragma unroll
-    for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
-    if (pr.x) {
-      cx<R> v[12];
-      load_spinor_rw<P, R>(v, (const char*)pr.x + (size_t)r * pr.s_x, cb, VP);
-      const R cbx = (R)pr.bx;
-#pragma unroll
-      for (int k = 0; k < 12; k++) {
-        acc[k].r = fma(cbx, v[k].r, acc[k].r);
-        acc[k].i = fma(cbx, v[k].i, acc[k].i);
-      }
-    }
-    if (pr.y) {
-      cx<R> v[12];
-      load_spinor_rw<P, R>(v, (const char*)pr.y + (size_t)r * pr.s_y, cb, VP);
-      const R ccy = (R)pr.cy;
-#pragma unroll
-      for (int k = 0; k < 12; k++) {
-        acc[k].r = fma(ccy, v[k].r, acc[k].r);
-        acc[k].i = fma(ccy, v[k].i, acc[k].i);
-      }
-    }
-    void* out = (char*)pr.out + (size_t)r * pr.s_out;
-    store_spinor<P, R>(out, cb, VP, acc);
-    if constexpr (NORM) {
-      if constexpr (P == WD_F16) load_spinor_rw<P, R>(acc, out, cb, VP);
-      nrm = site_norm2(acc);
-    }
-  }
+  if (act && cb < pr.g.Vh) nrm = mrhs_site<P, RC, DAG, NORM>(pr, cb, r);
   if constexpr (NORM) {
     // one warp = one right-hand side of these 32 sites; the per-(rhs,
     // sub-tile) partials are summed in a fixed order by sum_partials_kernel

@@ -44,6 +44,7 @@ EXPORTS = [
     "wd_nn_apply", "wd_nn_train", "wd_solve_fgcr", "wd_nn_layer", "wd_gaussian_spinor",
     "wd_nn_wgrad", "wd_set_autotune", "wd_mrhs_set_lanes", "wd_tune_report",
     "wd_wait_selftest", "wd_set_wait_limit", "wd_async_status", "wd_solve_fcg",
+    "wd_set_batch_mode",
 ]
 
 WD_NN_PARAMS = 2304
@@ -147,6 +148,7 @@ def lib():
         "wd_dslash_mrhs": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_double, vp, C.c_double,
                                      C.c_int, dp, i4, C.c_int, C.c_int]),
         "wd_set_autotune": (C.c_int, [C.c_int]),
+        "wd_set_batch_mode": (C.c_int, [C.c_int]),
         "wd_wait_selftest": (C.c_int, [C.c_longlong]),
         "wd_set_wait_limit": (C.c_int, [C.c_longlong]),
         "wd_async_status": (C.c_int, []),
@@ -298,6 +300,15 @@ def wd_async_status():
     if rc not in (WD_OK, WD_ERR_TIMEOUT):
         raise WdError(rc, "wd_async_status")
     return rc
+
+
+def wd_set_batch_mode(mode):
+    """0: one launch per step of a batched CG iteration (default); 1: one
+    persistent cooperative launch per iteration.  Returns the previous mode."""
+    prev = int(lib().wd_set_batch_mode(int(mode)))
+    if prev < 0:
+        raise WdError(-prev, "wd_set_batch_mode")
+    return prev
 
 
 def wd_set_autotune(enable):

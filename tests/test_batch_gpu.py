@@ -114,7 +114,9 @@ def test_batched_solve_pair_shape_is_bit_identical():
     thread gives the same solutions, bit for bit, and the same iteration
     counts as one right-hand side per thread.  The batch's right-hand sides
     converge at different iterations, so the convergence mask switches off
-    one member of a thread's pair while the other goes on."""
+    one member of a thread's pair while the other goes on.  (Tile shapes
+    belong to the per-step launches: batch mode 0.)"""
+    prev = W.wd_set_batch_mode(0)
     try:
         W.wd_mrhs_set_lanes(2)
         rc1, i1, k1 = _batch(W.WD_F32)
@@ -122,6 +124,7 @@ def test_batched_solve_pair_shape_is_bit_identical():
         rc2, i2, k2 = _batch(W.WD_F32)
     finally:
         W.wd_mrhs_set_lanes(0)
+        W.wd_set_batch_mode(prev)
     assert rc1 == rc2 == W.WD_OK
     assert len({d["iters"] for d in i1}) > 1
     assert [d["iters"] for d in i1] == [d["iters"] for d in i2]
@@ -224,12 +227,85 @@ def test_batched_matches_single_solves_iteration_counts():
         assert abs(one["iters"] - infos[r]["iters"]) <= 10
 
 
-def test_batched_graph_and_plain_agree():
-    rc1, i1, k1 = _batch(W.WD_F32, use_graph=1)
-    rc2, i2, k2 = _batch(W.WD_F32, use_graph=0)
+@pytest.mark.parametrize("mode", [1, 0])
+def test_batched_graph_and_plain_agree(mode):
+    """Captured graph and direct launches give the same iterates bit for bit,
+    in both batch modes (one persistent launch per iteration, one launch per
+    step)."""
+    prev = W.wd_set_batch_mode(mode)
+    try:
+        rc1, i1, k1 = _batch(W.WD_F32, use_graph=1)
+        rc2, i2, k2 = _batch(W.WD_F32, use_graph=0)
+    finally:
+        W.wd_set_batch_mode(prev)
+    assert rc1 == rc2 == W.WD_OK
     for (_, _, _, x1), (_, _, _, x2) in zip(k1, k2):
         assert np.array_equal(x1, x2)
     assert [d["iters"] for d in i1] == [d["iters"] for d in i2]
+
+
+@pytest.mark.parametrize("prec", [W.WD_F32, W.WD_F16])
+def test_persistent_iteration_matches_per_step_launches(prec):
+    """One persistent cooperative launch per iteration against one launch per
+    step: the same algorithm up to the summation order of the norms, so every
+    right-hand side converges (oracle residual) in the same number of
+    iterations to within one check interval, and two persistent runs agree
+    bit for bit (fixed-order reductions)."""
+    out = {}
+    prev = W.wd_set_batch_mode(1)
+    try:
+        for mode in (1, 0, 1):
+            W.wd_set_batch_mode(mode)
+            rc, infos, keep = _batch(prec)
+            assert rc == W.WD_OK, mode
+            for dims, U, b, x in keep:
+                for r in range(b.shape[0]):
+                    rel = (np.linalg.norm(b[r] - oracle.apply_D(x[r], U, dims, 0.136))
+                           / np.linalg.norm(b[r]))
+                    assert rel <= 1.05e-10, (mode, dims, r, rel)
+            out.setdefault(mode, []).append((infos, [k[3].copy() for k in keep]))
+    finally:
+        W.wd_set_batch_mode(prev)
+    (i1, x1), (i1b, x1b) = out[1]
+    (i0, _), = out[0]
+    for a, b in zip(x1, x1b):
+        assert np.array_equal(a, b)
+    assert [d["iters"] for d in i1] == [d["iters"] for d in i1b]
+    for a, b in zip(i1, i0):
+        assert abs(a["iters"] - b["iters"]) <= 10, (a["iters"], b["iters"])
+
+
+def test_persistent_iteration_barrier_timeout():
+    """The failure path of the grid barriers, run on purpose and without any
+    fault: with a wait limit of 0 polls every CTA but the last to arrive gives
+    up at the first barrier, raises the error word and leaves, the others see
+    it at their next barrier and leave, and the solve returns WD_ERR_TIMEOUT.
+    The next solve with the default limit is exact."""
+    prev = W.wd_set_batch_mode(1)
+    try:
+        W.wd_set_wait_limit(0)
+        dims = (4, 4, 4, 8)
+        U = fields.su3_links(dims, workers=1)
+        b = np.ascontiguousarray(np.stack([fields.gaussian_spinor(dims, seed=s)
+                                           for s in (11, 12, 13)]))
+        x = np.zeros_like(b)
+        pr = [{"dims": dims, "kappa": 0.13, "nrhs": 3, "gauge": U, "b": b, "x": x}]
+        rc, _ = W.wd_solve_batch(pr, check=False)
+        assert rc == W.WD_ERR_TIMEOUT
+    finally:
+        W.wd_set_wait_limit(1 << 22)
+        W.wd_set_batch_mode(prev)
+    x[:] = 0
+    rc, infos = W.wd_solve_batch(pr)
+    assert rc == W.WD_OK
+    for r in range(3):
+        rel = np.linalg.norm(b[r] - oracle.apply_D(x[r], U, dims, 0.13)) / np.linalg.norm(b[r])
+        assert rel <= 1.05e-10
+
+
+def test_batch_mode_rejects_other_values():
+    with pytest.raises(W.WdError):
+        W.wd_set_batch_mode(2)
 
 
 def test_batch_device_buffers():
