@@ -240,7 +240,9 @@ int wd_dslash_mrhs(void *out, const void *in, const void *gauge, int parity, int
 
 /*
  * Autotuner of the multi-right-hand-side tile shape of wd_dslash_mrhs and of
- * the hopping launches of wd_solve_batch (the paper has no such component).
+ * the hopping launches of wd_solve_batch, and of the CTA size of the
+ * single-field hopping kernel (wd_dslash_set_block below); the paper has no
+ * such component.
  * A shape code is w (1, 2, 4 or 8 right-hand-side warps per CTA, one
  * right-hand side per thread) or, for FP32 only, 16 + w (w = 1, 2 or 4 warps,
  * two right-hand sides per thread: each link is loaded and rebuilt once for
@@ -258,13 +260,25 @@ int wd_dslash_mrhs(void *out, const void *in, const void *gauge, int parity, int
  */
 int wd_set_autotune(int enable);
 
+/* Force the CTA size (64, 128 or 256 sites) of every single-field hopping
+ * launch without a fused reduction, or go back to the tuned sizes (sites =
+ * 0).  The autotuner (wd_set_autotune) times the three sizes for each new
+ * (link format, dagger, temporal gauge, lattice extents) met outside stream
+ * capture, on a temporary output, and keeps the fastest; every size gives
+ * bit-identical fields.  Launches with a fused norm keep 128 sites, so that
+ * the summation order of the norm never depends on a timing.
+ * wd_dslash_ex_noalloc never tunes (it would allocate).  WD_ERR_ARG for
+ * other sizes. */
+int wd_dslash_set_block(int sites);
+
 /* Force one tile shape for every multi-RHS launch (lanes = a shape code:
  * 1, 2, 4, 8, 17, 18 or 20; FP64 and FP16 launches run 16 + w as w), or go
  * back to the tuned/default shapes (lanes = 0).  WD_ERR_ARG otherwise. */
 int wd_mrhs_set_lanes(int lanes);
 
-/* Text table of the tuned shapes, one line per batch shape with the
- * microseconds of every candidate and the choice.  Writes at most len bytes,
+/* Text table of the tuned shapes, one line per multi-RHS batch shape and
+ * per single-field hopping shape, with the microseconds of every candidate
+ * and the choice.  Writes at most len bytes,
  * NUL-terminated, into buf (buf may be NULL when len is 0).  Returns the
  * number of tuned shapes. */
 int wd_tune_report(char *buf, size_t len);

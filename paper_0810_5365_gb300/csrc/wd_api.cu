@@ -33,6 +33,7 @@ void solver_finalize();
 cudaError_t wait_selftest(long spins, int* err, cudaStream_t st);
 int set_autotune(int enable);
 int set_batch_mode(int mode);
+int dslash_set_block(int bs);
 int mrhs_set_lanes(int lanes);
 int tune_report(char* buf, size_t len);
 }  // namespace wd
@@ -294,6 +295,8 @@ int wd_set_batch_mode(int mode) {
 }
 
 int wd_mrhs_set_lanes(int lanes) { return mrhs_set_lanes(lanes); }
+
+int wd_dslash_set_block(int sites) { return dslash_set_block(sites); }
 
 int wd_tune_report(char* buf, size_t len) {
   return guarded([&] { return tune_report(buf, len); });

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "wd_mrhs.cuh"
@@ -245,6 +246,26 @@ int set_autotune(int enable) {
   return prev;
 }
 
+int autotune_enabled() { return g_autotune; }
+
+namespace {
+int g_dslash_block = 0;  // forced CTA size of the single-field hopping kernel (0: tuned)
+std::vector<std::string>& dslash_lines() {
+  static std::vector<std::string> v;
+  return v;
+}
+}  // namespace
+
+int dslash_forced_block() { return g_dslash_block; }
+
+int dslash_set_block(int bs) {
+  if (bs != 0 && bs != 64 && bs != 128 && bs != 256) return WD_ERR_ARG;
+  g_dslash_block = bs;
+  return WD_OK;
+}
+
+void dslash_tune_record(const char* line) { dslash_lines().push_back(line); }
+
 int mrhs_set_lanes(int lanes) {
   if (lanes != 0 && !valid_shape(lanes)) return WD_ERR_ARG;
   g_force_lanes = lanes;
@@ -270,7 +291,13 @@ int tune_report(char* buf, size_t len) {
       used += n;
     }
   }
-  return (int)tune_table().size();
+  for (const std::string& l : dslash_lines()) {
+    if (buf && used + l.size() + 1 <= len) {
+      std::memcpy(buf + used, l.c_str(), l.size() + 1);
+      used += l.size();
+    }
+  }
+  return (int)(tune_table().size() + dslash_lines().size());
 }
 
 // tune a launch shape without running it (before a graph capture)

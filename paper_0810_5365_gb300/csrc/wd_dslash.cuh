@@ -12,6 +12,8 @@
 // hops that cross t = L3-1 <-> 0; links are never modified.
 #pragma once
 
+#include <cstdio>
+#include <map>
 #include <type_traits>
 
 #include "wd_internal.h"
@@ -421,8 +423,16 @@ __device__ __forceinline__ void hops_f16(cx<float> (&acc)[12], const void* __res
 
 // TG: links in temporal gauge (compile-time, so that the ordinary kernel keeps
 // its register budget)
+// BS sites per CTA; the register budget per thread is that of the 128-site
+// CTAs for every BS (the same number of resident warps)
+template <int P, bool NORM, int BS>
+struct DslashMinBlocksBS {
+  static constexpr int raw = DslashMinBlocks<P, NORM>::value * DSLASH_BS / BS;
+  static constexpr int value = raw < 1 ? 1 : raw;
+};
+
 template <int P, int RC, bool DAG, int RED, bool TG, int BS>
-__global__ void __launch_bounds__(BS, DslashMinBlocks<P, RED != RED_NONE>::value)
+__global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>::value))
     dslash_kernel(const DslashArgs a) {
   constexpr int NRED = RED == RED_NONE ? 1 : RED == RED_NORM ? 1 : RED == RED_NORM_DOTX ? 3 : 2;
   using R = typename std::conditional<P == WD_F64, double, float>::type;
@@ -527,13 +537,27 @@ __global__ void __launch_bounds__(BS, DslashMinBlocks<P, RED != RED_NONE>::value
   }
 }
 
+// the non-reducing kernel with BS sites per CTA (64, 128 or 256)
 template <int P, int RC, bool DG, bool TG>
-cudaError_t launch_dslash_red_tg(const DslashArgs& a, dim3 grid, dim3 block, cudaStream_t st) {
+cudaError_t launch_dslash_plain_bs(const DslashArgs& a, int bs, cudaStream_t st) {
+  const unsigned n = (unsigned)a.g.Vh;
+  switch (bs) {
+    case 64: dslash_kernel<P, RC, DG, RED_NONE, TG, 64><<<(n + 63) / 64, 64, 0, st>>>(a); break;
+    case 256: dslash_kernel<P, RC, DG, RED_NONE, TG, 256><<<(n + 255) / 256, 256, 0, st>>>(a); break;
+    default:
+      dslash_kernel<P, RC, DG, RED_NONE, TG, DSLASH_BS>
+          <<<(n + DSLASH_BS - 1) / DSLASH_BS, DSLASH_BS, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int P, int RC, bool DG, bool TG>
+cudaError_t launch_dslash_red_tg(const DslashArgs& a, dim3 grid, dim3 block, int bs,
+                                 cudaStream_t st) {
   const int mode = a.norm_out ? a.red_mode : RED_NONE;
   switch (mode) {
     case RED_NONE:
-      dslash_kernel<P, RC, DG, RED_NONE, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
-      break;
+      return launch_dslash_plain_bs<P, RC, DG, TG>(a, bs, st);
     case RED_NORM:
       dslash_kernel<P, RC, DG, RED_NORM, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
       break;
@@ -557,25 +581,130 @@ cudaError_t launch_dslash_red_tg(const DslashArgs& a, dim3 grid, dim3 block, cud
 }
 
 template <int P, int RC, bool DG>
-cudaError_t launch_dslash_red(const DslashArgs& a, dim3 grid, dim3 block, cudaStream_t st) {
-  return a.tg ? launch_dslash_red_tg<P, RC, DG, true>(a, grid, block, st)
-              : launch_dslash_red_tg<P, RC, DG, false>(a, grid, block, st);
+cudaError_t launch_dslash_red(const DslashArgs& a, dim3 grid, dim3 block, int bs,
+                              cudaStream_t st) {
+  return a.tg ? launch_dslash_red_tg<P, RC, DG, true>(a, grid, block, bs, st)
+              : launch_dslash_red_tg<P, RC, DG, false>(a, grid, block, bs, st);
+}
+
+template <int P>
+cudaError_t launch_dslash_bs(const DslashArgs& a, int recon, bool dagger, int bs,
+                             cudaStream_t st) {
+  const int BS = DSLASH_BS;
+  dim3 grid((a.g.Vh + BS - 1) / BS), block(BS);
+  if (recon == 12)
+    return dagger ? launch_dslash_red<P, 12, true>(a, grid, block, bs, st)
+                  : launch_dslash_red<P, 12, false>(a, grid, block, bs, st);
+  if constexpr (P != WD_F16) {
+    if (recon == 18)
+      return dagger ? launch_dslash_red<P, 18, true>(a, grid, block, bs, st)
+                    : launch_dslash_red<P, 18, false>(a, grid, block, bs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Run-time choice of the CTA size of the non-reducing hopping kernel (64,
+// 128 or 256 sites, the same register budget per thread).  A launch shape
+// (link format, dagger, temporal gauge, lattice extents) met for the first
+// time outside stream capture is timed with each size (CUDA events, one
+// warm-up and three launches, on a temporary output, so no caller data is
+// written) and the fastest is kept for the life of the process.  Every size
+// gives bit-identical fields.  The reducing variants keep 128 sites, so
+// that the summation order of their norms does not depend on a timing.
+// ---------------------------------------------------------------------------
+
+struct DslashTuneKey {
+  int recon, dagger, tg, L[4];
+  bool operator<(const DslashTuneKey& o) const {
+    const int x[7] = {recon, dagger, tg, L[0], L[1], L[2], L[3]};
+    const int y[7] = {o.recon, o.dagger, o.tg, o.L[0], o.L[1], o.L[2], o.L[3]};
+    for (int k = 0; k < 7; k++)
+      if (x[k] != y[k]) return x[k] < y[k];
+    return false;
+  }
+};
+
+template <int P>
+std::map<DslashTuneKey, int>& dslash_tune_table() {
+  static std::map<DslashTuneKey, int> t;
+  return t;
+}
+
+template <int P>
+cudaError_t dslash_block(const DslashArgs& a, int recon, bool dagger, cudaStream_t st, int* bs) {
+  *bs = DSLASH_BS;
+  if (a.norm_out) return cudaSuccess;
+  if (dslash_forced_block()) {
+    *bs = dslash_forced_block();
+    return cudaSuccess;
+  }
+  const DslashTuneKey key{recon, dagger ? 1 : 0, a.tg, {a.g.L[0], a.g.L[1], a.g.L[2], a.g.L[3]}};
+  auto& tab = dslash_tune_table<P>();
+  auto it = tab.find(key);
+  if (it != tab.end()) {
+    *bs = it->second;
+    return cudaSuccess;
+  }
+  if (a.no_tune || !autotune_enabled()) return cudaSuccess;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) return cudaSuccess;
+  void* tmp = nullptr;
+  if (cudaMalloc(&tmp, spinor_half_bytes(a.g, P)) != cudaSuccess) {
+    cudaGetLastError();  // no room to tune: keep the default
+    return cudaSuccess;
+  }
+  DslashArgs t = a;
+  t.out = tmp;  // x and y keep pointing at the caller's fields: only read
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int sizes[3] = {64, 128, 256};
+  float us[3] = {0.f, 0.f, 0.f};
+  int best = DSLASH_BS;
+  float best_us = 0.f;
+  for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+    e = launch_dslash_bs<P>(t, recon, dagger, sizes[c], st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int k = 0; k < 3 && e == cudaSuccess; k++)
+      e = launch_dslash_bs<P>(t, recon, dagger, sizes[c], st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    us[c] = ms * 1e3f / 3.f;
+    if (best_us == 0.f || us[c] < best_us) {
+      best_us = us[c];
+      best = sizes[c];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaError_t fe = cudaFree(tmp);
+  if (e != cudaSuccess) return e;
+  if (fe != cudaSuccess) return fe;
+  tab[key] = best;
+  char line[256];
+  std::snprintf(line, sizeof(line),
+                "dslash prec=%d recon=%d dagger=%d tg=%d dims=%dx%dx%dx%d "
+                "us[64,128,256]=%.1f,%.1f,%.1f block=%d\n",
+                P, recon, key.dagger, key.tg, key.L[0], key.L[1], key.L[2], key.L[3], us[0],
+                us[1], us[2], best);
+  dslash_tune_record(line);
+  *bs = best;
+  return cudaSuccess;
 }
 
 // Launch one instance; the .cu file of each precision instantiates it.
 template <int P>
 cudaError_t launch_dslash_prec(const DslashArgs& a, int recon, bool dagger, cudaStream_t st) {
-  const int BS = DSLASH_BS;
-  dim3 grid((a.g.Vh + BS - 1) / BS), block(BS);
-  if (recon == 12)
-    return dagger ? launch_dslash_red<P, 12, true>(a, grid, block, st)
-                  : launch_dslash_red<P, 12, false>(a, grid, block, st);
-  if constexpr (P != WD_F16) {
-    if (recon == 18)
-      return dagger ? launch_dslash_red<P, 18, true>(a, grid, block, st)
-                    : launch_dslash_red<P, 18, false>(a, grid, block, st);
-  }
-  return cudaErrorInvalidValue;
+  int bs = DSLASH_BS;
+  cudaError_t e = dslash_block<P>(a, recon, dagger, st, &bs);
+  if (e != cudaSuccess) return e;
+  return launch_dslash_bs<P>(a, recon, dagger, bs, st);
 }
 
 }  // namespace wd

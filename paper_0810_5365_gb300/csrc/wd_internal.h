@@ -57,7 +57,15 @@ struct DslashArgs {
   //   RED_DOTZ       norm_out[0..1] = <z, out>   (re, im),  <a, b> = sum conj(a) b
   int red_mode = 1;
   const void* z = nullptr;
+  // 1: never time launch shapes for this call (it must not allocate)
+  int no_tune = 0;
 };
+
+// the run-time tuners (wd_batch.cu): on/off switch, a forced CTA size of the
+// single-field hopping kernel (0: tuned), and the report lines of its choices
+int autotune_enabled();
+int dslash_forced_block();
+void dslash_tune_record(const char* line);
 
 enum { RED_NONE = 0, RED_NORM = 1, RED_NORM_DOTX = 2, RED_DOTZ = 3 };
 

@@ -132,6 +132,7 @@ extern "C" int wd_dslash_ex_noalloc(void* out, const void* in, const void* gauge
   d.g = g;
   d.parity = parity;
   d.tg = tg;
+  d.no_tune = 1;  // the CTA size tuner allocates: use the tuned or default size
   e = launch_dslash(prec, d, recon, dagger != 0, st);
   if (e != cudaSuccess) {
     state().last_cuda_error = (int)e;

@@ -192,3 +192,70 @@ def test_convert_precisions():
     W.wd_convert_spinor(B, W.WD_F32, A, W.WD_F64, dims, W.WD_FULL)
     got = unpack_spinor(B, dims, W.WD_FULL, W.WD_F32)
     assert np.array_equal(got, psi.astype(np.complex64).astype(np.complex128))
+
+
+@pytest.mark.parametrize("prec,recon", [(W.WD_F64, 18), (W.WD_F32, 12), (W.WD_F16, 12)])
+@pytest.mark.parametrize("flags", [0, W.WD_TEMPORAL_GAUGE])
+def test_every_cta_size_is_bit_identical(prec, recon, flags):
+    """The CTA sizes the single-field autotuner may choose (64, 128, 256
+    sites) give bit-identical fields, H and H^+, with the fused epilogue, on
+    a lattice whose last CTA is ragged for every size; and they match the
+    oracle.  Temporal-gauge links come from the host definition."""
+    from tests._wdutil import temporal_gauge_links
+    dims = (6, 4, 6, 10)   # V/2 = 720 sites: 11.25, 5.6, 2.8 CTAs
+    U = fields.su3_links(dims, workers=1)
+    if flags:
+        U, _ = temporal_gauge_links(U, dims)
+    g = pack_gauge(U, dims, prec, recon)
+    psi = fields.gaussian_spinor(dims)
+    xh = fields.to_half(fields.gaussian_spinor(dims, seed=91), dims, 0)
+    src = fields.to_half(psi, dims, 1)
+    inp = pack_spinor(src, dims, 1, prec)
+    xb = pack_spinor(xh, dims, 0, prec)
+    try:
+        for dagger in (0, 1):
+            outs = {}
+            for bs in (128, 64, 256):
+                W.wd_dslash_set_block(bs)
+                out = W.alloc_spinor(dims, 0, prec)
+                W.wd_dslash_ex(out, inp, g, 0, dagger, -0.13, xb, 0.5, None, 0.0, None, dims,
+                               prec, recon | flags)
+                torch.cuda.synchronize()
+                outs[bs] = unpack_spinor(out, dims, 0, prec)
+            assert np.array_equal(outs[64], outs[128]) and np.array_equal(outs[256], outs[128])
+            want = -0.13 * oracle.hop_block(0, src, U, dims, dagger=bool(dagger)) + 0.5 * xh
+            assert rel_l2(outs[128], want) <= PREC_TOL[prec]
+    finally:
+        W.wd_dslash_set_block(0)
+
+
+def test_cta_size_tuner_reports_its_choice():
+    dims = (8, 6, 4, 12)   # a shape no other test uses
+    prev = W.wd_set_autotune(1)
+    try:
+        U = fields.su3_links(dims, workers=1)
+        g = pack_gauge(U, dims, W.WD_F32, 12)
+        inp = pack_spinor(fields.to_half(fields.gaussian_spinor(dims), dims, 1), dims, 1,
+                          W.WD_F32)
+        out = W.alloc_spinor(dims, 0, W.WD_F32)
+        W.wd_dslash(out, inp, g, 0.13, 0, dims, W.WD_F32)
+        torch.cuda.synchronize()
+    finally:
+        W.wd_set_autotune(prev)
+    _, text = W.wd_tune_report()
+    mine = [l for l in text.splitlines() if l.startswith("dslash prec=1 recon=12 dagger=0 tg=0")
+            and "dims=8x6x4x12 " in l]
+    assert len(mine) == 1, text
+    us = [float(v) for v in mine[0].split("us[64,128,256]=")[1].split()[0].split(",")]
+    block = int(mine[0].split("block=")[1])
+    assert all(v > 0 for v in us) and us[[64, 128, 256].index(block)] == min(us)
+    # the choice changes nothing in the result
+    want = -0.13 * oracle.hop_block(0, fields.to_half(fields.gaussian_spinor(dims), dims, 1), U,
+                                    dims)
+    assert rel_l2(unpack_spinor(out, dims, 0, W.WD_F32), want) <= PREC_TOL[W.WD_F32]
+
+
+def test_cta_size_rejects_other_values():
+    for bad in (32, 96, 512):
+        with pytest.raises(W.WdError):
+            W.wd_dslash_set_block(bad)
