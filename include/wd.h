@@ -565,23 +565,28 @@ int wd_solve_fgcr(double *x, const double *b, const double *gauge, double kappa,
                   const wd_solve_params *params, wd_solve_info *info);
 
 /*
- * Flexible CG on the normal equations D^+ D x = D^+ b of the full lattice,
- * preconditioned by N N^+ with N the network above (weights NULL: plain
- * CGNR).  N N^+ is Hermitian positive definite, so the method converges where
- * GCR on D stalls (kappa beyond the critical region of the links, where the
- * spectrum of D surrounds the origin).  FP32 vectors and operator, BF16
- * network arithmetic; the small variation of N's rounding between
- * applications is absorbed by the flexible (Polak-Ribiere) beta.  FP64
- * reliable updates every params->reliable_interval iterations and whenever
- * the FP32 residual looks converged (x accumulated and r = b - D x recomputed
- * in FP64; the search direction restarts).  Stops on ||b - D x|| / ||b|| <=
- * params->tol in FP64.  Plain CG is the fallback: should the preconditioned
- * iteration stop short (params->maxiter, a non-finite residual, a network
- * wait that timed out) the even-odd mixed-precision CG of wd_solve_ex
- * continues from its iterate (info->fallback_iters > 0).  The paper's solver
- * is the unpreconditioned even-odd CG; this is an addition.  x, b, gauge:
- * canonical FP64, host or device.  info->reliable_updates counts the FP64
- * residual recomputations.
+ * Flexible CG on the even-odd preconditioned system (the paper's solver),
+ * preconditioned by the network above (weights NULL: CG on the normal
+ * equations of the even-odd system, no preconditioner).  The even-even block
+ * of D^-1 is exactly the inverse of Mhat = 1 - kappa^2 H_eo H_oe, so the
+ * even-even block N_e of a network trained as an approximate inverse of D
+ * approximates Mhat^-1.  CG runs on Mhat^+ Mhat x_e = Mhat^+ bhat_e with the
+ * preconditioner N_e N_e^+, which is Hermitian positive definite, so the
+ * method converges where GCR on D stalls (kappa beyond the critical region of
+ * the links, where the spectrum of D surrounds the origin); then
+ * x_o = b_o + kappa H_oe x_e.  FP32 vectors and operator, BF16 network
+ * arithmetic; the small variation of N's rounding between applications is
+ * absorbed by the flexible (Polak-Ribiere) beta.  FP64 reliable updates
+ * every params->reliable_interval iterations and whenever the FP32 residual
+ * looks converged (x accumulated and r = bhat - Mhat x recomputed in FP64;
+ * the search direction restarts).  Stops on ||b - D x|| / ||b|| <=
+ * params->tol, computed in FP64 on the full lattice.  Plain CG is the
+ * fallback: should the preconditioned iteration stop short (params->maxiter,
+ * a non-finite residual, a network wait that timed out) the even-odd
+ * mixed-precision CG of wd_solve_ex continues from its iterate
+ * (info->fallback_iters > 0).  The preconditioner is an addition to the
+ * paper.  x, b, gauge: canonical FP64, host or device.  info->reliable_updates
+ * counts the FP64 residual recomputations.
  */
 int wd_solve_fcg(double *x, const double *b, const double *gauge, double kappa,
                  const int dims[4], const float *weights, const wd_solve_params *params,

@@ -64,8 +64,11 @@ static cudaError_t launch_layer(const NnLayerArgs& A, int ntiles, cudaStream_t s
   return cudaGetLastError();
 }
 
+// out_parity: -1 both parities, else only that one; zero_in: the parity of
+// the input known to vanish (never read), or -1
 static cudaError_t nn_layer(int cin, int cout, const Geom& g, const void* gauge, const void* in,
-                            void* out, const float* w, int* err, cudaStream_t st) {
+                            void* out, const float* w, int* err, cudaStream_t st,
+                            int out_parity = -1, int zero_in = -1) {
   NnLayerArgs A;
   A.g = g;
   A.gauge = gauge;
@@ -75,7 +78,10 @@ static cudaError_t nn_layer(int cin, int cout, const Geom& g, const void* gauge,
   A.out_half = nn_half_bytes(g.Vh_pad, cout);
   A.w = w;
   A.err = err;
-  const int ntiles = 2 * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  A.p0 = out_parity < 0 ? 0 : out_parity;
+  A.np = out_parity < 0 ? 2 : 1;
+  A.zero_in = zero_in;
+  const int ntiles = A.np * ((g.Vh + NN_TILE - 1) / NN_TILE);
   if (cin == 4 && cout == 8) return launch_layer<4, 8>(A, ntiles, st);
   if (cin == 8 && cout == 8) return launch_layer<8, 8>(A, ntiles, st);
   if (cin == 8 && cout == 4) return launch_layer<8, 4>(A, ntiles, st);
@@ -425,6 +431,21 @@ static cudaError_t nn_forward(const Geom& g, const void* gauge, const float* w, 
   return nn_layer(8, 4, g, gauge, B.h2, out, w + nn_layer_offset(2), err, st);
 }
 
+// The even-even block P_e N P_e: the odd half of `in` is taken as zero and
+// never read (the first layer's even sites keep only their self term, its
+// odd sites only their hops), and the last layer computes the even sites
+// only (the odd half of `out` is left as it was).  About 2/3 of the work of
+// the full network.
+static cudaError_t nn_forward_even(const Geom& g, const void* gauge, const float* w,
+                                   const void* in, void* out, NnBuffers& B, int* err,
+                                   cudaStream_t st) {
+  cudaError_t e;
+  if ((e = nn_layer(4, 8, g, gauge, in, B.h1, w + nn_layer_offset(0), err, st, -1, WD_ODD)))
+    return e;
+  if ((e = nn_layer(8, 8, g, gauge, B.h1, B.h2, w + nn_layer_offset(1), err, st))) return e;
+  return nn_layer(8, 4, g, gauge, B.h2, out, w + nn_layer_offset(2), err, st, WD_EVEN);
+}
+
 // (1 + c kappa H) on the first four channels of a layer; identity on the rest
 static void init_hopping_layer(float* w, int cin, int cout, double cr, double ci, double kappa) {
   // chiral basis: gamma_mu = [[0, A_mu], [A_mu^+, 0]], A = -i sigma_{1,2,3}, A_t = 1
@@ -600,9 +621,10 @@ __global__ void __launch_bounds__(256) gcr_update_kernel(char* x, char* r, const
   if (grid_reduce<1, 256>(acc, rs, tot) && threadIdx.x == 0) out[0] = tot[0];
 }
 
-// x64 += xs (F32 -> F64, full fields); xs = 0
-__global__ void accumulate_full_kernel(char* x64, char* xs, Geom g, size_t h64, size_t h32) {
-  const long long n = 2LL * g.Vh;
+// x64 += xs (F32 -> F64; nh halves: 2 full fields, 1 the even sites); xs = 0
+__global__ void accumulate_full_kernel(char* x64, char* xs, Geom g, size_t h64, size_t h32,
+                                       int nh = 2) {
+  const long long n = (long long)nh * g.Vh;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
@@ -623,8 +645,9 @@ __global__ void accumulate_full_kernel(char* x64, char* xs, Geom g, size_t h64, 
 
 
 // ---------------------------------------------------------------------------
-// flexible CG on the normal equations D^+ D x = D^+ b with the preconditioner
-// N N^+ (N the network): packed FP32 full fields, scalars on the device.
+// flexible CG on normal equations A^+ A x = A^+ b with the preconditioner
+// N N^+ (N the network): packed FP32 fields of nh halves (nh = 1: the even
+// sites), scalars on the device.
 // rho[kp] = <s, z> of the current iteration, rho[1-kp] that of the next one;
 // qq[0..1] = ||D p||^2 on the even / odd half.
 // ---------------------------------------------------------------------------
@@ -641,10 +664,10 @@ struct FcgScalars {
 // x += alpha p ; r -= alpha q ; rr = ||r||^2 ; alpha = rho[kp] / ||q||^2
 __global__ void __launch_bounds__(256) fcg_update_xr(char* x, char* r, const char* p,
                                                      const char* q, FcgScalars* sc, int kp,
-                                                     Geom g, size_t half, RedScratch rs) {
+                                                     Geom g, size_t half, int nh, RedScratch rs) {
   const float a = (float)(sc->rho[kp] / (sc->qq[0] + sc->qq[1]));
   double acc[1] = {0.0};
-  const long long n = 2LL * g.Vh;
+  const long long n = (long long)nh * g.Vh;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
     cx<float> xv[12], rv[12], pv[12], qv[12];
@@ -670,9 +693,9 @@ __global__ void __launch_bounds__(256) fcg_update_xr(char* x, char* r, const cha
 // rho[slot] = Re <s, z> ; zeta = Re <s_old, z> (s_old may be null: zeta = 0)
 __global__ void __launch_bounds__(256) fcg_dots(const char* s, const char* s_old, const char* z,
                                                 FcgScalars* sc, int slot, Geom g, size_t half,
-                                                RedScratch rs) {
+                                                int nh, RedScratch rs) {
   double acc[3] = {0.0, 0.0, 0.0};
-  const long long n = 2LL * g.Vh;
+  const long long n = (long long)nh * g.Vh;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
     cx<float> sv[12], zv[12];
@@ -694,9 +717,10 @@ __global__ void __launch_bounds__(256) fcg_dots(const char* s, const char* s_old
 
 // p = z + beta p, beta = (rho[1-kp] - zeta) / rho[kp]  (restart: p = z)
 __global__ void __launch_bounds__(256) fcg_update_p(char* p, const char* z, const FcgScalars* sc,
-                                                    int kp, int restart, Geom g, size_t half) {
+                                                    int kp, int restart, Geom g, size_t half,
+                                                    int nh) {
   const float beta = restart ? 0.f : (float)((sc->rho[1 - kp] - sc->zeta) / sc->rho[kp]);
-  const long long n = 2LL * g.Vh;
+  const long long n = (long long)nh * g.Vh;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
     cx<float> pv[12], zv[12];
@@ -1131,17 +1155,28 @@ int fgcr_impl(double* x, const double* bsrc, const double* gauge, double kappa,
 int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
                const wd_solve_params* prm, wd_solve_info* info);
 
-// Flexible CG on the normal equations D^+ D x = D^+ b, preconditioned by
-// N N^+ (N the network; w == nullptr: plain CGNR), with FP32 vectors and
-// operator, FP64 reliable updates (x accumulated and r = b - D x recomputed in
-// FP64 every `reliable_interval` iterations and whenever the FP32 residual
-// looks converged; the search direction restarts there).  N N^+ is Hermitian
-// and positive definite, so CG applies; its BF16 arithmetic perturbs it a
-// little from one application to the next, which the Polak-Ribiere form of
-// beta = <z_new, s_new - s_old> / <z_old, s_old> absorbs (flexible CG,
-// Notay, SIAM J. Sci. Comput. 22, 2000).  If this does not reach the
-// tolerance (maxiter, a non-finite residual, a network wait that timed out),
-// the plain mixed-precision even-odd CG continues from the best iterate.
+// Flexible CG on the even-odd preconditioned system, preconditioned by the
+// network.  The even-even block of D^-1 is exactly the inverse of the Schur
+// complement Mhat = 1 - kappa^2 H_eo H_oe, so the even-even block of a
+// network trained as an approximate inverse of D, N_e = P_e N P_e, is an
+// approximate inverse of Mhat.  CG runs on Mhat^+ Mhat x_e = Mhat^+ bhat_e
+// (bhat_e = b_e + kappa H_eo b_o) with the preconditioner N_e N_e^+, which is
+// Hermitian and positive definite, so CG converges whatever the spectrum of
+// D; then x_o = b_o + kappa H_oe x_e.  An even-only input lets the network
+// skip a third of its work (nn_forward_even).  BF16 rounding makes N_e vary
+// slightly between applications; the Polak-Ribiere form of beta,
+// <z_new, s_new - s_old> / <z_old, s_old> (flexible CG, Notay, SIAM J. Sci.
+// Comput. 22, 2000) absorbs that.  FP32 vectors and operator, FP64 reliable
+// updates (x accumulated and r = bhat - Mhat x recomputed in FP64 every
+// `reliable_interval` iterations and whenever the FP32 residual looks
+// converged; the search direction restarts there).  The true residual
+// ||b - D x|| is computed in FP64 on the full lattice.  If this does not
+// reach the tolerance (maxiter, a non-finite residual, a network wait that
+// timed out), the plain mixed-precision even-odd CG continues from the best
+// iterate.  wts == nullptr: CGNR on the even-odd system, no network.
+int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
+               const wd_solve_params* prm, wd_solve_info* info);
+
 int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, const int dims[4],
              const float* wts, const wd_solve_params* prm, wd_solve_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -1180,14 +1215,20 @@ int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, c
       NCK(cudaMemcpyAsync(canon, bsrc, V * 24 * sizeof(double), cudaMemcpyHostToDevice, st));
       bd = canon;
     }
-    void *b64, *x64, *r64, *r, *xs, *p, *q, *sA, *sB, *w, *z, *scal, *wa = nullptr;
+    // FP64: b (full), x (full), bhat, r64 (even), t64 (odd); FP32 even
+    // fields, and full-size buffers for the network's input and output
+    // (their even halves are used)
+    void *b64, *x64, *bhat, *r64, *t64, *r, *xs, *p, *q, *ts, *sA, *sB, *w, *z, *scal, *wa = nullptr;
     NCK(al.get(&b64, 2 * h64));
     NCK(al.get(&x64, 2 * h64));
-    NCK(al.get(&r64, 2 * h64));
-    NCK(al.get(&r, 2 * h32));
-    NCK(al.get(&xs, 2 * h32));
-    NCK(al.get(&p, 2 * h32));
-    NCK(al.get(&q, 2 * h32));
+    NCK(al.get(&bhat, h64));
+    NCK(al.get(&r64, h64));
+    NCK(al.get(&t64, h64));
+    NCK(al.get(&r, h32));
+    NCK(al.get(&xs, h32));
+    NCK(al.get(&p, h32));
+    NCK(al.get(&q, h32));
+    NCK(al.get(&ts, h32));
     NCK(al.get(&sA, 2 * h32));
     NCK(al.get(&sB, 2 * h32));
     NCK(al.get(&w, 2 * h32));
@@ -1215,8 +1256,8 @@ int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, c
     NCK(pack_spinor(b64, bd, g, WD_FULL, WD_F64, st));
     NCK(norm2(&S->bn, b64, g, WD_F64, 2, st));
     NCK(cudaMemsetAsync(x64, 0, 2 * h64, st));
-    NCK(cudaMemsetAsync(xs, 0, 2 * h32, st));
-    const int grid = blas_grid(V, 256);
+    NCK(cudaMemsetAsync(xs, 0, h32, st));
+    const int grid = blas_grid(g.Vh, 256);
     RedScratch rs = scratch();
     FcgScalars hs;
     auto rd = [&]() -> cudaError_t {
@@ -1224,60 +1265,73 @@ int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, c
       if (e != cudaSuccess) return e;
       return cudaStreamSynchronize(st);
     };
-    // z = N N^+ s (or z = s without a network)
-    auto precond = [&](void* zo, const void* si) -> cudaError_t {
-      if (!wts) return cudaMemcpyAsync(zo, si, 2 * h32, cudaMemcpyDeviceToDevice, st);
-      cudaError_t e = nn_forward(g, g32, (const float*)wa, si, w, B, flag, st);
+    // one parity-restricted hopping launch: out = a H in + bx x + cy y
+    auto hop = [&](int prec, int recon, const void* gauge_p, void* out, const void* in, int parity,
+                   bool dagger, double a, const void* xf, double bx, const void* yf, double cy,
+                   double* nrm) -> cudaError_t {
+      DslashArgs d;
+      d.out = out;
+      d.in = in;
+      d.gauge = gauge_p;
+      d.a = a;
+      d.x = xf;
+      d.bx = bx;
+      d.y = yf;
+      d.cy = cy;
+      d.norm_out = nrm;
+      d.rs = rs;
+      d.g = g;
+      d.parity = parity;
+      return launch_dslash(prec, d, recon, dagger, st);
+    };
+    // out = Mhat in (or Mhat^+) in FP32 on the even sites, ||out||^2 -> nrm
+    auto mhat = [&](void* out, const void* in, bool dagger, double* nrm) -> cudaError_t {
+      cudaError_t e = hop(WD_F32, 12, g32, ts, in, WD_ODD, dagger, 1.0, nullptr, 0.0, nullptr, 0.0,
+                          nullptr);
       if (e != cudaSuccess) return e;
-      return nn_forward(g, g32, wts, w, zo, B, flag, st);
+      return hop(WD_F32, 12, g32, out, ts, WD_EVEN, dagger, -kappa * kappa, in, 1.0, nullptr, 0.0,
+                 nrm);
     };
-    // q = D p with ||q||^2 per half
-    auto apply_D = [&](void* out, const void* in) -> cudaError_t {
-      for (int par = 0; par < 2; par++) {
-        DslashArgs d;
-        d.out = (char*)out + par * h32;
-        d.in = (const char*)in + (1 - par) * h32;
-        d.gauge = g32;
-        d.a = -kappa;
-        d.x = (const char*)in + par * h32;
-        d.bx = 1.0;
-        d.y = nullptr;
-        d.cy = 0.0;
-        d.norm_out = &S->qq[par];
-        d.rs = rs;
-        d.g = g;
-        d.parity = par;
-        cudaError_t e = launch_dslash(WD_F32, d, 12, false, st);
-        if (e != cudaSuccess) return e;
-      }
-      return cudaSuccess;
+    // z = N_e N_e^+ s (or z = s without a network)
+    auto precond = [&](void* zo, const void* si) -> cudaError_t {
+      if (!wts) return cudaMemcpyAsync(zo, si, h32, cudaMemcpyDeviceToDevice, st);
+      cudaError_t e = nn_forward_even(g, g32, (const float*)wa, si, w, B, flag, st);
+      if (e != cudaSuccess) return e;
+      return nn_forward_even(g, g32, wts, w, zo, B, flag, st);
     };
+    // bhat = b_e + kappa H_eo b_o (FP64)
+    NCK(hop(WD_F64, 18, g64, bhat, (const char*)b64 + h64, WD_EVEN, false, kappa, b64, 1.0,
+            nullptr, 0.0, nullptr));
     void* s_cur = sA;
     void* s_old = sB;
     int kp = 0;
-    // r64 = b - D x64 (FP64), r = r64, s = D^+ r, z = N N^+ s, p = z
+    // r64 = bhat - Mhat x64_e (FP64), r = r64, s = Mhat^+ r, z = N_e N_e^+ s, p = z
     auto restart = [&]() -> cudaError_t {
-      cudaError_t e = full_op(WD_F64, 18, g64, r64, x64, kappa, g, st, b64);
-      if (e == cudaSuccess) e = norm2(&S->r64, r64, g, WD_F64, 2, st);
-      if (e == cudaSuccess) e = convert_spinor(r, WD_F32, r64, WD_F64, g, 2, st);
-      if (e == cudaSuccess) e = full_op(WD_F32, 12, g32, s_cur, r, kappa, g, st, nullptr, true);
+      cudaError_t e = hop(WD_F64, 18, g64, t64, x64, WD_ODD, false, 1.0, nullptr, 0.0, nullptr,
+                          0.0, nullptr);
+      if (e == cudaSuccess)
+        e = hop(WD_F64, 18, g64, r64, t64, WD_EVEN, false, kappa * kappa, x64, -1.0, bhat, 1.0,
+                &S->r64);
+      if (e == cudaSuccess) e = convert_spinor(r, WD_F32, r64, WD_F64, g, 1, st);
+      if (e == cudaSuccess) e = mhat(s_cur, r, true, nullptr);
       if (e == cudaSuccess) e = precond(z, s_cur);
       if (e != cudaSuccess) return e;
-      fcg_dots<<<grid, 256, 0, st>>>((const char*)s_cur, nullptr, (const char*)z, S, kp, g, h32, rs);
-      fcg_update_p<<<grid, 256, 0, st>>>((char*)p, (const char*)z, S, kp, 1, g, h32);
+      fcg_dots<<<grid, 256, 0, st>>>((const char*)s_cur, nullptr, (const char*)z, S, kp, g, h32, 1,
+                                     rs);
+      fcg_update_p<<<grid, 256, 0, st>>>((char*)p, (const char*)z, S, kp, 1, g, h32, 1);
       return cudaGetLastError();
     };
     NCK(restart());
     NCK(rd());
     const double bnorm = std::sqrt(hs.bn);
+    // the even-odd residual equals the full one up to rounding: aim a little lower
     const double target = P.tol * bnorm * 0.9;
-    rel = bnorm > 0 ? std::sqrt(hs.r64) / bnorm : 0.0;
     bool done = !(bnorm > 0) || std::sqrt(hs.r64) <= target;
     int since = 0;
     while (!done && iters < P.maxiter) {
-      NCK(apply_D(q, p));
+      NCK(mhat(q, p, false, &S->qq[0]));
       fcg_update_xr<<<grid, 256, 0, st>>>((char*)xs, (char*)r, (const char*)p, (const char*)q, S,
-                                         kp, g, h32, rs);
+                                         kp, g, h32, 1, rs);
       NCK(cudaGetLastError());
       iters++;
       since++;
@@ -1288,14 +1342,13 @@ int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, c
         break;
       }
       if (rn <= target || since >= P.reliable_interval) {
-        accumulate_full_kernel<<<grid, 256, 0, st>>>((char*)x64, (char*)xs, g, h64, h32);
+        accumulate_full_kernel<<<grid, 256, 0, st>>>((char*)x64, (char*)xs, g, h64, h32, 1);
         NCK(cudaGetLastError());
         NCK(restart());
         NCK(rd());
         restarts++;
         since = 0;
         const double r64v = std::sqrt(hs.r64);
-        rel = r64v / bnorm;
         if (!std::isfinite(r64v)) {
           status = WD_ERR_NONFINITE;
           break;
@@ -1304,19 +1357,32 @@ int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, c
         continue;
       }
       std::swap(s_cur, s_old);
-      NCK(full_op(WD_F32, 12, g32, s_cur, r, kappa, g, st, nullptr, true));
+      NCK(mhat(s_cur, r, true, nullptr));
       NCK(precond(z, s_cur));
       fcg_dots<<<grid, 256, 0, st>>>((const char*)s_cur, (const char*)s_old, (const char*)z, S,
-                                    1 - kp, g, h32, rs);
-      fcg_update_p<<<grid, 256, 0, st>>>((char*)p, (const char*)z, S, kp, 0, g, h32);
+                                     1 - kp, g, h32, 1, rs);
+      fcg_update_p<<<grid, 256, 0, st>>>((char*)p, (const char*)z, S, kp, 0, g, h32, 1);
       NCK(cudaGetLastError());
       kp ^= 1;
     }
     if (done) status = WD_OK;
-    // the best iterate: x64 (xs was folded in at the last reliable update;
-    // fold whatever accumulated since)
-    accumulate_full_kernel<<<grid, 256, 0, st>>>((char*)x64, (char*)xs, g, h64, h32);
+    // the best iterate: x64_e (plus whatever accumulated since the last
+    // reliable update), then x_o = b_o + kappa H_oe x_e, and the true
+    // residual of the full system in FP64: r_e = b_e - x_e + kappa H_eo x_o
+    // (the odd rows vanish up to rounding; they are computed as well)
+    accumulate_full_kernel<<<grid, 256, 0, st>>>((char*)x64, (char*)xs, g, h64, h32, 1);
     NCK(cudaGetLastError());
+    NCK(hop(WD_F64, 18, g64, (char*)x64 + h64, x64, WD_ODD, false, kappa, (const char*)b64 + h64,
+            1.0, nullptr, 0.0, nullptr));
+    {
+      // true residual: ||b - D x||^2 from the FP64 full field r64f
+      void* rf;
+      NCK(al.get(&rf, 2 * h64));
+      NCK(full_op(WD_F64, 18, g64, rf, x64, kappa, g, st, b64));
+      NCK(norm2(&S->r64, rf, g, WD_F64, 2, st));
+      NCK(rd());
+      rel = bnorm > 0 ? std::sqrt(hs.r64) / bnorm : 0.0;
+    }
     const bool xdev = on_device(x);
     double* xd = xdev ? x : canon;
     NCK(unpack_spinor(xd, x64, g, WD_FULL, WD_F64, st));

@@ -42,6 +42,12 @@ struct NnLayerArgs {
   size_t in_half, out_half;  // bytes per parity half
   const float* w;          // [9][COUT][CIN] complex (re, im)
   int* err;
+  // parity restriction (the even-odd preconditioner): only output sites of
+  // parity p0 .. p0 + np - 1 are computed; the input of parity zero_in
+  // (-1: none) is known to vanish and is never read, so an output site of
+  // that parity gets only its self term and one of the other parity only its
+  // hops
+  int p0 = 0, np = 2, zero_in = -1;
 };
 
 __host__ __device__ constexpr size_t nn_half_bytes(const int vh_pad, int C) {
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(NN_THREADS, WD_NN_MINB) nn_layer_kernel(const 
   const int s = tid & (NN_TILE - 1);   // site of the tile = A row = TMEM lane
   const int hh = tid >> 7;             // which half of the chunk's K columns
   const Geom& g = A.g;
-  const int tpp = (g.Vh + NN_TILE - 1) / NN_TILE;
+  const int tpp = (g.Vh + NN_TILE - 1) / NN_TILE;  // tiles per parity
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -273,9 +279,11 @@ __global__ void __launch_bounds__(NN_THREADS, WD_NN_MINB) nn_layer_kernel(const 
   uint32_t G = 0;  // chunks issued by this CTA so far
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int p = tile / tpp;
-    const int cb = (tile - p * tpp) * NN_TILE + s;
+    const int pt = tile / tpp;
+    const int p = A.p0 + pt;
+    const int cb = (tile - pt * tpp) * NN_TILE + s;
     const bool valid = cb < g.Vh;
+    const bool skip_self = A.zero_in == p, skip_hops = A.zero_in == 1 - p;
     int nb[NN_NDIR];
     int x3 = 0;
     if (valid) nn_nbr(nb, x3, cb, p, g);
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(NN_THREADS, WD_NN_MINB) nn_layer_kernel(const 
         n = hh ? nb[2 * c + 1 < NN_NDIR ? 2 * c + 1 : 0] : nb[2 * c];
       }
       cx<float> t[12];
-      if (valid && d < NN_NDIR) {
+      if (valid && d < NN_NDIR && !(d == 0 ? skip_self : skip_hops)) {
         nn_transport4<CIN>(t, A, d, p, cb, n, x3, c0);
       } else {
 #pragma unroll

@@ -1,13 +1,14 @@
-"""Flexible CG on the normal equations with the network preconditioner N N^+
-(GPU), at kappa = 0.137: beyond the critical region of these links, where
-GCR on D stalls.  Every solve is judged by the oracle's own true residual
+"""Flexible CG on the even-odd system with the network preconditioner
+N_e N_e^+ (GPU), at kappa = 0.137: beyond the critical region of these links,
+where GCR on D stalls.  Every solve is judged by the oracle's own true residual
 ||b - D x|| / ||b|| on the whole lattice (FP64, C oracle), computed from the
 returned x.
 
 * series weights (the truncated hopping series of D^-1), trained weights and
   no network (plain CGNR) each reach 1.05e-10 without the plain-CG fallback;
-* the series preconditioner needs well under half the iterations of plain
-  CGNR;
+* the series preconditioner needs well under the iterations of the
+  unpreconditioned even-odd CGNR (its even-even block is 1 + kappa^2 H_eo H_oe,
+  the first Neumann term of Mhat^-1);
 * the fallback: with maxiter = 3 the preconditioned iteration stops short and
   the even-odd CG finishes the solve from its iterate.
 """
@@ -60,7 +61,7 @@ def test_fcg_series_trained_and_plain(problem):
         assert r <= 1.05e-10, (name, r, info)
         assert abs(r - info["true_residual"]) <= 1e-11, (name, r, info)
         iters[name] = info["iters"]
-    assert iters["series"] < 0.5 * iters["plain"], iters
+    assert iters["series"] < 0.7 * iters["plain"], iters
 
 
 def test_fcg_falls_back_to_plain_cg(problem):
