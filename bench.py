@@ -702,6 +702,8 @@ def profile_case(name):
     ``batch``     one batched FP32-inner solve of 12 point sources on 24^3x48
                   (one launch per step);
     ``batch_persistent``  the same with one persistent launch per iteration;
+    ``fcg``       one learned-preconditioner solve (series weights, flexible CG
+                  on the even-odd system) on 16^3x32 at kappa 0.137;
     ``train``     4 Adam steps of 16 samples on 16^3x32 (forward, adjoint and
                   tensor-core weight-gradient kernels);
     ``nn``        2 applications of the series-initialised network (three
@@ -775,6 +777,17 @@ def profile_case(name):
         p.inner_prec = W.WD_F32
         W.wd_set_batch_mode(1)
         W.wd_solve_batch(probs, p)
+    elif name == "fcg":
+        # one learned-preconditioner solve (series weights) on 16^3x32 at
+        # kappa = 0.137: flexible CG on the even-odd system with N_e N_e^+
+        dims = (16, 16, 16, 32)
+        Ud = torch.from_numpy(fields.su3_links(dims).view(np.float64).reshape(-1)).cuda()
+        b = torch.from_numpy(fields.gaussian_spinor(dims, seed=2026).view(np.float64)
+                             .reshape(-1)).cuda()
+        x = torch.zeros_like(b)
+        w = torch.zeros(W.WD_NN_PARAMS, dtype=torch.float32, device="cuda")
+        W.wd_nn_init(w, NN_KAPPA)
+        W.wd_solve_fcg(x, b, Ud, NN_KAPPA, dims, w)
     elif name == "train":
         dims = (16, 16, 16, 32)
         Ud = torch.from_numpy(fields.su3_links(dims).view(np.float64).reshape(-1)).cuda()
@@ -1040,7 +1053,7 @@ def main():
     ap.add_argument("--no-oracle-cg", action="store_true",
                     help="skip the oracle's full FP64 CG timing (about 100 s of host time)")
     ap.add_argument("--profile", choices=["mrhs", "solve_f32", "solve_f16", "batch",
-                                          "batch_persistent", "train", "nn",
+                                          "batch_persistent", "fcg", "train", "nn",
                                           "staged"],
                     help="run a short fixed workload for an ncu capture and exit")
     args = ap.parse_args()
