@@ -548,6 +548,25 @@ int wd_gaussian_spinor(void *out, unsigned long long seed, unsigned long long st
 int wd_nn_apply(void *out, const void *in, const float *weights, const void *gauge,
                 const int dims[4]);
 
+/*
+ * out = N(in) with options (flags, OR-ed; the paper has no such component):
+ *   WD_NN_BF16  activations between the layers in BF16 (one bf16x2 per
+ *               complex value), the link transport in packed bf16x2
+ *               arithmetic, the channel mixing on the tensor cores with FP32
+ *               accumulation: about twice as fast, with about 2^-8 relative
+ *               rounding per layer.  in and out stay packed FP32 fields.
+ *   WD_NN_EVEN  only the even-even block P_e N P_e: the odd half of in is
+ *               taken as zero and never read, the odd half of out is not
+ *               written (the first layer gives even sites only their self
+ *               term and odd sites only their hops; the last layer computes
+ *               the even sites only).
+ * wd_solve_fcg applies N_e with both.  Synchronous; WD_ERR_ARG for other
+ * flag bits.
+ */
+enum { WD_NN_BF16 = 1, WD_NN_EVEN = 2 };
+int wd_nn_apply_ex(void *out, const void *in, const float *weights, const void *gauge,
+                   const int dims[4], int flags);
+
 /* Train N on pairs (D x, x) generated on the GPU (Adam, loss ||N(Dx) - x||^2).
  * gauge: canonical FP64 (host or device).  weights: device, in/out. */
 int wd_nn_train(float *weights, const double *gauge, double kappa, const int dims[4],

@@ -9,6 +9,8 @@
 namespace wd {
 int nn_apply_impl(void* out, const void* in, const float* w, const void* gauge, const int dims[4]);
 int nn_init_impl(float* w_dev, double kappa);
+int nn_apply_ex_impl(void* out, const void* in, const float* w, const void* gauge,
+                     const int dims[4], int flags);
 int nn_layer_impl(void* out, const void* in, const float* w, int cin, int cout, const void* gauge,
                   const int dims[4]);
 int gaussian_spinor_impl(void* out, unsigned long long seed, unsigned long long stream,
@@ -425,6 +427,16 @@ int wd_nn_apply(void* out, const void* in, const float* weights, const void* gau
   if (!aligned(out) || !aligned(in) || !aligned(weights) || !aligned(gauge)) return WD_ERR_ALIGN;
   if (out == in) return WD_ERR_ALIAS;
   return guarded([&] { return nn_apply_impl(out, in, weights, gauge, dims); });
+}
+
+int wd_nn_apply_ex(void* out, const void* in, const float* weights, const void* gauge,
+                   const int dims[4], int flags) {
+  WD_TRY(check_dims(dims));
+  if (!out || !in || !weights || !gauge) return WD_ERR_NULL;
+  if (!aligned(out) || !aligned(in) || !aligned(weights) || !aligned(gauge)) return WD_ERR_ALIGN;
+  if (out == in) return WD_ERR_ALIAS;
+  if (flags & ~(WD_NN_BF16 | WD_NN_EVEN)) return WD_ERR_ARG;
+  return guarded([&] { return nn_apply_ex_impl(out, in, weights, gauge, dims, flags); });
 }
 
 int wd_nn_train(float* weights, const double* gauge, double kappa, const int dims[4],

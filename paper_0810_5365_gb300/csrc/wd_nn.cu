@@ -29,14 +29,14 @@ constexpr int NN_PARAMS = nn_layer_offset(3);  // 2304 floats
 
 // persistent grid: as many CTAs as fit on the SMs at once (at most 8 per SM,
 // the 512 TMEM columns / 64 per CTA), never more than there are tiles
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool BIN = false, bool BOUT = false>
 static cudaError_t launch_layer(const NnLayerArgs& A, int ntiles, cudaStream_t st) {
   // residency from the kernel's own register and shared-memory footprint
   // (registers are allocated per warp in units of 256)
   static int per_sm = 0;
   if (per_sm == 0) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, nn_layer_kernel<CIN, COUT>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, nn_layer_kernel<CIN, COUT, BIN, BOUT>);
     if (e != cudaSuccess) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -53,14 +53,14 @@ static cudaError_t launch_layer(const NnLayerArgs& A, int ntiles, cudaStream_t s
     n = n < 1 ? 1 : (n > 8 ? 8 : n);
     // ask for a shared-memory carveout that holds all n CTAs
     const int pct = (int)((100LL * n * ((int)fa.sharedSizeBytes + 1024) + smem_sm - 1) / smem_sm);
-    e = cudaFuncSetAttribute(nn_layer_kernel<CIN, COUT>,
+    e = cudaFuncSetAttribute(nn_layer_kernel<CIN, COUT, BIN, BOUT>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, pct < 100 ? pct : 100);
     if (e != cudaSuccess) return e;
     per_sm = n;
   }
   const int cap = num_sms() * per_sm;
   const int grid = ntiles < cap ? ntiles : cap;
-  nn_layer_kernel<CIN, COUT><<<grid, NN_THREADS, 0, st>>>(A, ntiles);
+  nn_layer_kernel<CIN, COUT, BIN, BOUT><<<grid, NN_THREADS, 0, st>>>(A, ntiles);
   return cudaGetLastError();
 }
 
@@ -429,6 +429,50 @@ static cudaError_t nn_forward(const Geom& g, const void* gauge, const float* w, 
   if ((e = nn_layer(4, 8, g, gauge, in, B.h1, w + nn_layer_offset(0), err, st))) return e;
   if ((e = nn_layer(8, 8, g, gauge, B.h1, B.h2, w + nn_layer_offset(1), err, st))) return e;
   return nn_layer(8, 4, g, gauge, B.h2, out, w + nn_layer_offset(2), err, st);
+}
+
+// One layer of the BF16 inference path: bin/bout select BF16 activations for
+// the input/output (FP32 otherwise), with the parity restriction of nn_layer.
+static cudaError_t nn_layer_bf16(int cin, int cout, bool bin, bool bout, const Geom& g,
+                                 const void* gauge, const void* in, void* out, const float* w,
+                                 int* err, cudaStream_t st, int out_parity, int zero_in) {
+  NnLayerArgs A;
+  A.g = g;
+  A.gauge = gauge;
+  A.in = (const char*)in;
+  A.out = (char*)out;
+  A.in_half = bin ? nn_half_bytes_bf16(g.Vh_pad, cin) : nn_half_bytes(g.Vh_pad, cin);
+  A.out_half = bout ? nn_half_bytes_bf16(g.Vh_pad, cout) : nn_half_bytes(g.Vh_pad, cout);
+  A.w = w;
+  A.err = err;
+  A.p0 = out_parity < 0 ? 0 : out_parity;
+  A.np = out_parity < 0 ? 2 : 1;
+  A.zero_in = zero_in;
+  const int ntiles = A.np * ((g.Vh + NN_TILE - 1) / NN_TILE);
+  if (cin == 4 && cout == 8 && !bin && bout) return launch_layer<4, 8, false, true>(A, ntiles, st);
+  if (cin == 8 && cout == 8 && bin && bout) return launch_layer<8, 8, true, true>(A, ntiles, st);
+  if (cin == 8 && cout == 4 && bin && !bout) return launch_layer<8, 4, true, false>(A, ntiles, st);
+  return cudaErrorInvalidValue;
+}
+
+// N (even: P_e N P_e) with BF16 activations between the layers (input and output stay
+// packed FP32 fields): the link transport runs in packed bf16x2 arithmetic,
+// the channel mixing on the tensor cores with FP32 accumulation.  For the
+// preconditioner inside the flexible CG, whose beta absorbs the extra
+// rounding (about 2^-8 relative per layer).  B.h1 and B.h2 hold 8-channel
+// BF16 fields here.
+static cudaError_t nn_forward_bf16(const Geom& g, const void* gauge, const float* w,
+                                   const void* in, void* out, NnBuffers& B, int* err,
+                                   cudaStream_t st, bool even) {
+  cudaError_t e;
+  if ((e = nn_layer_bf16(4, 8, false, true, g, gauge, in, B.h1, w + nn_layer_offset(0), err, st,
+                         -1, even ? WD_ODD : -1)))
+    return e;
+  if ((e = nn_layer_bf16(8, 8, true, true, g, gauge, B.h1, B.h2, w + nn_layer_offset(1), err, st,
+                         -1, -1)))
+    return e;
+  return nn_layer_bf16(8, 4, true, false, g, gauge, B.h2, out, w + nn_layer_offset(2), err, st,
+                       even ? WD_EVEN : -1, -1);
 }
 
 // The even-even block P_e N P_e: the odd half of `in` is taken as zero and
@@ -825,6 +869,33 @@ int nn_apply_impl(void* out, const void* in, const float* w, const void* gauge, 
   return hflag ? WD_ERR_TIMEOUT : WD_OK;
 }
 
+// out = N(in) (flags & 2: only the even-even block P_e N P_e, the odd half of
+// in taken as zero and the odd half of out untouched), with FP32 (flags & 1
+// == 0) or BF16 activations between the layers
+int nn_apply_ex_impl(void* out, const void* in, const float* w, const void* gauge,
+                     const int dims[4], int flags) {
+  const Geom g = make_geom(dims);
+  cudaStream_t st = state().stream;
+  Alloc al;
+  NnBuffers B;
+  B.bytes8 = 2 * nn_half_bytes(g.Vh_pad, 8);
+  NCK(al.get(&B.h1, B.bytes8));
+  NCK(al.get(&B.h2, B.bytes8));
+  int* flag = nullptr;
+  NCK(device_flag(&flag, st));
+  const bool even = (flags & 2) != 0;
+  if (flags & 1)
+    NCK(nn_forward_bf16(g, gauge, w, in, out, B, flag, st, even));
+  else if (even)
+    NCK(nn_forward_even(g, gauge, w, in, out, B, flag, st));
+  else
+    NCK(nn_forward(g, gauge, w, in, out, B, flag, st));
+  int hflag = 0;
+  NCK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NCK(cudaStreamSynchronize(st));
+  return hflag ? WD_ERR_TIMEOUT : WD_OK;
+}
+
 int nn_layer_impl(void* out, const void* in, const float* w, int cin, int cout, const void* gauge,
                   const int dims[4]) {
   const Geom g = make_geom(dims);
@@ -1177,6 +1248,12 @@ int solve_impl(double* x, const double* b, const double* gauge, double kappa, co
 int solve_impl(double* x, const double* b, const double* gauge, double kappa, const int dims[4],
                const wd_solve_params* prm, wd_solve_info* info);
 
+// the preconditioner of the flexible CG runs the network with BF16
+// activations (1) or FP32 ones (0)
+#ifndef WD_NN_FCG_BF16
+#define WD_NN_FCG_BF16 1
+#endif
+
 int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, const int dims[4],
              const float* wts, const wd_solve_params* prm, wd_solve_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -1292,12 +1369,18 @@ int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, c
       return hop(WD_F32, 12, g32, out, ts, WD_EVEN, dagger, -kappa * kappa, in, 1.0, nullptr, 0.0,
                  nrm);
     };
-    // z = N_e N_e^+ s (or z = s without a network)
+    // z = N_e N_e^+ s (or z = s without a network), BF16 activations
     auto precond = [&](void* zo, const void* si) -> cudaError_t {
       if (!wts) return cudaMemcpyAsync(zo, si, h32, cudaMemcpyDeviceToDevice, st);
+#if WD_NN_FCG_BF16
+      cudaError_t e = nn_forward_bf16(g, g32, (const float*)wa, si, w, B, flag, st, true);
+      if (e != cudaSuccess) return e;
+      return nn_forward_bf16(g, g32, wts, w, zo, B, flag, st, true);
+#else
       cudaError_t e = nn_forward_even(g, g32, (const float*)wa, si, w, B, flag, st);
       if (e != cudaSuccess) return e;
       return nn_forward_even(g, g32, wts, w, zo, B, flag, st);
+#endif
     };
     // bhat = b_e + kappa H_eo b_o (FP64)
     NCK(hop(WD_F64, 18, g64, bhat, (const char*)b64 + h64, WD_EVEN, false, kappa, b64, 1.0,

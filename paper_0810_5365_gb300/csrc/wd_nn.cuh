@@ -225,7 +225,98 @@ __device__ __forceinline__ void nn_transport4(cx<float> (&t)[12], const NnLayerA
   }
 }
 
-template <int CIN, int COUT>
+// ---------------------------------------------------------------------------
+// BF16 activations (inference inside the solver).  A BF16 activation field
+// stores each complex value as one bf16x2 (re, im): C channels x 3 colours
+// per site, 12 C bytes, site-blocked in 16-byte groups (NG = 3C/4 groups of
+// four complex values; the complex index is c*3 + a as in the FP32 layout).
+// BF16 keeps the FP32 exponent range, so the tiny residuals near the end of
+// a solve never underflow.
+// ---------------------------------------------------------------------------
+
+__host__ __device__ constexpr size_t nn_half_bytes_bf16(const int vh_pad, int C) {
+  return ((size_t)vh_pad * C * 12 + 255) / 256 * 256;
+}
+
+// channels c0 .. c0+3 (12 complex: three 16-byte groups) of site cb
+template <int C>
+__device__ __forceinline__ void nn_load4_bf16(__nv_bfloat162 (&v)[12], const char* half, int cb,
+                                              int c0) {
+  constexpr int NG = 3 * C / 4;
+  const int4* p = (const int4*)half;
+  const int g0 = c0 * 3 / 4;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const int4 q = __ldg(p + sbi(cb, g0 + k, NG));
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[4 * k + j] = h[j];
+  }
+}
+
+// T_d of four input channels at this site in packed bf16x2 arithmetic.
+// With vx = i v, u v = u.r v + u.i vx and conj(u) v = u.r v - u.i vx, so each
+// complex multiply-accumulate is two packed FMAs.  The link is loaded and its
+// third row rebuilt in FP32, then rounded to BF16 with the antiperiodic sign
+// folded in.  The input is BF16 (BIN) or the packed FP32 field (rounded on
+// load).
+template <int C, bool BIN>
+__device__ __forceinline__ void nn_transport4_bf16(__nv_bfloat162 (&t)[12], const NnLayerArgs& A,
+                                                   int d, int p, int cb, int n, int x3, int c0) {
+  __nv_bfloat162 v[12];
+  const char* src = A.in + (d == 0 ? p : 1 - p) * A.in_half;
+  if constexpr (BIN) {
+    nn_load4_bf16<C>(v, src, n, c0);
+  } else {
+    cx<float> f[12];
+    nn_load4<C>(f, src, n, c0);
+#pragma unroll
+    for (int k = 0; k < 12; k++) v[k] = __floats2bfloat162_rn(f[k].r, f[k].i);
+  }
+  if (d == 0) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) t[k] = v[k];
+    return;
+  }
+  const int mu = (d - 1) >> 1;
+  const bool fwd = (d & 1) != 0;
+  cx<float> u[9];
+  load_link<WD_F32, 12, float>(u, A.gauge, 2 * mu + (fwd ? p : 1 - p), fwd ? cb : n,
+                               A.g.Vh_pad);
+  const bool flip = mu == 3 && (fwd ? x3 == A.g.L[3] - 1 : x3 == 0);
+  const float sg = flip ? -1.f : 1.f;
+  // ur[k] = (u.r, u.r), ui[k] = (u.i, u.i) of the element the product needs
+  __nv_bfloat162 ur[9], ui[9];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const cx<float> e = fwd ? u[a * 3 + b] : u[b * 3 + a];
+      ur[a * 3 + b] = __float2bfloat162_rn(sg * e.r);
+      ui[a * 3 + b] = __float2bfloat162_rn(sg * e.i);
+    }
+  // (-1, 1) turns the swapped (im, re) into i v; (1, -1) into -i v
+  const __nv_bfloat162 ix = fwd ? __floats2bfloat162_rn(-1.f, 1.f) : __floats2bfloat162_rn(1.f, -1.f);
+  const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    __nv_bfloat162 vx[3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) vx[b] = __hmul2(__lowhigh2highlow(v[c * 3 + b]), ix);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      __nv_bfloat162 w = zero;
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        w = __hfma2(ur[a * 3 + b], v[c * 3 + b], w);
+        w = __hfma2(ui[a * 3 + b], vx[b], w);
+      }
+      t[c * 3 + a] = w;
+    }
+  }
+}
+
+template <int CIN, int COUT, bool BIN = false, bool BOUT = false>
 __global__ void __launch_bounds__(NN_THREADS, WD_NN_MINB) nn_layer_kernel(const NnLayerArgs A, int ntiles) {
   static_assert(CIN == 4 || CIN == 8, "4 or 8 input channels");
   static_assert(COUT == 4 || COUT == 8, "4 or 8 output channels");
@@ -299,20 +390,40 @@ __global__ void __launch_bounds__(NN_THREADS, WD_NN_MINB) nn_layer_kernel(const 
       } else {
         n = hh ? nb[2 * c + 1 < NN_NDIR ? 2 * c + 1 : 0] : nb[2 * c];
       }
-      cx<float> t[12];
-      if (valid && d < NN_NDIR && !(d == 0 ? skip_self : skip_hops)) {
-        nn_transport4<CIN>(t, A, d, p, cb, n, x3, c0);
+      const bool live = valid && d < NN_NDIR && !(d == 0 ? skip_self : skip_hops);
+      if constexpr (BIN || BOUT) {
+        // BF16 inference path: transport in packed bf16x2, stored as is
+        __nv_bfloat162 t[12];
+        if (live) {
+          nn_transport4_bf16<CIN, BIN>(t, A, d, p, cb, n, x3, c0);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 12; k++) t[k] = __floats2bfloat162_rn(0.f, 0.f);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+#pragma unroll
+          for (int i = 0; i < 4; i++) {
+            const int k = 2 * (4 * hh + i);
+            *(__nv_bfloat162*)(sA[buf][a] + kmajor_offset(s, k, 16)) = t[i * 3 + a];
+          }
+        }
       } else {
+        cx<float> t[12];
+        if (live) {
+          nn_transport4<CIN>(t, A, d, p, cb, n, x3, c0);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 12; k++) t[k] = mk<float>(0.f, 0.f);
-      }
+          for (int k = 0; k < 12; k++) t[k] = mk<float>(0.f, 0.f);
+        }
 #pragma unroll
-      for (int a = 0; a < 3; a++) {
+        for (int a = 0; a < 3; a++) {
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-          const int k = 2 * (4 * hh + i);
-          __nv_bfloat162 h = __floats2bfloat162_rn(t[i * 3 + a].r, t[i * 3 + a].i);
-          *(__nv_bfloat162*)(sA[buf][a] + kmajor_offset(s, k, 16)) = h;
+          for (int i = 0; i < 4; i++) {
+            const int k = 2 * (4 * hh + i);
+            __nv_bfloat162 h = __floats2bfloat162_rn(t[i * 3 + a].r, t[i * 3 + a].i);
+            *(__nv_bfloat162*)(sA[buf][a] + kmajor_offset(s, k, 16)) = h;
+          }
         }
       }
       fence_smem_to_async();
@@ -344,7 +455,22 @@ __global__ void __launch_bounds__(NN_THREADS, WD_NN_MINB) nn_layer_kernel(const 
 #pragma unroll
         for (int o = 0; o < COUT; o++) y[o * 3 + a] = mk<float>(v[2 * o], v[2 * o + 1]);
       }
-      if (valid) nn_store<COUT>(A.out + p * A.out_half, cb, g.Vh_pad, y);
+      if (valid) {
+        if constexpr (BOUT) {
+          // COUT x 3 complex values as bf16x2, four per 16-byte group
+          constexpr int NG = 3 * COUT / 4;
+          int4* q = (int4*)(A.out + p * A.out_half);
+#pragma unroll
+          for (int k = 0; k < NG; k++) {
+            __nv_bfloat162 h[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) h[j] = __floats2bfloat162_rn(y[4 * k + j].r, y[4 * k + j].i);
+            q[sbi(cb, k, NG)] = *reinterpret_cast<const int4*>(h);
+          }
+        } else {
+          nn_store<COUT>(A.out + p * A.out_half, cb, g.Vh_pad, y);
+        }
+      }
     }
     // the next tile's first MMA is issued after a __syncthreads that follows
     // these TMEM reads

@@ -44,10 +44,11 @@ EXPORTS = [
     "wd_nn_apply", "wd_nn_train", "wd_solve_fgcr", "wd_nn_layer", "wd_gaussian_spinor",
     "wd_nn_wgrad", "wd_set_autotune", "wd_mrhs_set_lanes", "wd_tune_report",
     "wd_wait_selftest", "wd_set_wait_limit", "wd_async_status", "wd_solve_fcg",
-    "wd_set_batch_mode", "wd_dslash_set_block",
+    "wd_set_batch_mode", "wd_dslash_set_block", "wd_nn_apply_ex",
 ]
 
 WD_NN_PARAMS = 2304
+WD_NN_BF16, WD_NN_EVEN = 1, 2
 
 
 class WdError(RuntimeError):
@@ -138,6 +139,7 @@ def lib():
         "wd_nn_wgrad": (C.c_int, [dp, vp, vp, C.c_int, C.c_int, vp, i4]),
         "wd_gaussian_spinor": (C.c_int, [vp, C.c_ulonglong, C.c_ulonglong, C.c_ulonglong, i4]),
         "wd_nn_apply": (C.c_int, [vp, vp, dp, vp, i4]),
+        "wd_nn_apply_ex": (C.c_int, [vp, vp, dp, vp, i4, C.c_int]),
         "wd_nn_train": (C.c_int, [dp, dp, C.c_double, i4, C.POINTER(wd_nn_train_params),
                                   C.POINTER(wd_nn_train_info)]),
         "wd_solve_fgcr": (C.c_int, [dp, dp, dp, C.c_double, i4, dp, C.c_int,
@@ -400,6 +402,13 @@ def wd_nn_init(weights, kappa):
 
 def wd_nn_apply(out, inp, weights, gauge, dims):
     _ck(lib().wd_nn_apply(_p(out), _p(inp), _p(weights), _p(gauge), _d(dims)), "wd_nn_apply")
+
+
+def wd_nn_apply_ex(out, inp, weights, gauge, dims, flags=0):
+    """out = N(inp); flags: WD_NN_BF16 (BF16 activations), WD_NN_EVEN (the
+    even-even block only)."""
+    _ck(lib().wd_nn_apply_ex(_p(out), _p(inp), _p(weights), _p(gauge), _d(dims), int(flags)),
+        "wd_nn_apply_ex")
 
 
 def wd_nn_train(weights, gauge, kappa, dims, params=None):

@@ -238,3 +238,79 @@ def test_training_with_damped_samples():
     p.smooth = -1
     with pytest.raises(W.WdError):
         W.wd_nn_train(w, U, kappa, dims, p)
+
+
+def _net_case(dims, seed=5):
+    """series weights at kappa 0.13 plus random complex weights of size 0.05:
+    a well-conditioned network that uses every direction and channel"""
+    r = np.random.default_rng(seed)
+    Ws = series_weights(0.13)
+    Ws = [w + 0.05 * (r.normal(size=w.shape) + 1j * r.normal(size=w.shape)) for w in Ws]
+    wdev = torch.from_numpy(nn.join_weights(Ws)).cuda()
+    U = fields.su3_links(dims, workers=1)
+    b = fields.gaussian_spinor(dims, seed=seed + 1)
+    g = pack_gauge(U, dims, W.WD_F32, 12)
+    return Ws, wdev, U, b, g
+
+
+def _apply(flags, wdev, b, g, dims):
+    inp = W.alloc_spinor(dims, W.WD_FULL, W.WD_F32)
+    W.wd_pack_spinor(inp, dev(b), dims, W.WD_FULL, W.WD_F32)
+    out = W.alloc_spinor(dims, W.WD_FULL, W.WD_F32)
+    out.zero_()
+    if flags is None:
+        W.wd_nn_apply(out, inp, wdev, g, dims)
+    else:
+        W.wd_nn_apply_ex(out, inp, wdev, g, dims, flags)
+    return unpack_spinor(out, dims, W.WD_FULL, W.WD_F32)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 8), (6, 4, 4, 6)])
+def test_nn_apply_ex_even_block_and_fp32(dims):
+    """flags 0 is wd_nn_apply bit for bit; the even-even block (WD_NN_EVEN)
+    equals, bit for bit, the full network applied to the input with its odd
+    half set to zero (the directions it skips contribute exact zeros), and
+    matches the FP64 network of the oracle within the bound of the FP32
+    path."""
+    Ws, wdev, U, b, g = _net_case(dims)
+    assert np.array_equal(_apply(0, wdev, b, g, dims), _apply(None, wdev, b, g, dims))
+    par = fields.site_parity(dims)
+    be = b.copy()
+    be[par == 1] = 0
+    even = _apply(W.WD_NN_EVEN, wdev, b, g, dims)
+    full = _apply(0, wdev, be, g, dims)
+    assert np.array_equal(even[par == 0], full[par == 0])
+    want = nn.network(be, U, Ws, dims)[par == 0]
+    assert np.linalg.norm(even[par == 0] - want) / np.linalg.norm(want) < 2e-2
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 8), (6, 4, 4, 6)])
+@pytest.mark.parametrize("even", [False, True])
+def test_nn_apply_ex_bf16_activations(dims, even):
+    """BF16 activations (WD_NN_BF16), alone and with the even-even block,
+    against the FP64 network of the oracle.  Per layer the operands of the
+    link transport (activations, link entries) are rounded to BF16 (8
+    significant bits, 2^-9 relative) and each packed multiply-add rounds to
+    BF16 again; with the BF16 tensor-core operands of the FP32 path this adds
+    a few 2^-9 per layer, so three layers stay below 3e-2 relative (measured
+    about 1e-2)."""
+    Ws, wdev, U, b, g = _net_case(dims, seed=7)
+    par = fields.site_parity(dims)
+    src = b.copy()
+    if even:
+        src[par == 1] = 0
+    got = _apply(W.WD_NN_BF16 | (W.WD_NN_EVEN if even else 0), wdev, b if not even else b, g,
+                 dims)
+    want = nn.network(src, U, Ws, dims)
+    sel = (par == 0) if even else np.ones(len(par), bool)
+    err = np.linalg.norm(got[sel] - want[sel]) / np.linalg.norm(want[sel])
+    assert err < 3e-2, err
+
+
+def test_nn_apply_ex_rejects_unknown_flags():
+    dims = (4, 4, 4, 4)
+    _, wdev, _, b, g = _net_case(dims)
+    inp = W.alloc_spinor(dims, W.WD_FULL, W.WD_F32)
+    out = W.alloc_spinor(dims, W.WD_FULL, W.WD_F32)
+    with pytest.raises(W.WdError):
+        W.wd_nn_apply_ex(out, inp, wdev, g, dims, 4)
