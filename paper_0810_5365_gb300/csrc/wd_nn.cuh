@@ -159,6 +159,9 @@ constexpr int NN_THREADS = 2 * NN_TILE;
 #ifndef WD_NN_MINB
 #define WD_NN_MINB 3   // CTAs per SM the register budget is sized for
 #endif
+#ifndef WD_NN_MINB_BF16
+#define WD_NN_MINB_BF16 4   // the BF16-activation variants: fewer registers, one more CTA
+#endif
 
 // channels c0 .. c0+3 (12 complex, 6 groups) of site cb of a packed half
 template <int C>
@@ -317,7 +320,8 @@ __device__ __forceinline__ void nn_transport4_bf16(__nv_bfloat162 (&t)[12], cons
 }
 
 template <int CIN, int COUT, bool BIN = false, bool BOUT = false>
-__global__ void __launch_bounds__(NN_THREADS, WD_NN_MINB) nn_layer_kernel(const NnLayerArgs A, int ntiles) {
+__global__ void __launch_bounds__(NN_THREADS, (BIN || BOUT) ? WD_NN_MINB_BF16 : WD_NN_MINB)
+    nn_layer_kernel(const NnLayerArgs A, int ntiles) {
   static_assert(CIN == 4 || CIN == 8, "4 or 8 input channels");
   static_assert(COUT == 4 || COUT == 8, "4 or 8 output channels");
   constexpr int DPC = 16 / (2 * CIN);                  // directions per K = 16 chunk
