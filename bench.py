@@ -702,6 +702,8 @@ def profile_case(name):
     ``batch``     one batched FP32-inner solve of 12 point sources on 24^3x48
                   (one launch per step);
     ``batch_persistent``  the same with one persistent launch per iteration;
+    ``nn_bf16``   2 applications of the series network with BF16 activations
+                  on 24^3x48;
     ``fcg``       one learned-preconditioner solve (series weights, flexible CG
                   on the even-odd system) on 16^3x32 at kappa 0.137;
     ``train``     4 Adam steps of 16 samples on 16^3x32 (forward, adjoint and
@@ -808,6 +810,21 @@ def profile_case(name):
         b = torch.zeros_like(a)
         for _ in range(2):
             W.wd_nn_apply(b, a, w, g, dims)
+    elif name == "nn_bf16":
+        # two applications of the series network with BF16 activations on
+        # 24^3x48 (links 127 MB: the working set exceeds L2)
+        dims = (24, 24, 24, 48)
+        Ud = torch.from_numpy(fields.su3_links(dims).view(np.float64).reshape(-1)).cuda()
+        g = W.alloc_gauge(dims, W.WD_F32, 12)
+        W.wd_pack_gauge(g, Ud, dims, W.WD_F32, 12)
+        w = torch.zeros(W.WD_NN_PARAMS, dtype=torch.float32, device="cuda")
+        W.wd_nn_init(w, NN_KAPPA)
+        src = torch.from_numpy(fields.gaussian_spinor(dims).view(np.float64).reshape(-1)).cuda()
+        a = W.alloc_spinor(dims, W.WD_FULL, W.WD_F32)
+        W.wd_pack_spinor(a, src, dims, W.WD_FULL, W.WD_F32)
+        b = torch.zeros_like(a)
+        for _ in range(2):
+            W.wd_nn_apply_ex(b, a, w, g, dims, W.WD_NN_BF16)
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()
@@ -1053,7 +1070,7 @@ def main():
     ap.add_argument("--no-oracle-cg", action="store_true",
                     help="skip the oracle's full FP64 CG timing (about 100 s of host time)")
     ap.add_argument("--profile", choices=["mrhs", "solve_f32", "solve_f16", "batch",
-                                          "batch_persistent", "fcg", "train", "nn",
+                                          "batch_persistent", "fcg", "train", "nn", "nn_bf16",
                                           "staged"],
                     help="run a short fixed workload for an ncu capture and exit")
     args = ap.parse_args()
