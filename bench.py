@@ -26,8 +26,9 @@ The JSON line (rank 0) carries, besides metric/value/unit:
                 and BiCGstab against plain FP64 CG;
   batch         batched multi-right-hand-side solves against the same solves
                 one at a time, and the autotuner's tile shapes;
-  learned_preconditioner  training at kappa = 0.137, and flexible CG with the
-                preconditioner N N^+ (trained network, untrained series, none)
+  learned_preconditioner  training at kappa = 0.137, and even-odd flexible CG
+                with the preconditioner N_e N_e^+ (trained network, untrained
+                series, none)
                 against plain FP64 CG and mixed CG on 16^3x32 and 32^3x64.
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead
 (bounded sample per step).  ``--profile NAME`` runs a short fixed workload for
@@ -621,9 +622,11 @@ def nn_section(W, torch, U_big):
     critical region of these links, where restarted GCR on D stagnates): train
     on 16^3x32 (4096 on-GPU pairs (D x, x), Adam, starting from the hopping
     series 1 + kH + k^2H^2 + k^3H^3), then time-to-1e-10 on 16^3x32 and 32^3x64
-    of flexible CG on D^+ D with the preconditioner N N^+ for the trained
-    network, the untrained series and no network (plain CGNR), against plain
-    FP64 even-odd CG and the mixed-precision even-odd CG on the same GPU.  The
+    of flexible CG on the even-odd normal equations Mhat^+ Mhat x_e =
+    Mhat^+ bhat_e with the preconditioner N_e N_e^+ (N_e the even-even block of
+    the network, run with BF16 activations) for the trained network, the
+    untrained series and no network (plain even-odd CGNR), against plain FP64
+    even-odd CG and the mixed-precision even-odd CG on the same GPU.  The
     network is local and gauge covariant, so the weights trained on the small
     lattice serve the large one.  Every time is one solve after a short
     warm-up solve; the true residual is the solver's FP64 one."""
@@ -687,7 +690,9 @@ def nn_section(W, torch, U_big):
         torch.cuda.empty_cache()
     out["config"] = {"kappa": NN_KAPPA, "network": "3 layers, 12->24->24->12 complex channels, "
                      "nearest-neighbour gauge-covariant, BF16 tensor-core contraction (tcgen05), "
-                     "FP32 accumulation", "solver": "flexible CG on D^+ D, preconditioner N N^+, "
+                     "FP32 accumulation, BF16 activations between layers",
+                     "solver": "flexible CG (Polak-Ribiere beta) on the even-odd normal equations "
+                     "Mhat^+ Mhat, preconditioner N_e N_e^+ (the even-even block of the network), "
                      "FP32 vectors, FP64 reliable updates every 50 iterations; plain CG fallback",
                      "tol": 1e-10}
     return out
