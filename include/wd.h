@@ -271,6 +271,19 @@ int wd_set_autotune(int enable);
  * other sizes. */
 int wd_dslash_set_block(int sites);
 
+/* Launch overlap of consecutive single-field hopping kernels (the paper has
+ * no such component).  enable = 1 (the default): every hopping launch of
+ * wd_dslash, wd_dslash_dag, wd_dslash_ex, wd_mhat and the solvers is a
+ * programmatic dependent launch.  The kernel first lets the next kernel of
+ * the stream be scheduled once all of its own CTAs have started, then waits
+ * until the previous kernel of the stream has completed and its writes are
+ * visible, before it reads or writes any memory.  So consecutive launches
+ * overlap only their scheduling (the next grid's CTAs take the SM slots that
+ * the last wave frees), never their memory accesses, and results are
+ * bit-identical with either setting.  enable = 0: plain stream-ordered
+ * launches.  Returns the previous setting. */
+int wd_set_launch_overlap(int enable);
+
 /* Force one tile shape for every multi-RHS launch (lanes = a shape code:
  * 1, 2, 4, 8, 17, 18 or 20; FP64 and FP16 launches run 16 + w as w), or go
  * back to the tuned/default shapes (lanes = 0).  WD_ERR_ARG otherwise. */

@@ -300,6 +300,8 @@ int wd_mrhs_set_lanes(int lanes) { return mrhs_set_lanes(lanes); }
 
 int wd_dslash_set_block(int sites) { return dslash_set_block(sites); }
 
+int wd_set_launch_overlap(int enable) { return set_launch_overlap(enable); }
+
 int wd_tune_report(char* buf, size_t len) {
   return guarded([&] { return tune_report(buf, len); });
 }

@@ -249,6 +249,18 @@ int set_autotune(int enable) {
 int autotune_enabled() { return g_autotune; }
 
 namespace {
+int g_launch_overlap = 1;  // hopping kernels as programmatic dependent launches
+}  // namespace
+
+int launch_overlap() { return g_launch_overlap; }
+
+int set_launch_overlap(int enable) {
+  const int prev = g_launch_overlap;
+  g_launch_overlap = enable ? 1 : 0;
+  return prev;
+}
+
+namespace {
 int g_dslash_block = 0;  // forced CTA size of the single-field hopping kernel (0: tuned)
 std::vector<std::string>& dslash_lines() {
   static std::vector<std::string> v;

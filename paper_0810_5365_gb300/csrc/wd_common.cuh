@@ -197,6 +197,17 @@ inline size_t spinor_half_bytes(const Geom& g, int prec) {
   return round_up((size_t)g.Vh_pad * per, 256);
 }
 
+// Programmatic dependent launch.  launch_dependents lets the next kernel of
+// the stream be scheduled once every CTA of this grid has started (its CTAs
+// then fill the SM slots that this grid's last wave frees); wait blocks until
+// the previous kernel of the stream has completed and its writes are
+// visible.  A kernel calls this before its first global memory access, so it
+// never reads or writes anything its predecessor may still touch.  Both are
+// no-ops for a launch without the programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.launch_dependents;\n\tgriddepcontrol.wait;\n" ::: "memory");
+}
+
 // A load of an input field.  COH = false: the read-only data path (the field
 // is not written while the kernel runs).  COH = true: an ordinary coherent
 // load, for a kernel that reads fields written earlier in the same launch by

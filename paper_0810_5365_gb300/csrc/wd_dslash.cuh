@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
     dslash_kernel(const DslashArgs a) {
   constexpr int NRED = RED == RED_NONE ? 1 : RED == RED_NORM ? 1 : RED == RED_NORM_DOTX ? 3 : 2;
   using R = typename std::conditional<P == WD_F64, double, float>::type;
+  pdl_begin();
   const Geom& g = a.g;
   const int cb = blockIdx.x * BS + threadIdx.x;
   double red[NRED];
@@ -537,18 +538,27 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
   }
 }
 
+// Launch a hopping kernel (see launch_pdl)
+inline cudaError_t launch_hopping(void (*k)(const DslashArgs), dim3 grid, dim3 block,
+                                  const DslashArgs& a, cudaStream_t st) {
+  return launch_pdl(k, grid, block, st, a);
+}
+
 // the non-reducing kernel with BS sites per CTA (64, 128 or 256)
 template <int P, int RC, bool DG, bool TG>
 cudaError_t launch_dslash_plain_bs(const DslashArgs& a, int bs, cudaStream_t st) {
   const unsigned n = (unsigned)a.g.Vh;
   switch (bs) {
-    case 64: dslash_kernel<P, RC, DG, RED_NONE, TG, 64><<<(n + 63) / 64, 64, 0, st>>>(a); break;
-    case 256: dslash_kernel<P, RC, DG, RED_NONE, TG, 256><<<(n + 255) / 256, 256, 0, st>>>(a); break;
+    case 64:
+      return launch_hopping(dslash_kernel<P, RC, DG, RED_NONE, TG, 64>, dim3((n + 63) / 64),
+                            dim3(64), a, st);
+    case 256:
+      return launch_hopping(dslash_kernel<P, RC, DG, RED_NONE, TG, 256>, dim3((n + 255) / 256),
+                            dim3(256), a, st);
     default:
-      dslash_kernel<P, RC, DG, RED_NONE, TG, DSLASH_BS>
-          <<<(n + DSLASH_BS - 1) / DSLASH_BS, DSLASH_BS, 0, st>>>(a);
+      return launch_hopping(dslash_kernel<P, RC, DG, RED_NONE, TG, DSLASH_BS>,
+                            dim3((n + DSLASH_BS - 1) / DSLASH_BS), dim3(DSLASH_BS), a, st);
   }
-  return cudaGetLastError();
 }
 
 template <int P, int RC, bool DG, bool TG>
@@ -559,25 +569,23 @@ cudaError_t launch_dslash_red_tg(const DslashArgs& a, dim3 grid, dim3 block, int
     case RED_NONE:
       return launch_dslash_plain_bs<P, RC, DG, TG>(a, bs, st);
     case RED_NORM:
-      dslash_kernel<P, RC, DG, RED_NORM, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
-      break;
+      return launch_hopping(dslash_kernel<P, RC, DG, RED_NORM, TG, DSLASH_BS>, grid, block, a, st);
     case RED_NORM_DOTX:
     case RED_DOTZ:
       // the dot-product epilogues serve BiCGstab, which never applies H^+
       if constexpr (!DG) {
         if (mode == RED_NORM_DOTX) {
           if (!a.x) return cudaErrorInvalidValue;
-          dslash_kernel<P, RC, DG, RED_NORM_DOTX, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
-        } else {
-          if (!a.z) return cudaErrorInvalidValue;
-          dslash_kernel<P, RC, DG, RED_DOTZ, TG, DSLASH_BS><<<grid, block, 0, st>>>(a);
+          return launch_hopping(dslash_kernel<P, RC, DG, RED_NORM_DOTX, TG, DSLASH_BS>, grid,
+                                block, a, st);
         }
-        break;
+        if (!a.z) return cudaErrorInvalidValue;
+        return launch_hopping(dslash_kernel<P, RC, DG, RED_DOTZ, TG, DSLASH_BS>, grid, block, a,
+                              st);
       }
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <int P, int RC, bool DG>

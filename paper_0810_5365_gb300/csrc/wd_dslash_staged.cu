@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
     dslash_f16_staged_kernel(const DslashArgs a, long spin_limit) {
   __shared__ StageWarp stage[STG_WARPS];
   __shared__ uint64_t bar[STG_WARPS];
+  pdl_begin();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const Geom& g = a.g;
   const int blk = blockIdx.x * STG_WARPS + warp;
@@ -230,11 +231,8 @@ cudaError_t launch_dslash_f16_staged(const DslashArgs& a, int recon, bool dagger
     cudaGetLastError();
     g_carveout_set[dev] = true;
   }
-  if (dagger)
-    dslash_f16_staged_kernel<true><<<grid, block, 0, st>>>(a, spin_limit);
-  else
-    dslash_f16_staged_kernel<false><<<grid, block, 0, st>>>(a, spin_limit);
-  return cudaGetLastError();
+  if (dagger) return launch_pdl(dslash_f16_staged_kernel<true>, grid, block, st, a, spin_limit);
+  return launch_pdl(dslash_f16_staged_kernel<false>, grid, block, st, a, spin_limit);
 }
 
 // Read and clear the current device's fault flag after the work queued on

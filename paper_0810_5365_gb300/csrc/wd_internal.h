@@ -66,6 +66,28 @@ struct DslashArgs {
 int autotune_enabled();
 int dslash_forced_block();
 void dslash_tune_record(const char* line);
+// 1: hopping kernels are launched as programmatic dependent launches
+int launch_overlap();
+int set_launch_overlap(int enable);
+
+// Launch kernel k (which starts with pdl_begin) with launch overlap on
+// (wd_set_launch_overlap) as a programmatic dependent launch, else as a
+// plain stream-ordered launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = launch_overlap() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 enum { RED_NONE = 0, RED_NORM = 1, RED_NORM_DOTX = 2, RED_DOTZ = 3 };
 

@@ -44,7 +44,7 @@ EXPORTS = [
     "wd_nn_apply", "wd_nn_train", "wd_solve_fgcr", "wd_nn_layer", "wd_gaussian_spinor",
     "wd_nn_wgrad", "wd_set_autotune", "wd_mrhs_set_lanes", "wd_tune_report",
     "wd_wait_selftest", "wd_set_wait_limit", "wd_async_status", "wd_solve_fcg",
-    "wd_set_batch_mode", "wd_dslash_set_block", "wd_nn_apply_ex",
+    "wd_set_batch_mode", "wd_dslash_set_block", "wd_nn_apply_ex", "wd_set_launch_overlap",
 ]
 
 WD_NN_PARAMS = 2304
@@ -152,6 +152,7 @@ def lib():
         "wd_set_autotune": (C.c_int, [C.c_int]),
         "wd_set_batch_mode": (C.c_int, [C.c_int]),
         "wd_dslash_set_block": (C.c_int, [C.c_int]),
+        "wd_set_launch_overlap": (C.c_int, [C.c_int]),
         "wd_wait_selftest": (C.c_int, [C.c_longlong]),
         "wd_set_wait_limit": (C.c_int, [C.c_longlong]),
         "wd_async_status": (C.c_int, []),
@@ -324,6 +325,13 @@ def wd_dslash_set_block(sites):
     """Force the CTA size (64, 128, 256) of the non-reducing single-field
     hopping launches, or return to the tuned sizes (0)."""
     _ck(lib().wd_dslash_set_block(int(sites)), "wd_dslash_set_block")
+
+
+def wd_set_launch_overlap(enable):
+    """Launch the single-field hopping kernels as programmatic dependent
+    launches (1, the default) or as plain stream-ordered launches (0); results
+    are identical.  Returns the previous setting."""
+    return int(lib().wd_set_launch_overlap(int(enable)))
 
 
 def wd_mrhs_set_lanes(lanes):

@@ -259,3 +259,68 @@ def test_cta_size_rejects_other_values():
     for bad in (32, 96, 512):
         with pytest.raises(W.WdError):
             W.wd_dslash_set_block(bad)
+
+
+@pytest.mark.parametrize("prec,recon", [(W.WD_F64, 18), (W.WD_F32, 12), (W.WD_F16, 12)])
+def test_launch_overlap_chain_is_bit_identical(prec, recon):
+    """A chain of dependent hopping launches (each reads the field the
+    previous one wrote, alternating parity, plain and with the fused norm) as
+    programmatic dependent launches gives exactly the fields and norms of
+    plain stream-ordered launches; and the two-hop result matches the
+    oracle."""
+    dims = (8, 6, 4, 12)
+    U, psi = fields.su3_links(dims, workers=1), fields.gaussian_spinor(dims)
+    g = pack_gauge(U, dims, prec, recon)
+    src = fields.to_half(psi, dims, 1)
+    res = {}
+    prev = W.wd_set_launch_overlap(1)
+    try:
+        for on in (1, 0):
+            W.wd_set_launch_overlap(on)
+            a = pack_spinor(src, dims, 1, prec)
+            b = W.alloc_spinor(dims, 0, prec)
+            nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+            for _ in range(5):   # a -> b (even), b -> a (odd), ...
+                W.wd_dslash_ex(b, a, g, 0, 0, -0.12, None, 0.0, None, 0.0, None, dims, prec,
+                               recon)
+                W.wd_dslash_ex(a, b, g, 1, 0, -0.12, None, 0.0, None, 0.0, nrm, dims, prec,
+                               recon)
+            torch.cuda.synchronize()
+            res[on] = (unpack_spinor(a, dims, 1, prec), unpack_spinor(b, dims, 0, prec),
+                       float(nrm.item()))
+    finally:
+        W.wd_set_launch_overlap(prev)
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[0][2] == res[1][2]
+    # one more pair from the chain's last odd field, checked against the oracle
+    odd = res[1][0]
+    want_b = -0.12 * oracle.hop_block(0, odd, U, dims)
+    a = pack_spinor(odd, dims, 1, prec)
+    b = W.alloc_spinor(dims, 0, prec)
+    W.wd_dslash_ex(b, a, g, 0, 0, -0.12, None, 0.0, None, 0.0, None, dims, prec, recon)
+    torch.cuda.synchronize()
+    assert rel_l2(unpack_spinor(b, dims, 0, prec), want_b) <= PREC_TOL[prec]
+
+
+def test_launch_overlap_solve_is_bit_identical():
+    """The mixed-precision solve (graphs of hopping and BLAS launches) gives
+    the same iterate, iteration count and residual with and without launch
+    overlap, and the oracle confirms the residual."""
+    dims, kappa = (8, 8, 8, 8), 0.137
+    U, b = fields.su3_links(dims, workers=1), fields.gaussian_spinor(dims, seed=7)
+    out = {}
+    prev = W.wd_set_launch_overlap(1)
+    try:
+        for on in (1, 0):
+            W.wd_set_launch_overlap(on)
+            x = np.zeros_like(b)
+            q = W.wd_solve_params_default()
+            q.inner_prec = W.WD_F16
+            info = W.wd_solve_ex(x, b, U, kappa, dims, q)
+            out[on] = (x, info["iters"], info["true_residual"])
+    finally:
+        W.wd_set_launch_overlap(prev)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
+    r = b - oracle.apply_D(out[1][0], U, dims, kappa)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10
