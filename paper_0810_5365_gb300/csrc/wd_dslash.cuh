@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <type_traits>
 
@@ -260,8 +261,7 @@ __device__ __forceinline__ void hop(cx<R> (&acc)[12], const void* __restrict__ i
 // ---------------------------------------------------------------------------
 
 struct RawF16 {
-  int4 s[3];   // 24 halves of the neighbour spinor
-  float sc;    // its site scale
+  int4 s[3];   // 24 halves of the neighbour spinor (its site scale is loaded apart)
   int4 la;     // link U00 U01 U02 U10
   int2 lb;     // link U11 U12
 };
@@ -274,7 +274,6 @@ __device__ __forceinline__ RawF16 fetch_f16(const void* __restrict__ in,
   const int4* p = (const int4*)in;
 #pragma unroll
   for (int k = 0; k < 3; k++) r.s[k] = ldin<COH>(p + sbi(nb, k, 3));
-  r.sc = ldin<COH>((const float*)((const char*)in + (size_t)VP * 48) + nb);
   if (!unit) {
     r.la = __ldg((const int4*)gauge + (size_t)region * VP + lcb);
     r.lb = __ldg((const int2*)((const char*)gauge + (size_t)8 * VP * 16) + (size_t)region * VP + lcb);
@@ -293,16 +292,41 @@ __device__ __forceinline__ __half2 h2_cmac(__half2 u, __half2 h, __half2 hx, __h
   return __hfma2(__high2half2(u), hx, w);
 }
 
+// Exact sign and lane moves on a half2 done on the integer pipe (GB300 issues
+// packed half FMAs at half the rate of FP32 ones, so the half pipe is kept
+// for the arithmetic): h2_sgn flips the sign of the lanes in MASK
+// (0x0000ffff: re, 0xffff0000: im); h2_i is i h = (-h.i, h.r), h2_mi is
+// -i h = (h.i, -h.r).
+__device__ __forceinline__ unsigned h2_bits(__half2 h) {
+  unsigned u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+__device__ __forceinline__ __half2 h2_from_bits(unsigned u) {
+  __half2 h;
+  memcpy(&h, &u, 4);
+  return h;
+}
+template <unsigned MASK>
+__device__ __forceinline__ __half2 h2_sgn(__half2 h) {
+  return h2_from_bits(h2_bits(h) ^ (MASK & 0x80008000u));
+}
+__device__ __forceinline__ __half2 h2_i(__half2 h) {
+  return h2_from_bits(__byte_perm(h2_bits(h), 0, 0x1032) ^ 0x00008000u);
+}
+__device__ __forceinline__ __half2 h2_mi(__half2 h) {
+  return h2_from_bits(__byte_perm(h2_bits(h), 0, 0x1032) ^ 0x80000000u);
+}
+
 // conj(a b - c d) on half2 (the SU(3) third row from the first two)
 __device__ __forceinline__ __half2 h2_conj_cross(__half2 a, __half2 b, __half2 c, __half2 d) {
-  const __half2 pm = __floats2half2_rn(-1.f, 1.f);
-  const __half2 bx = __hmul2(__lowhigh2highlow(b), pm);  // i b
-  const __half2 dx = __hmul2(__lowhigh2highlow(d), pm);  // i d
+  const __half2 bx = h2_i(b);
+  const __half2 dx = h2_i(d);
   __half2 x = __hmul2(__low2half2(a), b);
   x = __hfma2(__high2half2(a), bx, x);
   x = __hfma2(__hneg2(__low2half2(c)), d, x);
   x = __hfma2(__hneg2(__high2half2(c)), dx, x);
-  return __hmul2(x, __floats2half2_rn(1.f, -1.f));
+  return h2_sgn<0xffff0000u>(x);
 }
 
 // The transported half spinor t = U h (FWD) or U^+ h in half2 arithmetic:
@@ -322,10 +346,9 @@ __device__ __forceinline__ void transport_h2(const RawF16& r, const __half2 (&h)
   u[6] = h2_conj_cross(u[1], u[5], u[2], u[4]);
   u[7] = h2_conj_cross(u[2], u[3], u[0], u[5]);
   u[8] = h2_conj_cross(u[0], u[4], u[1], u[3]);
-  const __half2 sx = FWD ? __floats2half2_rn(-1.f, 1.f) : __floats2half2_rn(1.f, -1.f);
   __half2 hx[6];
 #pragma unroll
-  for (int k = 0; k < 6; k++) hx[k] = __hmul2(__lowhigh2highlow(h[k]), sx);
+  for (int k = 0; k < 6; k++) hx[k] = FWD ? h2_i(h[k]) : h2_mi(h[k]);
 #pragma unroll
   for (int hs = 0; hs < 2; hs++) {
 #pragma unroll
@@ -341,8 +364,17 @@ __device__ __forceinline__ void transport_h2(const RawF16& r, const __half2 (&h)
   }
 }
 
+// One FP16 hop: project, transport, expand and accumulate, all in packed
+// half2.  rs = (rel, rel), rel = s / smax the neighbour's site scale relative
+// to the largest scale of the site's eight neighbours (negated for a hop
+// across the antiperiodic time boundary), so every accumulated term is at
+// most the size
+// of a transported component (below 4) and the eight-hop sums stay below 32:
+// no overflow, and a neighbour too small to register in half precision is
+// also below the rounding of the result.  The caller applies smax (and the
+// kernel's factor a) once, in FP32, after the last hop.
 template <int MU, int S, bool FWD>
-__device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& r, bool flip,
+__device__ __forceinline__ void compute_f16(__half2 (&acc)[12], const RawF16& r, __half2 rs,
                                             bool unit = false) {
   __half2 v[12];
 #pragma unroll
@@ -353,72 +385,146 @@ __device__ __forceinline__ void compute_f16(cx<float> (&acc)[12], const RawF16& 
   }
   __half2 hh[6];
   project_h2<MU, S>(v, hh);
-  __half2 t2[6];
+  __half2 t[6];
   if (MU == 3 && unit) {
 #pragma unroll
-    for (int k = 0; k < 6; k++) t2[k] = hh[k];
+    for (int k = 0; k < 6; k++) t[k] = hh[k];
   } else {
-    transport_h2<FWD>(r, hh, t2);
+    transport_h2<FWD>(r, hh, t);
   }
-  cx<float> t[6];
+  // the lower two spins are +-S t or +-S i t of the upper ones (the same
+  // expansion as expand_add): with i t = swap(t) * (-1, 1), -S i t = swap(t)
+  // * (S, -S)
+  const __half2 rn = h2_sgn<0xffffffffu>(rs);
+  const __half2 ri = h2_sgn<(S > 0 ? 0xffff0000u : 0x0000ffffu)>(rs);  // (S r, -S r)
 #pragma unroll
-  for (int k = 0; k < 6; k++) {
-    const float2 f = __half22float2(t2[k]);
-    t[k] = mk<float>(f.x, f.y);
+  for (int c = 0; c < 3; c++) {
+    acc[c] = __hfma2(rs, t[c], acc[c]);
+    acc[3 + c] = __hfma2(rs, t[3 + c], acc[3 + c]);
+    if constexpr (MU == 0) {          // lower = (-S i t1, -S i t0)
+      acc[6 + c] = __hfma2(ri, __lowhigh2highlow(t[3 + c]), acc[6 + c]);
+      acc[9 + c] = __hfma2(ri, __lowhigh2highlow(t[c]), acc[9 + c]);
+    } else if constexpr (MU == 1) {   // lower = (-S t1, S t0)
+      acc[6 + c] = __hfma2(S > 0 ? rn : rs, t[3 + c], acc[6 + c]);
+      acc[9 + c] = __hfma2(S > 0 ? rs : rn, t[c], acc[9 + c]);
+    } else if constexpr (MU == 2) {   // lower = (-S i t0, S i t1)
+      acc[6 + c] = __hfma2(ri, __lowhigh2highlow(t[c]), acc[6 + c]);
+      acc[9 + c] = __hfma2(h2_sgn<0xffffffffu>(ri), __lowhigh2highlow(t[3 + c]), acc[9 + c]);
+    } else {                          // lower = (-S t0, -S t1)
+      acc[6 + c] = __hfma2(S > 0 ? rn : rs, t[c], acc[6 + c]);
+      acc[9 + c] = __hfma2(S > 0 ? rn : rs, t[3 + c], acc[9 + c]);
+    }
   }
-  const float sc = (MU == 3 && flip) ? -r.sc : r.sc;
-  expand_add<MU, S, false>(acc, t, sc);
+}
+
+// The largest of the eight neighbour scales s (hop order f0 b0 f1 b1 f2 b2
+// f3 b3), and the scales relative to it rounded to half, two hops per
+// register (rel[k] = (s[2k], s[2k+1]) / smax, the time hops' signs folded
+// in).  An all-zero neighbourhood gives smax = 0 and rel = 0.
+__device__ __forceinline__ float f16_rel(const float (&s)[8], bool fflip, bool bflip,
+                                         __half2 (&rel)[4]) {
+  const float m = fmaxf(fmaxf(fmaxf(s[0], s[1]), fmaxf(s[2], s[3])),
+                        fmaxf(fmaxf(s[4], s[5]), fmaxf(s[6], s[7])));
+  const float inv = m > 0.f ? __frcp_rn(m) : 0.f;
+  rel[0] = __floats2half2_rn(s[0] * inv, s[1] * inv);
+  rel[1] = __floats2half2_rn(s[2] * inv, s[3] * inv);
+  rel[2] = __floats2half2_rn(s[4] * inv, s[5] * inv);
+  rel[3] = __floats2half2_rn((fflip ? -s[6] : s[6]) * inv, (bflip ? -s[7] : s[7]) * inv);
+  return m;
+}
+
+// acc = post * smax * (half2 sums), in FP32
+__device__ __forceinline__ void f16_widen(cx<float> (&acc)[12], const __half2 (&ah)[12],
+                                          float k) {
+#pragma unroll
+  for (int j = 0; j < 12; j++) {
+    const float2 f = __half22float2(ah[j]);
+    acc[j] = mk<float>(k * f.x, k * f.y);
+  }
 }
 
 #ifndef WD_F16_PREFETCH
 #define WD_F16_PREFETCH 2
 #endif
 
-// The eight hops of one FP16 site: the loads of the next hops are issued
-// before the current one is computed (WD_F16_PREFETCH hops in flight).
-// funit/bunit: the forward/backward time link is the identity (temporal gauge).
+// The eight hops of one FP16 site: the eight neighbour scales are loaded
+// first, then the loads of the next hops are issued before the current one
+// is computed (WD_F16_PREFETCH hops in flight).  The hops are accumulated in
+// half2 relative to the largest neighbour scale (compute_f16); on return
+// acc = post * H in at this site, in FP32.  funit/bunit: the forward/backward
+// time link is the identity (temporal gauge).
 template <int SF, int SB_, bool COH = false>
 __device__ __forceinline__ void hops_f16(cx<float> (&acc)[12], const void* __restrict__ in,
                                          const void* __restrict__ ga, int p, int cb, int f0,
                                          int b0, int f1, int b1, int f2, int b2, int f3, int b3,
-                                         bool fflip, bool bflip, bool funit, bool bunit, int VP) {
+                                         bool fflip, bool bflip, bool funit, bool bunit, int VP,
+                                         float post) {
   const int q = 1 - p;
+  const float* scl = (const float*)((const char*)in + (size_t)VP * 48);
+  float sc[8] = {ldin<COH>(scl + f0), ldin<COH>(scl + b0), ldin<COH>(scl + f1),
+                 ldin<COH>(scl + b1), ldin<COH>(scl + f2), ldin<COH>(scl + b2),
+                 ldin<COH>(scl + f3), ldin<COH>(scl + b3)};
+  __half2 ah[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) ah[k] = __float2half2_rn(0.f);
 #define WD_F(nb, reg, lcb) fetch_f16<COH>(in, ga, nb, reg, lcb, VP)
-#if WD_F16_PREFETCH >= 2
+#if WD_F16_PREFETCH >= 3
+  RawF16 r0 = WD_F(f0, 0 + p, cb), r1 = WD_F(b0, 0 + q, b0);
+  RawF16 r2 = WD_F(f1, 2 + p, cb), r3 = WD_F(b1, 2 + q, b1);
+  __half2 rel[4];
+  const float smax = f16_rel(sc, fflip, bflip, rel);
+  compute_f16<0, SF, true>(ah, r0, __low2half2(rel[0]));
+  r0 = WD_F(f2, 4 + p, cb);
+  compute_f16<0, SB_, false>(ah, r1, __high2half2(rel[0]));
+  r1 = WD_F(b2, 4 + q, b2);
+  compute_f16<1, SF, true>(ah, r2, __low2half2(rel[1]));
+  r2 = fetch_f16<COH>(in, ga, f3, 6 + p, cb, VP, funit);
+  compute_f16<1, SB_, false>(ah, r3, __high2half2(rel[1]));
+  r3 = fetch_f16<COH>(in, ga, b3, 6 + q, b3, VP, bunit);
+  compute_f16<2, SF, true>(ah, r0, __low2half2(rel[2]));
+  compute_f16<2, SB_, false>(ah, r1, __high2half2(rel[2]));
+  compute_f16<3, SF, true>(ah, r2, __low2half2(rel[3]), funit);
+  compute_f16<3, SB_, false>(ah, r3, __high2half2(rel[3]), bunit);
+#elif WD_F16_PREFETCH >= 2
   RawF16 r0 = WD_F(f0, 0 + p, cb), r1 = WD_F(b0, 0 + q, b0);
   RawF16 r2 = WD_F(f1, 2 + p, cb);
-  compute_f16<0, SF, true>(acc, r0, false);
+  __half2 rel[4];
+  const float smax = f16_rel(sc, fflip, bflip, rel);
+  compute_f16<0, SF, true>(ah, r0, __low2half2(rel[0]));
   RawF16 r3 = WD_F(b1, 2 + q, b1);
-  compute_f16<0, SB_, false>(acc, r1, false);
+  compute_f16<0, SB_, false>(ah, r1, __high2half2(rel[0]));
   r0 = WD_F(f2, 4 + p, cb);
-  compute_f16<1, SF, true>(acc, r2, false);
+  compute_f16<1, SF, true>(ah, r2, __low2half2(rel[1]));
   r1 = WD_F(b2, 4 + q, b2);
-  compute_f16<1, SB_, false>(acc, r3, false);
+  compute_f16<1, SB_, false>(ah, r3, __high2half2(rel[1]));
   r2 = fetch_f16<COH>(in, ga, f3, 6 + p, cb, VP, funit);
-  compute_f16<2, SF, true>(acc, r0, false);
+  compute_f16<2, SF, true>(ah, r0, __low2half2(rel[2]));
   r3 = fetch_f16<COH>(in, ga, b3, 6 + q, b3, VP, bunit);
-  compute_f16<2, SB_, false>(acc, r1, false);
-  compute_f16<3, SF, true>(acc, r2, fflip, funit);
-  compute_f16<3, SB_, false>(acc, r3, bflip, bunit);
+  compute_f16<2, SB_, false>(ah, r1, __high2half2(rel[2]));
+  compute_f16<3, SF, true>(ah, r2, __low2half2(rel[3]), funit);
+  compute_f16<3, SB_, false>(ah, r3, __high2half2(rel[3]), bunit);
 #else
   RawF16 r0 = WD_F(f0, 0 + p, cb);
   RawF16 r1 = WD_F(b0, 0 + q, b0);
-  compute_f16<0, SF, true>(acc, r0, false);
+  __half2 rel[4];
+  const float smax = f16_rel(sc, fflip, bflip, rel);
+  compute_f16<0, SF, true>(ah, r0, __low2half2(rel[0]));
   r0 = WD_F(f1, 2 + p, cb);
-  compute_f16<0, SB_, false>(acc, r1, false);
+  compute_f16<0, SB_, false>(ah, r1, __high2half2(rel[0]));
   r1 = WD_F(b1, 2 + q, b1);
-  compute_f16<1, SF, true>(acc, r0, false);
+  compute_f16<1, SF, true>(ah, r0, __low2half2(rel[1]));
   r0 = WD_F(f2, 4 + p, cb);
-  compute_f16<1, SB_, false>(acc, r1, false);
+  compute_f16<1, SB_, false>(ah, r1, __high2half2(rel[1]));
   r1 = WD_F(b2, 4 + q, b2);
-  compute_f16<2, SF, true>(acc, r0, false);
+  compute_f16<2, SF, true>(ah, r0, __low2half2(rel[2]));
   r0 = fetch_f16<COH>(in, ga, f3, 6 + p, cb, VP, funit);
-  compute_f16<2, SB_, false>(acc, r1, false);
+  compute_f16<2, SB_, false>(ah, r1, __high2half2(rel[2]));
   r1 = fetch_f16<COH>(in, ga, b3, 6 + q, b3, VP, bunit);
-  compute_f16<3, SF, true>(acc, r0, fflip, funit);
-  compute_f16<3, SB_, false>(acc, r1, bflip, bunit);
+  compute_f16<3, SF, true>(ah, r0, __low2half2(rel[3]), funit);
+  compute_f16<3, SB_, false>(ah, r1, __high2half2(rel[3]), bunit);
 #endif
 #undef WD_F
+  f16_widen(acc, ah, post * smax);
 }
 
 // TG: links in temporal gauge (compile-time, so that the ordinary kernel keeps
@@ -475,7 +581,7 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
 
     if constexpr (P == WD_F16) {
       hops_f16<SF, SB_>(acc, a.in, a.gauge, p, cb, f0, b0, f1, b1, f2, b2, f3, b3, fflip, bflip,
-                        funit, bunit, VP);
+                        funit, bunit, VP, (float)a.a);
     } else {
       hop<P, RC, 0, SF, true>(acc, a.in, a.gauge, f0, 0 + p, cb, false, VP);
       hop<P, RC, 0, SB_, false>(acc, a.in, a.gauge, b0, 0 + q, b0, false, VP);
@@ -487,9 +593,11 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
       hop<P, RC, 3, SB_, false>(acc, a.in, a.gauge, b3, 6 + q, b3, bflip, VP, bunit);
     }
 
-    const R ca = (R)a.a;
+    if constexpr (P != WD_F16) {  // (the FP16 hops apply a themselves)
+      const R ca = (R)a.a;
 #pragma unroll
-    for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
+      for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
+    }
     if (a.x) {
       cx<R> v[12];
       load_spinor_rw<P, R>(v, a.x, cb, VP);

@@ -6,13 +6,14 @@
 // its +z, -z, +t and -t neighbours in four whole 32-site blocks of the other
 // parity's field: the same lane of the block one z- or t-stride away (with
 // the periodic wrap applied to the block index).  In the FP16 format such a
-// block is one contiguous 1536-byte span (three planes of 32 x 16 bytes) plus
-// a 128-byte span of site scales, so each warp stages its four far
-// neighbour blocks with eight cp.async.bulk copies issued by one lane and
-// completed on the warp's own mbarrier.  The copies run while the warp
-// computes its x and y hops from global memory (near neighbours, mostly L1
-// hits); the z and t hops then read their spinors from shared memory.  Links
-// are used once per application and are loaded directly.
+// block is one contiguous 1536-byte span (three planes of 32 x 16 bytes), so
+// each warp stages its four far neighbour blocks with four cp.async.bulk
+// copies issued by one lane and completed on the warp's own mbarrier.  The
+// copies run while the warp computes its x and y hops from global memory
+// (near neighbours, mostly L1 hits); the z and t hops then read their
+// spinors from shared memory.  The eight neighbour scales are needed before
+// the first hop (the hops accumulate relative to the largest) and are loaded
+// directly, as are the links, which are used once per application.
 //
 // Each warp's mbarrier is used once (phase 0).  The wait is bounded: if it
 // gives up after `spin_limit` polls, the kernel raises the device's fault
@@ -46,7 +47,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 constexpr int STG_WARPS = 4;           // CTA = 4 site blocks = 128 sites
 constexpr uint32_t STG_SPAN = 1536;    // bytes of one FP16 site block (3 x 32 x 16)
-constexpr uint32_t STG_SCALE = 128;    // bytes of its 32 site scales
 // polls of the drain wait after a timeout: about 7 s at some 100 ns per poll,
 // far beyond any copy of 6.5 KB
 constexpr long STG_DRAIN_LIMIT = 1L << 26;
@@ -58,7 +58,6 @@ __device__ int g_stage_fault;
 
 struct __align__(16) StageWarp {
   int4 sp[4][3][32];  // [z+, z-, t+, t-][plane][lane]
-  float sc[4][32];
 };
 
 // the link of a hop whose spinor comes from shared memory
@@ -95,15 +94,12 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
     mbar_init(&bar[warp], 1);
     mbar_fence_init();
     fence_smem_to_async();
-    mbar_arrive_expect_tx(&bar[warp], 4 * (STG_SPAN + STG_SCALE));
+    mbar_arrive_expect_tx(&bar[warp], 4 * STG_SPAN);
     const char* sp = (const char*)a.in;
-    const char* sc = sp + (size_t)VP * 48;
     const int nb[4] = {bzf, bzb, btf, btb};
 #pragma unroll
-    for (int d = 0; d < 4; d++) {
+    for (int d = 0; d < 4; d++)
       bulk_g2s(&s.sp[d][0][0], sp + (size_t)nb[d] * STG_SPAN, STG_SPAN, &bar[warp]);
-      bulk_g2s(&s.sc[d][0], sc + (size_t)nb[d] * STG_SCALE, STG_SCALE, &bar[warp]);
-    }
   }
   __syncwarp();  // the barrier is initialised before any lane polls it
 
@@ -112,28 +108,39 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
   const int b0 = row + ((x0 == 0 ? g.L[0] - 1 : x0 - 1) >> 1);
   const int f1 = x1 == g.L[1] - 1 ? cb - (g.L[1] - 1) * g.S1 : cb + g.S1;
   const int b1 = x1 == 0 ? cb + (g.L[1] - 1) * g.S1 : cb - g.S1;
-  const int b2 = bzb * 32 + lane, b3 = btb * 32 + lane;  // sites of the backward links
+  // sites of the far neighbours (the same lane of the neighbour blocks),
+  // also the sites of the backward z and t links
+  const int f2 = bzf * 32 + lane, b2 = bzb * 32 + lane;
+  const int f3 = btf * 32 + lane, b3 = btb * 32 + lane;
   const bool fflip = x3 == g.L[3] - 1;
   const bool bflip = x3 == 0;
   constexpr int SF = DAG ? -1 : 1;
   constexpr int SB_ = -SF;
 
   cx<float> acc[12];
-#pragma unroll
-  for (int k = 0; k < 12; k++) acc[k] = mk<float>(0.f, 0.f);
-  // near hops from global memory, two hops of loads in flight
+  // the eight neighbour scales first, then the near hops from global memory
+  // with two hops of loads in flight (the same arithmetic, in the same
+  // order, as the unstaged kernel's hops_f16)
   {
+    const float* scl = (const float*)((const char*)a.in + (size_t)VP * 48);
+    float sc[8] = {__ldg(scl + f0), __ldg(scl + b0), __ldg(scl + f1), __ldg(scl + b1),
+                   __ldg(scl + f2), __ldg(scl + b2), __ldg(scl + f3), __ldg(scl + b3)};
+    __half2 ah[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) ah[k] = __float2half2_rn(0.f);
     RawF16 r0 = fetch_f16(a.in, a.gauge, f0, 0 + p, cb, VP);
     RawF16 r1 = fetch_f16(a.in, a.gauge, b0, 0 + q, b0, VP);
     RawF16 r2 = fetch_f16(a.in, a.gauge, f1, 2 + p, cb, VP);
-    compute_f16<0, SF, true>(acc, r0, false);
+    __half2 rel[4];
+    const float smax = f16_rel(sc, fflip, bflip, rel);
+    compute_f16<0, SF, true>(ah, r0, __low2half2(rel[0]));
     RawF16 r3 = fetch_f16(a.in, a.gauge, b1, 2 + q, b1, VP);
-    compute_f16<0, SB_, false>(acc, r1, false);
+    compute_f16<0, SB_, false>(ah, r1, __high2half2(rel[0]));
     fetch_link_f16(r0, a.gauge, 4 + p, cb, VP);
     fetch_link_f16(r1, a.gauge, 4 + q, b2, VP);
-    compute_f16<1, SF, true>(acc, r2, false);
+    compute_f16<1, SF, true>(ah, r2, __low2half2(rel[1]));
     fetch_link_f16(r2, a.gauge, 6 + p, cb, VP);
-    compute_f16<1, SB_, false>(acc, r3, false);
+    compute_f16<1, SB_, false>(ah, r3, __high2half2(rel[1]));
     fetch_link_f16(r3, a.gauge, 6 + q, b3, VP);
     // far hops from shared memory
     if (mbar_wait_bounded(&bar[warp], 0, spin_limit)) {
@@ -142,19 +149,16 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
         r0.s[k] = s.sp[0][k][lane];
         r1.s[k] = s.sp[1][k][lane];
       }
-      r0.sc = s.sc[0][lane];
-      r1.sc = s.sc[1][lane];
-      compute_f16<2, SF, true>(acc, r0, false);
-      compute_f16<2, SB_, false>(acc, r1, false);
+      compute_f16<2, SF, true>(ah, r0, __low2half2(rel[2]));
+      compute_f16<2, SB_, false>(ah, r1, __high2half2(rel[2]));
 #pragma unroll
       for (int k = 0; k < 3; k++) {
         r2.s[k] = s.sp[2][k][lane];
         r3.s[k] = s.sp[3][k][lane];
       }
-      r2.sc = s.sc[2][lane];
-      r3.sc = s.sc[3][lane];
-      compute_f16<3, SF, true>(acc, r2, fflip);
-      compute_f16<3, SB_, false>(acc, r3, bflip);
+      compute_f16<3, SF, true>(ah, r2, __low2half2(rel[3]));
+      compute_f16<3, SB_, false>(ah, r3, __high2half2(rel[3]));
+      f16_widen(acc, ah, (float)a.a * smax);
     } else {
       if (lane == 0) atomicExch(&g_stage_fault, 1);
       // the copies may still be in flight: drain them (bounded, long) before
@@ -167,9 +171,6 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
     }
   }
 
-  const float ca = (float)a.a;
-#pragma unroll
-  for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
   if (a.x) {
     cx<float> v[12];
     load_spinor_rw<WD_F16, float>(v, a.x, cb, VP);

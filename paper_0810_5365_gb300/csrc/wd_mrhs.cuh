@@ -103,7 +103,7 @@ __device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r
   for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
   if constexpr (P == WD_F16) {
     hops_f16<SF, SB_, COH>(acc, in, ga, p, cb, f0, b0, f1, b1, f2, b2, f3, b3, fflip, bflip,
-                           false, false, VP);
+                           false, false, VP, (float)pr.a);
   } else {
     hop<P, RC, 0, SF, true, R, COH>(acc, in, ga, f0, 0 + p, cb, false, VP);
     hop<P, RC, 0, SB_, false, R, COH>(acc, in, ga, b0, 0 + qq, b0, false, VP);
@@ -114,9 +114,11 @@ __device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r
     hop<P, RC, 3, SF, true, R, COH>(acc, in, ga, f3, 6 + p, cb, fflip, VP);
     hop<P, RC, 3, SB_, false, R, COH>(acc, in, ga, b3, 6 + qq, b3, bflip, VP);
   }
-  const R ca = (R)pr.a;
+  if constexpr (P != WD_F16) {  // (the FP16 hops apply a themselves)
+    const R ca = (R)pr.a;
 #pragma unroll
-  for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
+    for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
+  }
   if (pr.x) {
     cx<R> v[12];
     load_spinor_rw<P, R>(v, (const char*)pr.x + (size_t)r * pr.s_x, cb, VP);
