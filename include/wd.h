@@ -264,11 +264,16 @@ int wd_set_autotune(int enable);
  * launch without a fused reduction, or go back to the tuned sizes (sites =
  * 0).  The autotuner (wd_set_autotune) times the three sizes for each new
  * (link format, dagger, temporal gauge, lattice extents) met outside stream
- * capture, on a temporary output, and keeps the fastest; every size gives
+ * capture, on a temporary output, and keeps the fastest; for FP16 with
+ * 12-real links (no temporal gauge) on lattices whose (z, t) slices hold a
+ * multiple of 32 sites of one parity it also times the kernel that stages
+ * the far neighbours in shared memory (see WD_STAGE_NEIGHBOURS, whose
+ * bounded wait and wd_async_status then apply).  Every candidate gives
  * bit-identical fields.  Launches with a fused norm keep 128 sites, so that
  * the summation order of the norm never depends on a timing.
- * wd_dslash_ex_noalloc never tunes (it would allocate).  WD_ERR_ARG for
- * other sizes. */
+ * wd_dslash_ex_noalloc never tunes (it would allocate) but uses a choice
+ * already made.  A forced size always runs the unstaged kernel.  WD_ERR_ARG
+ * for other sizes. */
 int wd_dslash_set_block(int sites);
 
 /* Launch overlap of consecutive single-field hopping kernels (the paper has

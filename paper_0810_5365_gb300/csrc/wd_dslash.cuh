@@ -443,6 +443,38 @@ __device__ __forceinline__ void f16_widen(cx<float> (&acc)[12], const __half2 (&
   }
 }
 
+// Store k * ah as an FP16 site (the format of store_spinor: values scaled by
+// the site's largest |component| m, and m as the site scale) without leaving
+// half2 when it can: the largest |component| of ah is found in half2, and
+// ah is scaled by 1/max in half2 when that reciprocal is representable
+// (max >= 2^-14); a smaller (nonzero) maximum takes the FP32 route.
+__device__ __forceinline__ void store_f16_h2(void* base, int cb, int Vh_pad,
+                                             const __half2 (&ah)[12], float k) {
+  __half2 m2 = __habs2(ah[0]);
+#pragma unroll
+  for (int j = 1; j < 12; j++) m2 = __hmax2(m2, __habs2(ah[j]));
+  const float m = fmaxf(__low2float(m2), __high2float(m2));
+  int4* p = (int4*)base;
+  float* sc = (float*)((char*)base + (size_t)Vh_pad * 48);
+  int4 v[3];
+  __half2* h = reinterpret_cast<__half2*>(v);
+  if (m >= 6.103515625e-05f) {
+    const __half2 inv = __float2half2_rn(k < 0.f ? -__frcp_rn(m) : __frcp_rn(m));
+#pragma unroll
+    for (int j = 0; j < 12; j++) h[j] = __hmul2(ah[j], inv);
+  } else {
+    const float inv = m > 0.f ? (k < 0.f ? -1.f : 1.f) / m : 0.f;
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+      const float2 f = __half22float2(ah[j]);
+      h[j] = __floats2half2_rn(f.x * inv, f.y * inv);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; j++) p[sbi(cb, j, 3)] = v[j];
+  sc[cb] = m * fabsf(k);
+}
+
 #ifndef WD_F16_PREFETCH
 #define WD_F16_PREFETCH 2
 #endif
@@ -450,21 +482,19 @@ __device__ __forceinline__ void f16_widen(cx<float> (&acc)[12], const __half2 (&
 // The eight hops of one FP16 site: the eight neighbour scales are loaded
 // first, then the loads of the next hops are issued before the current one
 // is computed (WD_F16_PREFETCH hops in flight).  The hops are accumulated in
-// half2 relative to the largest neighbour scale (compute_f16); on return
-// acc = post * H in at this site, in FP32.  funit/bunit: the forward/backward
-// time link is the identity (temporal gauge).
+// half2 relative to the largest neighbour scale (compute_f16), which is
+// returned: H in at this site = smax * ah.  funit/bunit: the
+// forward/backward time link is the identity (temporal gauge).
 template <int SF, int SB_, bool COH = false>
-__device__ __forceinline__ void hops_f16(cx<float> (&acc)[12], const void* __restrict__ in,
-                                         const void* __restrict__ ga, int p, int cb, int f0,
-                                         int b0, int f1, int b1, int f2, int b2, int f3, int b3,
-                                         bool fflip, bool bflip, bool funit, bool bunit, int VP,
-                                         float post) {
+__device__ __forceinline__ float hops_f16(__half2 (&ah)[12], const void* __restrict__ in,
+                                          const void* __restrict__ ga, int p, int cb, int f0,
+                                          int b0, int f1, int b1, int f2, int b2, int f3, int b3,
+                                          bool fflip, bool bflip, bool funit, bool bunit, int VP) {
   const int q = 1 - p;
   const float* scl = (const float*)((const char*)in + (size_t)VP * 48);
   float sc[8] = {ldin<COH>(scl + f0), ldin<COH>(scl + b0), ldin<COH>(scl + f1),
                  ldin<COH>(scl + b1), ldin<COH>(scl + f2), ldin<COH>(scl + b2),
                  ldin<COH>(scl + f3), ldin<COH>(scl + b3)};
-  __half2 ah[12];
 #pragma unroll
   for (int k = 0; k < 12; k++) ah[k] = __float2half2_rn(0.f);
 #define WD_F(nb, reg, lcb) fetch_f16<COH>(in, ga, nb, reg, lcb, VP)
@@ -524,7 +554,7 @@ __device__ __forceinline__ void hops_f16(cx<float> (&acc)[12], const void* __res
   compute_f16<3, SB_, false>(ah, r1, __high2half2(rel[3]), bunit);
 #endif
 #undef WD_F
-  f16_widen(acc, ah, post * smax);
+  return smax;
 }
 
 // TG: links in temporal gauge (compile-time, so that the ordinary kernel keeps
@@ -579,9 +609,18 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
 
+    bool stored = false;
     if constexpr (P == WD_F16) {
-      hops_f16<SF, SB_>(acc, a.in, a.gauge, p, cb, f0, b0, f1, b1, f2, b2, f3, b3, fflip, bflip,
-                        funit, bunit, VP, (float)a.a);
+      __half2 ah[12];
+      const float kf = (float)a.a * hops_f16<SF, SB_>(ah, a.in, a.gauge, p, cb, f0, b0, f1, b1,
+                                                      f2, b2, f3, b3, fflip, bflip, funit, bunit,
+                                                      VP);
+      if (!a.x && !a.y) {
+        store_f16_h2(a.out, cb, VP, ah, kf);
+        stored = true;
+      } else {
+        f16_widen(acc, ah, kf);
+      }
     } else {
       hop<P, RC, 0, SF, true>(acc, a.in, a.gauge, f0, 0 + p, cb, false, VP);
       hop<P, RC, 0, SB_, false>(acc, a.in, a.gauge, b0, 0 + q, b0, false, VP);
@@ -598,27 +637,29 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
 #pragma unroll
       for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
     }
-    if (a.x) {
-      cx<R> v[12];
-      load_spinor_rw<P, R>(v, a.x, cb, VP);
-      const R cbx = (R)a.bx;
+    if (!stored) {
+      if (a.x) {
+        cx<R> v[12];
+        load_spinor_rw<P, R>(v, a.x, cb, VP);
+        const R cbx = (R)a.bx;
 #pragma unroll
-      for (int k = 0; k < 12; k++) {
-        acc[k].r = fma(cbx, v[k].r, acc[k].r);
-        acc[k].i = fma(cbx, v[k].i, acc[k].i);
+        for (int k = 0; k < 12; k++) {
+          acc[k].r = fma(cbx, v[k].r, acc[k].r);
+          acc[k].i = fma(cbx, v[k].i, acc[k].i);
+        }
       }
-    }
-    if (a.y) {
-      cx<R> v[12];
-      load_spinor_rw<P, R>(v, a.y, cb, VP);
-      const R ccy = (R)a.cy;
+      if (a.y) {
+        cx<R> v[12];
+        load_spinor_rw<P, R>(v, a.y, cb, VP);
+        const R ccy = (R)a.cy;
 #pragma unroll
-      for (int k = 0; k < 12; k++) {
-        acc[k].r = fma(ccy, v[k].r, acc[k].r);
-        acc[k].i = fma(ccy, v[k].i, acc[k].i);
+        for (int k = 0; k < 12; k++) {
+          acc[k].r = fma(ccy, v[k].r, acc[k].r);
+          acc[k].i = fma(ccy, v[k].i, acc[k].i);
+        }
       }
+      store_spinor<P, R>(a.out, cb, VP, acc);
     }
-    store_spinor<P, R>(a.out, cb, VP, acc);
     if constexpr (RED != RED_NONE) {
       if constexpr (P == WD_F16) {
         // reduce what was stored (after rounding to half)
@@ -747,6 +788,26 @@ std::map<DslashTuneKey, int>& dslash_tune_table() {
   return t;
 }
 
+// the tuner's code for the FP16 kernel with the far neighbours staged in
+// shared memory (wd_dslash_staged.cu) in place of a CTA size
+constexpr int DSLASH_STAGED = 1;
+
+// the staged kernel serves FP16 with 12-real links, no temporal gauge, no
+// fused reduction, on lattices whose (z, t) slices hold a multiple of 32
+// sites of one parity
+template <int P>
+bool dslash_staged_ok(const DslashArgs& a, int recon) {
+  return P == WD_F16 && recon == 12 && !a.tg && !a.norm_out && (a.g.S2 & 31) == 0;
+}
+
+template <int P>
+cudaError_t launch_dslash_sel(const DslashArgs& a, int recon, bool dagger, int bs,
+                              cudaStream_t st) {
+  if (bs == DSLASH_STAGED)
+    return launch_dslash_f16_staged(a, recon, dagger, state().wait_limit, st);
+  return launch_dslash_bs<P>(a, recon, dagger, bs, st);
+}
+
 template <int P>
 cudaError_t dslash_block(const DslashArgs& a, int recon, bool dagger, cudaStream_t st, int* bs) {
   *bs = DSLASH_BS;
@@ -777,15 +838,18 @@ cudaError_t dslash_block(const DslashArgs& a, int recon, bool dagger, cudaStream
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int sizes[3] = {64, 128, 256};
-  float us[3] = {0.f, 0.f, 0.f};
+  // candidates: the three CTA sizes, and for FP16 the staged kernel where
+  // the lattice allows it (bit-identical results)
+  const int sizes[4] = {64, 128, 256, DSLASH_STAGED};
+  const int ncand = dslash_staged_ok<P>(a, recon) ? 4 : 3;
+  float us[4] = {0.f, 0.f, 0.f, 0.f};
   int best = DSLASH_BS;
   float best_us = 0.f;
-  for (int c = 0; c < 3 && e == cudaSuccess; c++) {
-    e = launch_dslash_bs<P>(t, recon, dagger, sizes[c], st);
+  for (int c = 0; c < ncand && e == cudaSuccess; c++) {
+    e = launch_dslash_sel<P>(t, recon, dagger, sizes[c], st);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     for (int k = 0; k < 3 && e == cudaSuccess; k++)
-      e = launch_dslash_bs<P>(t, recon, dagger, sizes[c], st);
+      e = launch_dslash_sel<P>(t, recon, dagger, sizes[c], st);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -804,11 +868,22 @@ cudaError_t dslash_block(const DslashArgs& a, int recon, bool dagger, cudaStream
   if (fe != cudaSuccess) return fe;
   tab[key] = best;
   char line[256];
-  std::snprintf(line, sizeof(line),
-                "dslash prec=%d recon=%d dagger=%d tg=%d dims=%dx%dx%dx%d "
-                "us[64,128,256]=%.1f,%.1f,%.1f block=%d\n",
-                P, recon, key.dagger, key.tg, key.L[0], key.L[1], key.L[2], key.L[3], us[0],
-                us[1], us[2], best);
+  if (ncand == 4)
+    std::snprintf(line, sizeof(line),
+                  "dslash prec=%d recon=%d dagger=%d tg=%d dims=%dx%dx%dx%d "
+                  "us[64,128,256,staged]=%.1f,%.1f,%.1f,%.1f block=%s\n",
+                  P, recon, key.dagger, key.tg, key.L[0], key.L[1], key.L[2], key.L[3], us[0],
+                  us[1], us[2], us[3],
+                  best == DSLASH_STAGED ? "staged"
+                  : best == 64          ? "64"
+                  : best == 128         ? "128"
+                                        : "256");
+  else
+    std::snprintf(line, sizeof(line),
+                  "dslash prec=%d recon=%d dagger=%d tg=%d dims=%dx%dx%dx%d "
+                  "us[64,128,256]=%.1f,%.1f,%.1f block=%d\n",
+                  P, recon, key.dagger, key.tg, key.L[0], key.L[1], key.L[2], key.L[3], us[0],
+                  us[1], us[2], best);
   dslash_tune_record(line);
   *bs = best;
   return cudaSuccess;
@@ -820,7 +895,8 @@ cudaError_t launch_dslash_prec(const DslashArgs& a, int recon, bool dagger, cuda
   int bs = DSLASH_BS;
   cudaError_t e = dslash_block<P>(a, recon, dagger, st, &bs);
   if (e != cudaSuccess) return e;
-  return launch_dslash_bs<P>(a, recon, dagger, bs, st);
+  if (bs == DSLASH_STAGED && !dslash_staged_ok<P>(a, recon)) bs = DSLASH_BS;
+  return launch_dslash_sel<P>(a, recon, dagger, bs, st);
 }
 
 }  // namespace wd

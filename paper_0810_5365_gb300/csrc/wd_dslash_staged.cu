@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
   constexpr int SB_ = -SF;
 
   cx<float> acc[12];
+  bool stored = false;
   // the eight neighbour scales first, then the near hops from global memory
   // with two hops of loads in flight (the same arithmetic, in the same
   // order, as the unstaged kernel's hops_f16)
@@ -158,7 +159,13 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
       }
       compute_f16<3, SF, true>(ah, r2, __low2half2(rel[3]));
       compute_f16<3, SB_, false>(ah, r3, __high2half2(rel[3]));
-      f16_widen(acc, ah, (float)a.a * smax);
+      const float kf = (float)a.a * smax;
+      if (!a.x && !a.y) {
+        store_f16_h2(a.out, cb, VP, ah, kf);
+        stored = true;
+      } else {
+        f16_widen(acc, ah, kf);
+      }
     } else {
       if (lane == 0) atomicExch(&g_stage_fault, 1);
       // the copies may still be in flight: drain them (bounded, long) before
@@ -171,6 +178,7 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
     }
   }
 
+  if (stored) return;
   if (a.x) {
     cx<float> v[12];
     load_spinor_rw<WD_F16, float>(v, a.x, cb, VP);

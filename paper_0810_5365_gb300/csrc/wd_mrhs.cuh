@@ -101,9 +101,19 @@ __device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r
   cx<R> acc[12];
 #pragma unroll
   for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
+  void* out = (char*)pr.out + (size_t)r * pr.s_out;
+  bool stored = false;
   if constexpr (P == WD_F16) {
-    hops_f16<SF, SB_, COH>(acc, in, ga, p, cb, f0, b0, f1, b1, f2, b2, f3, b3, fflip, bflip,
-                           false, false, VP, (float)pr.a);
+    __half2 ah[12];
+    const float kf = (float)pr.a * hops_f16<SF, SB_, COH>(ah, in, ga, p, cb, f0, b0, f1, b1, f2,
+                                                         b2, f3, b3, fflip, bflip, false, false,
+                                                         VP);
+    if (!pr.x && !pr.y) {
+      store_f16_h2(out, cb, VP, ah, kf);
+      stored = true;
+    } else {
+      f16_widen(acc, ah, kf);
+    }
   } else {
     hop<P, RC, 0, SF, true, R, COH>(acc, in, ga, f0, 0 + p, cb, false, VP);
     hop<P, RC, 0, SB_, false, R, COH>(acc, in, ga, b0, 0 + qq, b0, false, VP);
@@ -119,28 +129,29 @@ __device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = ca * acc[k];
   }
-  if (pr.x) {
-    cx<R> v[12];
-    load_spinor_rw<P, R>(v, (const char*)pr.x + (size_t)r * pr.s_x, cb, VP);
-    const R cbx = (R)pr.bx;
+  if (!stored) {
+    if (pr.x) {
+      cx<R> v[12];
+      load_spinor_rw<P, R>(v, (const char*)pr.x + (size_t)r * pr.s_x, cb, VP);
+      const R cbx = (R)pr.bx;
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      acc[k].r = fma(cbx, v[k].r, acc[k].r);
-      acc[k].i = fma(cbx, v[k].i, acc[k].i);
+      for (int k = 0; k < 12; k++) {
+        acc[k].r = fma(cbx, v[k].r, acc[k].r);
+        acc[k].i = fma(cbx, v[k].i, acc[k].i);
+      }
     }
-  }
-  if (pr.y) {
-    cx<R> v[12];
-    load_spinor_rw<P, R>(v, (const char*)pr.y + (size_t)r * pr.s_y, cb, VP);
-    const R ccy = (R)pr.cy;
+    if (pr.y) {
+      cx<R> v[12];
+      load_spinor_rw<P, R>(v, (const char*)pr.y + (size_t)r * pr.s_y, cb, VP);
+      const R ccy = (R)pr.cy;
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      acc[k].r = fma(ccy, v[k].r, acc[k].r);
-      acc[k].i = fma(ccy, v[k].i, acc[k].i);
+      for (int k = 0; k < 12; k++) {
+        acc[k].r = fma(ccy, v[k].r, acc[k].r);
+        acc[k].i = fma(ccy, v[k].i, acc[k].i);
+      }
     }
+    store_spinor<P, R>(out, cb, VP, acc);
   }
-  void* out = (char*)pr.out + (size_t)r * pr.s_out;
-  store_spinor<P, R>(out, cb, VP, acc);
   double nrm = 0.0;
   if constexpr (NORM) {
     if constexpr (P == WD_F16) load_spinor_rw<P, R>(acc, out, cb, VP);
