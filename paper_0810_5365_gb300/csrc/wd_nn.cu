@@ -417,6 +417,33 @@ __global__ void nn_adam(float* w, const float* grad, float* m, float* v, int n, 
 // network application
 // ---------------------------------------------------------------------------
 
+// the BF16 link copy of the inference layers from the packed FP32 12-real
+// links (rows 0 and 1 rounded to BF16; padding sites converted as they are)
+__global__ void nn_gauge_to_bf16(const float4* __restrict__ g32, int4* __restrict__ ga,
+                                 int2* __restrict__ gb, int vh_pad) {
+  const long n = 8L * vh_pad;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / vh_pad), cb = (int)(i - (long)r * vh_pad);
+    const float4* p = g32 + (size_t)r * vh_pad * 3;
+    const float4 a = __ldg(p + sbi(cb, 0, 3)), b = __ldg(p + sbi(cb, 1, 3)),
+                 c = __ldg(p + sbi(cb, 2, 3));
+    const __nv_bfloat162 h[6] = {__floats2bfloat162_rn(a.x, a.y), __floats2bfloat162_rn(a.z, a.w),
+                                 __floats2bfloat162_rn(b.x, b.y), __floats2bfloat162_rn(b.z, b.w),
+                                 __floats2bfloat162_rn(c.x, c.y), __floats2bfloat162_rn(c.z, c.w)};
+    ga[i] = make_int4((int)bf2_u(h[0]), (int)bf2_u(h[1]), (int)bf2_u(h[2]), (int)bf2_u(h[3]));
+    gb[i] = make_int2((int)bf2_u(h[4]), (int)bf2_u(h[5]));
+  }
+}
+
+static cudaError_t nn_gauge_bf16(void* gbf, const void* g32, const Geom& g, cudaStream_t st) {
+  int4* ga = (int4*)gbf;
+  int2* gb = (int2*)((char*)gbf + (size_t)8 * g.Vh_pad * 16);
+  nn_gauge_to_bf16<<<blas_grid(8LL * g.Vh_pad, 256), 256, 0, st>>>((const float4*)g32, ga, gb,
+                                                                   g.Vh_pad);
+  return cudaGetLastError();
+}
+
 struct NnBuffers {
   void* h1 = nullptr;  // 8 channels
   void* h2 = nullptr;  // 8 channels
@@ -456,7 +483,8 @@ static cudaError_t nn_layer_bf16(int cin, int cout, bool bin, bool bout, const G
 }
 
 // N (even: P_e N P_e) with BF16 activations between the layers (input and output stay
-// packed FP32 fields): the link transport runs in packed bf16x2 arithmetic,
+// packed FP32 fields; gauge: the BF16 link copy, nn_gauge_bf16): the link
+// transport runs in packed bf16x2 arithmetic,
 // the channel mixing on the tensor cores with FP32 accumulation.  For the
 // preconditioner inside the flexible CG, whose beta absorbs the extra
 // rounding (about 2^-8 relative per layer).  B.h1 and B.h2 hold 8-channel
@@ -884,8 +912,12 @@ int nn_apply_ex_impl(void* out, const void* in, const float* w, const void* gaug
   int* flag = nullptr;
   NCK(device_flag(&flag, st));
   const bool even = (flags & 2) != 0;
-  if (flags & 1)
-    NCK(nn_forward_bf16(g, gauge, w, in, out, B, flag, st, even));
+  if (flags & 1) {
+    void* gbf;
+    NCK(al.get(&gbf, nn_gauge_bytes_bf16(g.Vh_pad)));
+    NCK(nn_gauge_bf16(gbf, gauge, g, st));
+    NCK(nn_forward_bf16(g, gbf, w, in, out, B, flag, st, even));
+  }
   else if (even)
     NCK(nn_forward_even(g, gauge, w, in, out, B, flag, st));
   else
@@ -1281,6 +1313,13 @@ int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, c
     }
     NCK(pack_gauge(g32, gd, g, WD_F32, 12, st));
     NCK(pack_gauge(g64, gd, g, WD_F64, 18, st));
+#if WD_NN_FCG_BF16
+    void* gbf = nullptr;  // the BF16 link copy of the network's layers
+    if (wts) {
+      NCK(al.get(&gbf, nn_gauge_bytes_bf16(g.Vh_pad)));
+      NCK(nn_gauge_bf16(gbf, g32, g, st));
+    }
+#endif
     const double* bd = bsrc;
     double* canon = nullptr;
     {
@@ -1373,9 +1412,9 @@ int fcg_impl(double* x, const double* bsrc, const double* gauge, double kappa, c
     auto precond = [&](void* zo, const void* si) -> cudaError_t {
       if (!wts) return cudaMemcpyAsync(zo, si, h32, cudaMemcpyDeviceToDevice, st);
 #if WD_NN_FCG_BF16
-      cudaError_t e = nn_forward_bf16(g, g32, (const float*)wa, si, w, B, flag, st, true);
+      cudaError_t e = nn_forward_bf16(g, gbf, (const float*)wa, si, w, B, flag, st, true);
       if (e != cudaSuccess) return e;
-      return nn_forward_bf16(g, g32, wts, w, zo, B, flag, st, true);
+      return nn_forward_bf16(g, gbf, wts, w, zo, B, flag, st, true);
 #else
       cudaError_t e = nn_forward_even(g, g32, (const float*)wa, si, w, B, flag, st);
       if (e != cudaSuccess) return e;

@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cstring>
 
 #include "wd_internal.h"
 #include "wd_tc.cuh"
@@ -36,7 +37,7 @@ constexpr long NN_SPIN_LIMIT = 1L << 22;
 
 struct NnLayerArgs {
   Geom g;
-  const void* gauge;       // packed FP32, 12 reals
+  const void* gauge;       // packed FP32, 12 reals (the BF16 copy for BF16 activations)
   const char* in;          // CIN channels, full field
   char* out;               // COUT channels, full field
   size_t in_half, out_half;  // bytes per parity half
@@ -257,12 +258,64 @@ __device__ __forceinline__ void nn_load4_bf16(__nv_bfloat162 (&v)[12], const cha
   }
 }
 
+// Exact lane moves on a bf16x2 (re low, im high) on the integer pipe:
+// bf2_i(v) = i v = (-v.i, v.r); bf2_conj(v) = (v.r, -v.i).
+__device__ __forceinline__ __nv_bfloat162 bf2_bits(unsigned x) {
+  __nv_bfloat162 h;
+  memcpy(&h, &x, 4);
+  return h;
+}
+__device__ __forceinline__ unsigned bf2_u(__nv_bfloat162 h) {
+  unsigned x;
+  memcpy(&x, &h, 4);
+  return x;
+}
+__device__ __forceinline__ __nv_bfloat162 bf2_i(__nv_bfloat162 v) {
+  return bf2_bits(__byte_perm(bf2_u(v), 0, 0x1032) ^ 0x00008000u);
+}
+__device__ __forceinline__ __nv_bfloat162 bf2_conj(__nv_bfloat162 v) {
+  return bf2_bits(bf2_u(v) ^ 0x80000000u);
+}
+
+// conj(a b - c d) in bf16x2 arithmetic (the SU(3) third row from the first two)
+__device__ __forceinline__ __nv_bfloat162 bf2_conj_cross(__nv_bfloat162 a, __nv_bfloat162 b,
+                                                         __nv_bfloat162 c, __nv_bfloat162 d) {
+  __nv_bfloat162 x = __hmul2(__low2bfloat162(a), b);
+  x = __hfma2(__high2bfloat162(a), bf2_i(b), x);
+  x = __hfma2(__hneg2(__low2bfloat162(c)), d, x);
+  x = __hfma2(__hneg2(__high2bfloat162(c)), bf2_i(d), x);
+  return bf2_conj(x);
+}
+
+// The BF16 copy of the 12-real links used by the inference layers: region r
+// = 2 mu + parity holds, per site, U00 U01 U02 U10 as four bf16x2 (one int4,
+// in the first 8 regions) and U11 U12 as two bf16x2 (one int2, in 8 more
+// regions after them): 24 bytes per link, half of the FP32 copy's.
+__host__ __device__ constexpr size_t nn_gauge_bytes_bf16(int vh_pad) {
+  return (size_t)8 * vh_pad * 24;
+}
+
+__device__ __forceinline__ void nn_link_bf16(__nv_bfloat162 (&u)[9], const void* gauge,
+                                             int region, int cb, int vh_pad) {
+  const int4 la = __ldg((const int4*)gauge + (size_t)region * vh_pad + cb);
+  const int2 lb =
+      __ldg((const int2*)((const char*)gauge + (size_t)8 * vh_pad * 16) + (size_t)region * vh_pad + cb);
+  u[0] = bf2_bits((unsigned)la.x);
+  u[1] = bf2_bits((unsigned)la.y);
+  u[2] = bf2_bits((unsigned)la.z);
+  u[3] = bf2_bits((unsigned)la.w);
+  u[4] = bf2_bits((unsigned)lb.x);
+  u[5] = bf2_bits((unsigned)lb.y);
+  u[6] = bf2_conj_cross(u[1], u[5], u[2], u[4]);
+  u[7] = bf2_conj_cross(u[2], u[3], u[0], u[5]);
+  u[8] = bf2_conj_cross(u[0], u[4], u[1], u[3]);
+}
+
 // T_d of four input channels at this site in packed bf16x2 arithmetic.
 // With vx = i v, u v = u.r v + u.i vx and conj(u) v = u.r v - u.i vx, so each
-// complex multiply-accumulate is two packed FMAs.  The link is loaded and its
-// third row rebuilt in FP32, then rounded to BF16 with the antiperiodic sign
-// folded in.  The input is BF16 (BIN) or the packed FP32 field (rounded on
-// load).
+// complex multiply-accumulate is two packed FMAs.  The link comes from the
+// BF16 copy (nn_link_bf16), its third row rebuilt in bf16x2.  The input is
+// BF16 (BIN) or the packed FP32 field (rounded on load).
 template <int C, bool BIN>
 __device__ __forceinline__ void nn_transport4_bf16(__nv_bfloat162 (&t)[12], const NnLayerArgs& A,
                                                    int d, int p, int cb, int n, int x3, int c0) {
@@ -283,29 +336,36 @@ __device__ __forceinline__ void nn_transport4_bf16(__nv_bfloat162 (&t)[12], cons
   }
   const int mu = (d - 1) >> 1;
   const bool fwd = (d & 1) != 0;
-  cx<float> u[9];
-  load_link<WD_F32, 12, float>(u, A.gauge, 2 * mu + (fwd ? p : 1 - p), fwd ? cb : n,
-                               A.g.Vh_pad);
+  // the link in BF16: rows 0 and 1 loaded, row 2 rebuilt in bf16x2
+  __nv_bfloat162 u[9];
+  nn_link_bf16(u, A.gauge, 2 * mu + (fwd ? p : 1 - p), fwd ? cb : n, A.g.Vh_pad);
+  // the antiperiodic sign of a hop across the time boundary, applied to the
+  // result as a sign-bit flip (exact, as a negated link would be)
   const bool flip = mu == 3 && (fwd ? x3 == A.g.L[3] - 1 : x3 == 0);
-  const float sg = flip ? -1.f : 1.f;
+  const unsigned sgn = flip ? 0x80008000u : 0u;
   // ur[k] = (u.r, u.r), ui[k] = (u.i, u.i) of the element the product needs
   __nv_bfloat162 ur[9], ui[9];
 #pragma unroll
   for (int a = 0; a < 3; a++)
 #pragma unroll
     for (int b = 0; b < 3; b++) {
-      const cx<float> e = fwd ? u[a * 3 + b] : u[b * 3 + a];
-      ur[a * 3 + b] = __float2bfloat162_rn(sg * e.r);
-      ui[a * 3 + b] = __float2bfloat162_rn(sg * e.i);
+      const __nv_bfloat162 e = fwd ? u[a * 3 + b] : u[b * 3 + a];
+      ur[a * 3 + b] = __low2bfloat162(e);
+      ui[a * 3 + b] = __high2bfloat162(e);
     }
-  // (-1, 1) turns the swapped (im, re) into i v; (1, -1) into -i v
-  const __nv_bfloat162 ix = fwd ? __floats2bfloat162_rn(-1.f, 1.f) : __floats2bfloat162_rn(1.f, -1.f);
   const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
 #pragma unroll
   for (int c = 0; c < 4; c++) {
+    // vx = i v (U v) or -i v (U^+ v): a lane swap and a sign-bit flip on the
+    // integer pipe (the packed BF16 FMAs issue at half the FP32 rate)
     __nv_bfloat162 vx[3];
 #pragma unroll
-    for (int b = 0; b < 3; b++) vx[b] = __hmul2(__lowhigh2highlow(v[c * 3 + b]), ix);
+    for (int b = 0; b < 3; b++) {
+      unsigned x;
+      memcpy(&x, &v[c * 3 + b], 4);
+      x = __byte_perm(x, 0, 0x1032) ^ (fwd ? 0x00008000u : 0x80000000u);
+      memcpy(&vx[b], &x, 4);
+    }
 #pragma unroll
     for (int a = 0; a < 3; a++) {
       __nv_bfloat162 w = zero;
@@ -314,7 +374,10 @@ __device__ __forceinline__ void nn_transport4_bf16(__nv_bfloat162 (&t)[12], cons
         w = __hfma2(ur[a * 3 + b], v[c * 3 + b], w);
         w = __hfma2(ui[a * 3 + b], vx[b], w);
       }
-      t[c * 3 + a] = w;
+      unsigned y;
+      memcpy(&y, &w, 4);
+      y ^= sgn;
+      memcpy(&t[c * 3 + a], &y, 4);
     }
   }
 }
@@ -382,8 +445,12 @@ __global__ void __launch_bounds__(NN_THREADS, (BIN || BOUT) ? WD_NN_MINB_BF16 : 
     int nb[NN_NDIR];
     int x3 = 0;
     if (valid) nn_nbr(nb, x3, cb, p, g);
+    // a tile whose hops vanish (its input parity is zero) needs the chunk of
+    // the self term only (chunk 0); the condition is the same in the whole CTA
+    const int nch = skip_hops ? 1 : NCHUNK;
 #pragma unroll
-    for (int c = 0; c < NCHUNK; c++, G++) {
+    for (int c = 0; c < NCHUNK; c++) {
+      if (c >= nch) break;
       const uint32_t buf = G & 1u;
       if (G >= 2) ok = mbar_wait_bounded(&bar[buf], ((G - 2) >> 1) & 1u, NN_SPIN_LIMIT) && ok;
       const int d = CIN == 8 ? c : 2 * c + hh;
@@ -443,6 +510,7 @@ __global__ void __launch_bounds__(NN_THREADS, (BIN || BOUT) ? WD_NN_MINB_BF16 : 
         }
         tc_commit(&bar[buf]);
       }
+      G++;
     }
     // the tile's last commit covers every MMA issued before it
     ok = mbar_wait_bounded(&bar[(G - 1) & 1u], ((G - 1) >> 1) & 1u, NN_SPIN_LIMIT) && ok;
