@@ -291,6 +291,35 @@ __device__ __forceinline__ void load_spinor_rw(cx<R> (&s)[12], const void* base,
   }
 }
 
+// An FP16 site: the values scaled by the site's largest |real component| m,
+// rounded to half, and m as the site scale.  KEEP: s is overwritten with
+// what was stored (the rounded values times m, as load_spinor_rw would read
+// them back), for a norm or dot product of the stored field.
+template <typename R, bool KEEP>
+__device__ __forceinline__ void store_spinor_f16(void* base, int cb, int Vh_pad, cx<R> (&s)[12]) {
+  float m = 0.f;
+#pragma unroll
+  for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf((float)s[k].r), fabsf((float)s[k].i)));
+  float inv = m > 0.f ? 1.0f / m : 0.f;
+  int4* p = (int4*)base;
+  float* sc = (float*)((char*)base + (size_t)Vh_pad * 48);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    int4 v;
+    __half2* h = reinterpret_cast<__half2*>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      h[j] = __floats2half2_rn((float)s[4 * k + j].r * inv, (float)s[4 * k + j].i * inv);
+      if constexpr (KEEP) {
+        const float2 f = __half22float2(h[j]);
+        s[4 * k + j] = mk<R>((R)(f.x * m), (R)(f.y * m));
+      }
+    }
+    p[sbi(cb, k, 3)] = v;
+  }
+  sc[cb] = m;
+}
+
 template <int P, typename R>
 __device__ __forceinline__ void store_spinor(void* base, int cb, int Vh_pad, const cx<R> (&s)[12]) {
   if constexpr (P == WD_F64) {
@@ -304,23 +333,7 @@ __device__ __forceinline__ void store_spinor(void* base, int cb, int Vh_pad, con
       p[sbi(cb, k, 6)] = make_float4((float)s[2 * k].r, (float)s[2 * k].i,
                                      (float)s[2 * k + 1].r, (float)s[2 * k + 1].i);
   } else {
-    // per-site scale: the largest |real component| of the site
-    float m = 0.f;
-#pragma unroll
-    for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf((float)s[k].r), fabsf((float)s[k].i)));
-    float inv = m > 0.f ? 1.0f / m : 0.f;
-    int4* p = (int4*)base;
-    float* sc = (float*)((char*)base + (size_t)Vh_pad * 48);
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      int4 v;
-      __half2* h = reinterpret_cast<__half2*>(&v);
-#pragma unroll
-      for (int j = 0; j < 4; j++)
-        h[j] = __floats2half2_rn((float)s[4 * k + j].r * inv, (float)s[4 * k + j].i * inv);
-      p[sbi(cb, k, 3)] = v;
-    }
-    sc[cb] = m;
+    store_spinor_f16<R, false>(base, cb, Vh_pad, const_cast<cx<R>(&)[12]>(s));
   }
 }
 
@@ -451,8 +464,11 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[N], RedScratch rs, doubl
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < N; j++) rs.partials[(size_t)blockIdx.x * N + j] = v[j];
-    __threadfence();
-    unsigned t = atomicAdd(rs.counter, 1u);
+    // one acquire-release arrival: it orders the partials written above
+    // before it for the last block, and that block's reads after it
+    unsigned t;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                 : "=r"(t) : "l"(rs.counter) : "memory");
     last = (t == gridDim.x - 1);
   }
   __syncthreads();

@@ -447,9 +447,12 @@ __device__ __forceinline__ void f16_widen(cx<float> (&acc)[12], const __half2 (&
 // the site's largest |component| m, and m as the site scale) without leaving
 // half2 when it can: the largest |component| of ah is found in half2, and
 // ah is scaled by 1/max in half2 when that reciprocal is representable
-// (max >= 2^-14); a smaller (nonzero) maximum takes the FP32 route.
+// (max >= 2^-14); a smaller (nonzero) maximum takes the FP32 route.  KEEP:
+// kept receives the stored site (for a fused norm).
+template <bool KEEP = false>
 __device__ __forceinline__ void store_f16_h2(void* base, int cb, int Vh_pad,
-                                             const __half2 (&ah)[12], float k) {
+                                             const __half2 (&ah)[12], float k,
+                                             cx<float> (&kept)[12]) {
   __half2 m2 = __habs2(ah[0]);
 #pragma unroll
   for (int j = 1; j < 12; j++) m2 = __hmax2(m2, __habs2(ah[j]));
@@ -472,7 +475,15 @@ __device__ __forceinline__ void store_f16_h2(void* base, int cb, int Vh_pad,
   }
 #pragma unroll
   for (int j = 0; j < 3; j++) p[sbi(cb, j, 3)] = v[j];
-  sc[cb] = m * fabsf(k);
+  const float so = m * fabsf(k);
+  sc[cb] = so;
+  if constexpr (KEEP) {  // what was stored, as load_spinor_rw would read it back
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+      const float2 f = __half22float2(h[j]);
+      kept[j] = mk<float>(f.x * so, f.y * so);
+    }
+  }
 }
 
 #ifndef WD_F16_PREFETCH
@@ -616,7 +627,7 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
                                                       f2, b2, f3, b3, fflip, bflip, funit, bunit,
                                                       VP);
       if (!a.x && !a.y) {
-        store_f16_h2(a.out, cb, VP, ah, kf);
+        store_f16_h2<RED != RED_NONE>(a.out, cb, VP, ah, kf, acc);
         stored = true;
       } else {
         f16_widen(acc, ah, kf);
@@ -658,13 +669,13 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
           acc[k].i = fma(ccy, v[k].i, acc[k].i);
         }
       }
-      store_spinor<P, R>(a.out, cb, VP, acc);
+      if constexpr (P == WD_F16 && RED != RED_NONE)
+        store_spinor_f16<R, true>(a.out, cb, VP, acc);
+      else
+        store_spinor<P, R>(a.out, cb, VP, acc);
     }
     if constexpr (RED != RED_NONE) {
-      if constexpr (P == WD_F16) {
-        // reduce what was stored (after rounding to half)
-        load_spinor_rw<P, R>(acc, a.out, cb, VP);
-      }
+      // (for FP16, acc now holds what was stored, after rounding to half)
       if constexpr (RED == RED_NORM || RED == RED_NORM_DOTX) red[0] = site_norm2(acc);
       if constexpr (RED == RED_NORM_DOTX) {
         cx<R> v[12];

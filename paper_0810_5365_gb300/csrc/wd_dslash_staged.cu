@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(STG_WARPS * 32, DslashMinBlocks<WD_F16, false>
       compute_f16<3, SB_, false>(ah, r3, __high2half2(rel[3]));
       const float kf = (float)a.a * smax;
       if (!a.x && !a.y) {
-        store_f16_h2(a.out, cb, VP, ah, kf);
+        store_f16_h2(a.out, cb, VP, ah, kf, acc);
         stored = true;
       } else {
         f16_widen(acc, ah, kf);

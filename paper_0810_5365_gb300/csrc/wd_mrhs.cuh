@@ -109,7 +109,7 @@ __device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r
                                                          b2, f3, b3, fflip, bflip, false, false,
                                                          VP);
     if (!pr.x && !pr.y) {
-      store_f16_h2(out, cb, VP, ah, kf);
+      store_f16_h2<NORM>(out, cb, VP, ah, kf, acc);
       stored = true;
     } else {
       f16_widen(acc, ah, kf);
@@ -150,13 +150,13 @@ __device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r
         acc[k].i = fma(ccy, v[k].i, acc[k].i);
       }
     }
-    store_spinor<P, R>(out, cb, VP, acc);
+    if constexpr (P == WD_F16 && NORM)
+      store_spinor_f16<R, true>(out, cb, VP, acc);
+    else
+      store_spinor<P, R>(out, cb, VP, acc);
   }
   double nrm = 0.0;
-  if constexpr (NORM) {
-    if constexpr (P == WD_F16) load_spinor_rw<P, R>(acc, out, cb, VP);
-    nrm = site_norm2(acc);
-  }
+  if constexpr (NORM) nrm = site_norm2(acc);  // (FP16: acc holds what was stored)
   return nrm;
 }
 
