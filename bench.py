@@ -67,7 +67,7 @@ def dslash_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0810_5365_gb300", "csrc")
     for f in ("wd_common.cuh", "wd_dslash.cuh", "wd_internal.h", "wd_dslash_f32.cu",
-              "wd_dslash_f16.cu", "wd_dslash_f64.cu"):
+              "wd_dslash_f16.cu", "wd_dslash_f64.cu", "wd_dslash_staged.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -716,7 +716,8 @@ def profile_case(name):
     ``nn``        2 applications of the series-initialised network (three
                   tensor-core layers) on 16^3x32;
     ``staged``    4 FP16 parity dslashes on 32^3x64 with the far neighbours
-                  staged by bulk copies (WD_STAGE_NEIGHBOURS), then 4 without."""
+                  staged by bulk copies (WD_STAGE_NEIGHBOURS), then 4 with the
+                  unstaged kernel (128-site CTAs forced, so no tuning runs)."""
     import torch
     from synth import fields
     import paper_0810_5365_gb300 as W
@@ -747,10 +748,12 @@ def profile_case(name):
         W.wd_pack_spinor(a, src, dims, W.WD_FULL, W.WD_F16)
         del src
         h = W.wd_spinor_bytes(dims, W.WD_EVEN, W.WD_F16)
+        W.wd_dslash_set_block(128)
         for recon in (12 | W.WD_STAGE_NEIGHBOURS, 12):
             for _ in range(4):
                 W.wd_dslash_ex(a[:h], a[h:], g, W.WD_EVEN, 0, -KAPPA, None, 0.0, None, 0.0,
                                None, dims, W.WD_F16, recon)
+        W.wd_dslash_set_block(0)
     elif name in ("solve_f32", "solve_f16"):
         dims = SOLVE_DIMS
         Ud = torch.from_numpy(fields.su3_links(dims).view(np.float64).reshape(-1)).cuda()
