@@ -1026,7 +1026,8 @@ def run_ours(args, rank, world, local):
         if name == "f16_staged":
             line["variants"][name]["note"] = (
                 "FP16 with the +-z and +-t neighbour spinors staged in shared memory by "
-                "bulk asynchronous (TMA) copies, one mbarrier per warp; bit-identical to f16")
+                "bulk asynchronous (TMA) copies, one mbarrier per warp; bit-identical to f16, "
+                "and the kernel the CTA-size tuner chooses for plain FP16 calls on this lattice")
         line["gpu_launches"] += st
     line["e2e"] = {"value": FLOPS_PER_SITE * Vh * k_e2e * world / dt_e2e / 1e9, "unit": "Gflops",
                    "steps": k_e2e, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
