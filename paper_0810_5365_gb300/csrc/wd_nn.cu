@@ -64,6 +64,45 @@ static cudaError_t launch_layer(const NnLayerArgs& A, int ntiles, cudaStream_t s
   return cudaGetLastError();
 }
 
+// the one-thread-per-site inference kernel, with its residency computed the
+// same way
+template <int CIN, int COUT, bool BIN, bool BOUT>
+static cudaError_t launch_infer(const NnLayerArgs& A, int ntiles, cudaStream_t st) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, nn_infer_kernel<CIN, COUT, BIN, BOUT>);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    int regs_sm = 0, smem_sm = 0, thr_sm = 0;
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = regs_sm / (warp_regs * (NN_TILE / 32));
+    const int by_smem = smem_sm / ((int)fa.sharedSizeBytes + 1024);
+    const int by_thr = thr_sm / NN_TILE;
+    int n = by_regs < by_smem ? by_regs : by_smem;
+    n = n < by_thr ? n : by_thr;
+    // (at most 8: eight CTAs fill the 512 TMEM columns of an SM)
+    n = n < 1 ? 1 : (n > 8 ? 8 : n);
+    const int pct = (int)((100LL * n * ((int)fa.sharedSizeBytes + 1024) + smem_sm - 1) / smem_sm);
+    e = cudaFuncSetAttribute(nn_infer_kernel<CIN, COUT, BIN, BOUT>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, pct < 100 ? pct : 100);
+    if (e != cudaSuccess) return e;
+    per_sm = n;
+  }
+  const int cap = num_sms() * per_sm;
+  const int grid = ntiles < cap ? ntiles : cap;
+  nn_infer_kernel<CIN, COUT, BIN, BOUT><<<grid, NN_TILE, 0, st>>>(A, ntiles);
+  return cudaGetLastError();
+}
+
+#ifndef WD_NN_INFER1
+#define WD_NN_INFER1 1  // BF16 inference layers: the one-thread-per-site kernel
+#endif
+
 // out_parity: -1 both parities, else only that one; zero_in: the parity of
 // the input known to vanish (never read), or -1
 static cudaError_t nn_layer(int cin, int cout, const Geom& g, const void* gauge, const void* in,
@@ -476,9 +515,15 @@ static cudaError_t nn_layer_bf16(int cin, int cout, bool bin, bool bout, const G
   A.np = out_parity < 0 ? 2 : 1;
   A.zero_in = zero_in;
   const int ntiles = A.np * ((g.Vh + NN_TILE - 1) / NN_TILE);
+#if WD_NN_INFER1
+  if (cin == 4 && cout == 8 && !bin && bout) return launch_infer<4, 8, false, true>(A, ntiles, st);
+  if (cin == 8 && cout == 8 && bin && bout) return launch_infer<8, 8, true, true>(A, ntiles, st);
+  if (cin == 8 && cout == 4 && bin && !bout) return launch_infer<8, 4, true, false>(A, ntiles, st);
+#else
   if (cin == 4 && cout == 8 && !bin && bout) return launch_layer<4, 8, false, true>(A, ntiles, st);
   if (cin == 8 && cout == 8 && bin && bout) return launch_layer<8, 8, true, true>(A, ntiles, st);
   if (cin == 8 && cout == 4 && bin && !bout) return launch_layer<8, 4, true, false>(A, ntiles, st);
+#endif
   return cudaErrorInvalidValue;
 }
 

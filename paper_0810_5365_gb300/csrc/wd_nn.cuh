@@ -558,4 +558,252 @@ __global__ void __launch_bounds__(NN_THREADS, (BIN || BOUT) ? WD_NN_MINB_BF16 : 
   if (warp == 0) tmem_dealloc(tbase, 64);
 }
 
+// ---------------------------------------------------------------------------
+// Inference kernel with one thread per site (BF16 activations, the flexible
+// CG's preconditioner).  Each thread transports all input channels of its
+// site for a chunk's directions, so the link of a (site, direction) is
+// loaded, rebuilt and broadcast once (the two-thread kernel above does it in
+// both threads), and each per-chunk CTA barrier joins 4 warps instead of 8.
+// Same chunks, A layout, MMAs, TMEM accumulators and epilogue as above, and
+// bit-identical results.  Measured against the two-thread kernel on the
+// learned-preconditioner solve (32^3x64): 0.206 -> 0.200 s at 80 registers
+// (6 CTAs per SM); 72 and 64 registers spill and are slower, and loading a
+// chunk ahead (30 more registers) spills or costs residency: 0.203-0.251 s.
+// ---------------------------------------------------------------------------
+
+#ifndef WD_NN_MINB_INF
+#define WD_NN_MINB_INF 6   // 128-thread CTAs per SM the register budget is sized for
+#endif
+
+// the link of direction d > 0 at this site, as the broadcasts the product
+// needs (ur = (u.r, u.r), ui = (u.i, u.i) of U (forward) or U^+ (backward)),
+// and the sign-bit mask of the antiperiodic boundary
+struct NnLinkBf {
+  __nv_bfloat162 ur[9], ui[9];
+  unsigned sgn;
+  bool fwd;
+};
+
+__device__ __forceinline__ void nn_link_prep_bf16(NnLinkBf& L, const NnLayerArgs& A, int d, int p,
+                                                  int cb, int n, int x3) {
+  const int mu = (d - 1) >> 1;
+  L.fwd = (d & 1) != 0;
+  __nv_bfloat162 u[9];
+  nn_link_bf16(u, A.gauge, 2 * mu + (L.fwd ? p : 1 - p), L.fwd ? cb : n, A.g.Vh_pad);
+  const bool flip = mu == 3 && (L.fwd ? x3 == A.g.L[3] - 1 : x3 == 0);
+  L.sgn = flip ? 0x80008000u : 0u;
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const __nv_bfloat162 e = L.fwd ? u[a * 3 + b] : u[b * 3 + a];
+      L.ur[a * 3 + b] = __low2bfloat162(e);
+      L.ui[a * 3 + b] = __high2bfloat162(e);
+    }
+}
+
+// four channels (c0 .. c0+3) of the neighbour n of direction d (0: the site
+// itself), transported with L, written as the A-row columns 8 h .. 8 h + 7
+// of row s (one bf16x2 per complex value, per colour tile)
+template <int C, bool BIN>
+__device__ __forceinline__ void nn_hop4_rows(unsigned char (&sAb)[3][NN_TILE * 16 * 2],
+                                             const NnLayerArgs& A, const NnLinkBf& L, int d,
+                                             int p, int n, int c0, int h, int s, bool live) {
+  __nv_bfloat162 t[12];
+  if (!live) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) t[k] = __floats2bfloat162_rn(0.f, 0.f);
+  } else {
+    __nv_bfloat162 v[12];
+    const char* src = A.in + (d == 0 ? p : 1 - p) * A.in_half;
+    if constexpr (BIN) {
+      nn_load4_bf16<C>(v, src, n, c0);
+    } else {
+      cx<float> f[12];
+      nn_load4<C>(f, src, n, c0);
+#pragma unroll
+      for (int k = 0; k < 12; k++) v[k] = __floats2bfloat162_rn(f[k].r, f[k].i);
+    }
+    if (d == 0) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) t[k] = v[k];
+    } else {
+      const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        __nv_bfloat162 vx[3];
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+          vx[b] = bf2_bits(__byte_perm(bf2_u(v[c * 3 + b]), 0, 0x1032) ^
+                           (L.fwd ? 0x00008000u : 0x80000000u));
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          __nv_bfloat162 w = zero;
+#pragma unroll
+          for (int b = 0; b < 3; b++) {
+            w = __hfma2(L.ur[a * 3 + b], v[c * 3 + b], w);
+            w = __hfma2(L.ui[a * 3 + b], vx[b], w);
+          }
+          t[c * 3 + a] = bf2_bits(bf2_u(w) ^ L.sgn);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+      *(__nv_bfloat162*)(sAb[a] + kmajor_offset(s, 2 * (4 * h + i), 16)) = t[i * 3 + a];
+}
+
+template <int CIN, int COUT, bool BIN, bool BOUT>
+__global__ void __launch_bounds__(NN_TILE, WD_NN_MINB_INF)
+    nn_infer_kernel(const NnLayerArgs A, int ntiles) {
+  static_assert(CIN == 4 || CIN == 8, "4 or 8 input channels");
+  static_assert(COUT == 4 || COUT == 8, "4 or 8 output channels");
+  constexpr int DPC = 16 / (2 * CIN);                  // directions per K = 16 chunk
+  constexpr int NCHUNK = (NN_NDIR + DPC - 1) / DPC;
+  constexpr int NPAD = 16;                             // N of the MMA (2 COUT <= 16)
+  constexpr uint32_t ABUF = NN_TILE * 16 * 2;          // one colour's A chunk, bytes
+  __shared__ __align__(128) unsigned char sA[2][3][ABUF];
+  __shared__ __align__(128) unsigned char sB[NCHUNK][NPAD * 16 * 2];
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t tmem_base;
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int s = tid;  // site of the tile = A row = TMEM lane
+  const Geom& g = A.g;
+  const int tpp = (g.Vh + NN_TILE - 1) / NN_TILE;  // tiles per parity
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 64);
+    tmem_relinquish();
+  }
+  // weights -> BF16 B^T chunks (real form of the complex product), once per CTA
+  for (int e = tid; e < NCHUNK * NPAD * 16; e += NN_TILE) {
+    const int c = e / (NPAD * 16), rem = e - c * NPAD * 16;
+    const int nn = rem / 16, k = rem - nn * 16;
+    const int j = k / (2 * CIN), i = (k / 2) % CIN, ri = k & 1;
+    const int o = nn >> 1, ro = nn & 1;
+    const int d = c * DPC + j;
+    float val = 0.f;
+    if (d < NN_NDIR && o < COUT) {
+      const float wr = A.w[((d * COUT + o) * CIN + i) * 2];
+      const float wi = A.w[((d * COUT + o) * CIN + i) * 2 + 1];
+      // Y.re = Xr Wr - Xi Wi ; Y.im = Xr Wi + Xi Wr
+      val = ro == 0 ? (ri == 0 ? wr : -wi) : (ri == 0 ? wi : wr);
+    }
+    *(__nv_bfloat16*)(sB[c] + kmajor_offset(nn, k, 16)) = __float2bfloat16_rn(val);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t idesc = make_idesc_bf16(NN_TILE, NPAD);
+  bool ok = true;
+  uint32_t G = 0;  // chunks issued by this CTA so far
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int pt = tile / tpp;
+    const int p = A.p0 + pt;
+    const int cb = (tile - pt * tpp) * NN_TILE + s;
+    const bool valid = cb < g.Vh;
+    const bool skip_self = A.zero_in == p, skip_hops = A.zero_in == 1 - p;
+    int nb[NN_NDIR];
+    int x3 = 0;
+    if (valid) nn_nbr(nb, x3, cb, p, g);
+    // a tile whose hops vanish needs the self-term chunk only (the condition
+    // is the same in the whole CTA)
+    const int nch = skip_hops ? 1 : NCHUNK;
+#pragma unroll
+    for (int c = 0; c < NCHUNK; c++) {
+      if (c >= nch) break;
+      const uint32_t buf = G & 1u;
+      if (G >= 2) ok = mbar_wait_bounded(&bar[buf], ((G - 2) >> 1) & 1u, NN_SPIN_LIMIT) && ok;
+      NnLinkBf L;
+      if constexpr (CIN == 8) {
+        // one direction, its link prepared once for both channel halves
+        const int d = c;
+        const bool live = valid && !(d == 0 ? skip_self : skip_hops);
+        if (live && d > 0) nn_link_prep_bf16(L, A, d, p, cb, nb[c], x3);
+        nn_hop4_rows<CIN, BIN>(sA[buf], A, L, d, p, nb[c], 0, 0, s, live);
+        nn_hop4_rows<CIN, BIN>(sA[buf], A, L, d, p, nb[c], 4, 1, s, live);
+      } else {
+        // two directions of all four channels
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int d = 2 * c + h;
+          if (d < NN_NDIR) {
+            const bool live = valid && !(d == 0 ? skip_self : skip_hops);
+            if (live && d > 0) nn_link_prep_bf16(L, A, d, p, cb, nb[d], x3);
+            nn_hop4_rows<CIN, BIN>(sA[buf], A, L, d, p, nb[d], 0, h, s, live);
+          } else {
+            nn_hop4_rows<CIN, BIN>(sA[buf], A, L, 0, p, cb, 0, h, s, false);
+          }
+        }
+      }
+      fence_smem_to_async();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        const uint64_t bd = make_smem_desc(smem_u32(sB[c]), 128, 256);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const uint64_t ad = make_smem_desc(smem_u32(sA[buf][a]), 128, 256);
+          tc_mma_bf16(tbase + (uint32_t)(a * NPAD), ad, bd, idesc, c > 0 ? 1u : 0u);
+        }
+        tc_commit(&bar[buf]);
+      }
+      G++;
+    }
+    // the tile's last commit covers every MMA issued before it
+    ok = mbar_wait_bounded(&bar[(G - 1) & 1u], ((G - 1) >> 1) & 1u, NN_SPIN_LIMIT) && ok;
+    // tcgen05.ld is warp-collective: decide once for the whole CTA
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    if (!ok) break;
+    cx<float> y[COUT * 3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * NPAD), v);
+#pragma unroll
+      for (int o = 0; o < COUT; o++) y[o * 3 + a] = mk<float>(v[2 * o], v[2 * o + 1]);
+    }
+    if (valid) {
+      if constexpr (BOUT) {
+        constexpr int NG = 3 * COUT / 4;
+        int4* q = (int4*)(A.out + p * A.out_half);
+#pragma unroll
+        for (int k = 0; k < NG; k++) {
+          __nv_bfloat162 hv[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+            hv[j] = __floats2bfloat162_rn(y[4 * k + j].r, y[4 * k + j].i);
+          q[sbi(cb, k, NG)] = *reinterpret_cast<const int4*>(hv);
+        }
+      } else {
+        nn_store<COUT>(A.out + p * A.out_half, cb, g.Vh_pad, y);
+      }
+    }
+    // the next tile's first MMA is issued after a __syncthreads that follows
+    // these TMEM reads
+    tc_fence_before();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(A.err, 1);
+    // give MMAs still in flight a second bounded wait before TMEM is freed
+    if (G > 0) mbar_wait_bounded(&bar[(G - 1) & 1u], ((G - 1) >> 1) & 1u, NN_SPIN_LIMIT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 64);
+}
+
 }  // namespace wd
