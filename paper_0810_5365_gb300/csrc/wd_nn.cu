@@ -66,6 +66,10 @@ static cudaError_t launch_layer(const NnLayerArgs& A, int ntiles, cudaStream_t s
 
 // the one-thread-per-site inference kernel, with its residency computed the
 // same way
+// (returns cudaErrorNotReady, launching nothing, when ntiles is below two
+// waves of its CTAs: a 4-warp CTA takes twice as long per tile as the
+// two-thread kernel's 8-warp one, so with one or two tiles per CTA the
+// two-thread kernel is the faster)
 template <int CIN, int COUT, bool BIN, bool BOUT>
 static cudaError_t launch_infer(const NnLayerArgs& A, int ntiles, cudaStream_t st) {
   static int per_sm = 0;
@@ -94,8 +98,8 @@ static cudaError_t launch_infer(const NnLayerArgs& A, int ntiles, cudaStream_t s
     per_sm = n;
   }
   const int cap = num_sms() * per_sm;
-  const int grid = ntiles < cap ? ntiles : cap;
-  nn_infer_kernel<CIN, COUT, BIN, BOUT><<<grid, NN_TILE, 0, st>>>(A, ntiles);
+  if (ntiles < 2 * cap) return cudaErrorNotReady;
+  nn_infer_kernel<CIN, COUT, BIN, BOUT><<<cap, NN_TILE, 0, st>>>(A, ntiles);
   return cudaGetLastError();
 }
 
@@ -515,15 +519,18 @@ static cudaError_t nn_layer_bf16(int cin, int cout, bool bin, bool bout, const G
   A.np = out_parity < 0 ? 2 : 1;
   A.zero_in = zero_in;
   const int ntiles = A.np * ((g.Vh + NN_TILE - 1) / NN_TILE);
-#if WD_NN_INFER1
-  if (cin == 4 && cout == 8 && !bin && bout) return launch_infer<4, 8, false, true>(A, ntiles, st);
-  if (cin == 8 && cout == 8 && bin && bout) return launch_infer<8, 8, true, true>(A, ntiles, st);
-  if (cin == 8 && cout == 4 && bin && !bout) return launch_infer<8, 4, true, false>(A, ntiles, st);
-#else
+  // the one-thread-per-site kernel where the tiles fill two waves of it,
+  // else the two-thread kernel (bit-identical results either way)
+  cudaError_t e = cudaErrorNotReady;
+  if (WD_NN_INFER1) {
+    if (cin == 4 && cout == 8 && !bin && bout) e = launch_infer<4, 8, false, true>(A, ntiles, st);
+    if (cin == 8 && cout == 8 && bin && bout) e = launch_infer<8, 8, true, true>(A, ntiles, st);
+    if (cin == 8 && cout == 4 && bin && !bout) e = launch_infer<8, 4, true, false>(A, ntiles, st);
+  }
+  if (e != cudaErrorNotReady) return e;
   if (cin == 4 && cout == 8 && !bin && bout) return launch_layer<4, 8, false, true>(A, ntiles, st);
   if (cin == 8 && cout == 8 && bin && bout) return launch_layer<8, 8, true, true>(A, ntiles, st);
   if (cin == 8 && cout == 4 && bin && !bout) return launch_layer<8, 4, true, false>(A, ntiles, st);
-#endif
   return cudaErrorInvalidValue;
 }
 

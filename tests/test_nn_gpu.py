@@ -307,6 +307,25 @@ def test_nn_apply_ex_bf16_activations(dims, even):
     assert err < 3e-2, err
 
 
+@pytest.mark.parametrize("even", [False, True])
+def test_nn_apply_ex_bf16_one_thread_per_site_kernel(even):
+    """On 16^3x64 the BF16 layers with at least two waves of tiles run the
+    one-thread-per-site inference kernel (the full-lattice layers here; the
+    even-only last layer of the even block, with half the tiles, runs the
+    two-thread kernel): the same bound against the FP64 network."""
+    dims = (16, 16, 16, 64)
+    Ws, wdev, U, b, g = _net_case(dims, seed=7)
+    par = fields.site_parity(dims)
+    src = b.copy()
+    if even:
+        src[par == 1] = 0
+    got = _apply(W.WD_NN_BF16 | (W.WD_NN_EVEN if even else 0), wdev, b, g, dims)
+    want = nn.network(src, U, Ws, dims)
+    sel = (par == 0) if even else np.ones(len(par), bool)
+    err = np.linalg.norm(got[sel] - want[sel]) / np.linalg.norm(want[sel])
+    assert err < 3e-2, err
+
+
 def test_nn_apply_ex_rejects_unknown_flags():
     dims = (4, 4, 4, 4)
     _, wdev, _, b, g = _net_case(dims)
