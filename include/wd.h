@@ -77,7 +77,9 @@ enum { WD_TEMPORAL_GAUGE = 0x100 };
  * (the TMA engine) while it computes its x and y hops.  Results are
  * bit-identical to the unstaged kernel.  Requires prec = WD_F16, recon = 12,
  * no temporal gauge, norm2 == NULL and L0*L1/2 a multiple of 32; WD_ERR_ARG
- * otherwise.  The wait for the copies is bounded (wd_set_wait_limit); should
+ * otherwise.  Without this bit the CTA-size tuner (wd_dslash_set_block) may
+ * choose the same kernel for such calls when it is the faster one.  The wait
+ * for the copies is bounded (wd_set_wait_limit); should
  * it give up, the kernel writes NaN to the sites of that warp (so any later
  * norm, solve or check of the output fails) instead of hanging, and raises
  * the device's fault flag, which wd_async_status reports. */

@@ -49,8 +49,8 @@ __device__ __forceinline__ void project(const cx<R> (&p)[12], cx<R> (&h)[6]) {
 }
 
 // Expansion of the transported half spinor t back to four spins, scaled by
-// sc and added to acc (sc carries the FP16 site scale and the antiperiodic
-// sign; SC1 marks sc == 1 known at compile time).
+// sc and added to acc (sc carries the antiperiodic sign; SC1 marks sc == 1
+// known at compile time).
 template <int MU, int S, bool SC1, typename R>
 __device__ __forceinline__ void expand_add(cx<R> (&acc)[12], const cx<R> (&t)[6], R sc) {
 #pragma unroll
@@ -169,37 +169,15 @@ __device__ __forceinline__ void su3_mul_f32x2(const cx<float> (&u)[9], const cx<
 }
 #endif
 
-// Load the neighbour spinor and project it: h receives the half spinor, the
-// return value the factor still to apply (the FP16 site scale, else 1).
+// Load the neighbour spinor and project it into the half spinor h (FP64 and
+// FP32 fields; the FP16 hops run their own pipeline, hops_f16).
 template <int P, int MU, int S, typename R, bool COH = false>
-__device__ __forceinline__ R load_project(cx<R> (&h)[6], const void* __restrict__ in, int nb,
-                                          int Vh_pad) {
-  if constexpr (P == WD_F16) {
-    const int4* p = (const int4*)in;
-    const float* scp = (const float*)((const char*)in + (size_t)Vh_pad * 48);
-    __half2 v[12];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      int4 w = ldin<COH>(p + sbi(nb, k, 3));
-      const __half2* q = reinterpret_cast<const __half2*>(&w);
-#pragma unroll
-      for (int j = 0; j < 4; j++) v[4 * k + j] = q[j];
-    }
-    const float scale = ldin<COH>(scp + nb);
-    __half2 hh[6];
-    project_h2<MU, S>(v, hh);
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-      float2 f = __half22float2(hh[k]);
-      h[k] = mk<R>(f.x, f.y);
-    }
-    return scale;
-  } else {
-    cx<R> psi[12];
-    load_spinor<P, R, COH>(psi, in, nb, Vh_pad);
-    project<MU, S>(psi, h);
-    return (R)1;
-  }
+__device__ __forceinline__ void load_project(cx<R> (&h)[6], const void* __restrict__ in, int nb,
+                                             int Vh_pad) {
+  static_assert(P != WD_F16, "FP16 hops: hops_f16");
+  cx<R> psi[12];
+  load_spinor<P, R, COH>(psi, in, nb, Vh_pad);
+  project<MU, S>(psi, h);
 }
 
 // One hop: neighbour site nb (opposite parity), link in `region` at site lcb.
@@ -212,7 +190,7 @@ __device__ __forceinline__ void hop(cx<R> (&acc)[12], const void* __restrict__ i
                                     const void* __restrict__ gauge, int nb, int region, int lcb,
                                     bool flip, int Vh_pad, bool unit = false) {
   cx<R> h[6];
-  R sc = load_project<P, MU, S, R, COH>(h, in, nb, Vh_pad);
+  load_project<P, MU, S, R, COH>(h, in, nb, Vh_pad);
   cx<R> t[6];
   if (MU == 3 && unit) {
 #pragma unroll
@@ -243,10 +221,7 @@ __device__ __forceinline__ void hop(cx<R> (&acc)[12], const void* __restrict__ i
       }
     }
   }
-  if constexpr (P == WD_F16) {
-    if (MU == 3 && flip) sc = -sc;
-    expand_add<MU, S, false>(acc, t, sc);
-  } else if constexpr (MU == 3) {
+  if constexpr (MU == 3) {
     expand_add<MU, S, false>(acc, t, flip ? (R)-1 : (R)1);
   } else {
     expand_add<MU, S, true>(acc, t, (R)1);

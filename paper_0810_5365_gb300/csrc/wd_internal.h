@@ -12,10 +12,10 @@ namespace wd {
 #ifndef WD_DSLASH_BS
 #define WD_DSLASH_BS 128
 #endif
-// Register budgets from a sweep on GB300 (32^3x64): FP32 is fastest with 7
-// resident 128-thread blocks per SM (<= 72 registers), FP16 with 5 (<= 102
-// registers, two hops of loads in flight); FP64 is ALU-bound and gets 3
-// (168 registers, no spills).
+// Register budgets from sweeps on GB300 (32^3x64): FP32 is fastest with 7
+// resident 128-thread blocks per SM (<= 72 registers), FP16 with 6 (<= 80
+// registers, two hops of loads in flight; 5 and 7 are slower); FP64 is
+// bound by its arithmetic pipe and gets 3 (168 registers, no spills).
 #ifndef WD_DSLASH_MINB_F64
 #define WD_DSLASH_MINB_F64 3
 #endif
