@@ -614,7 +614,7 @@ def batch_section(W, torch):
     return out
 
 
-NN_KAPPA = 0.1370     # BASELINE config 5: beyond the critical region of these links
+NN_KAPPA = 0.1370     # the learned-preconditioner workload: beyond the critical region of these links
 
 
 def nn_section(W, torch, U_big):
