@@ -175,7 +175,10 @@ int wd_dslash_dag(void *out, const void *in, const void *gauge, double kappa,
  *     out_p = a * H_{p,1-p} in_{1-p}  [+ bx * x_p]  [+ cy * y_p]
  * (H^+ when dagger != 0).  x and y may be NULL (term dropped) and may alias
  * out; in must not.  If norm2 != NULL (device double*), ||out_p||^2 is
- * written there (FP64, deterministic reduction order).  recon is 12 or 18.
+ * written there: summed in the working precision (FP64 for WD_F64, else FP32)
+ * over each 128-site CTA, then over the CTA partials in FP64 in a fixed order
+ * by a second, one-CTA launch on the same stream (deterministic).  recon is
+ * 12 or 18.
  */
 int wd_dslash_ex(void *out, const void *in, const void *gauge, int parity, int dagger,
                  double a, const void *x, double bx, const void *y, double cy,
@@ -199,16 +202,17 @@ int wd_dslash_ex(void *out, const void *in, const void *gauge, int parity, int d
  * any allocating routine.
  *
  * Its reduction scratch is a fixed array compiled into libwd (16384 FP64
- * partial sums plus a counter, about 128 KB), held by every GPU that loads
- * the library until the process exits.  Limit: V/2 <= 2,097,152 sites
+ * partial sums, 128 KB), held by every GPU that loads the library until the
+ * process exits.  Limit: V/2 <= 2,097,152 sites
  * (16384 CTAs of 128 sites); larger lattices return WD_ERR_SCRATCH before
  * any work is queued.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the one array and it keeps
- * the last call's contents: each call clears the counter itself (an
- * asynchronous memset on the stream) when norm2 != NULL.  Calls that overlap
- * on the GPU (several streams, or several host threads) race on the array.
+ * before any stream capture.  Every call shares the one array: with
+ * norm2 != NULL the hopping kernel leaves one partial sum per CTA there and a
+ * second, one-CTA launch on the same stream adds them into *norm2.  Calls
+ * that overlap on the GPU (several streams, or several host threads) race on
+ * the array.
  */
 int wd_dslash_ex_noalloc(void *out, const void *in, const void *gauge, int parity,
                          int dagger, double a, const void *x, double bx, const void *y,
@@ -234,7 +238,8 @@ int wd_mhat(void *out, const void *in, const void *gauge, void *tmp, double kapp
  * warps per CTA, right-hand sides per thread) comes from the autotuner
  * below.  x may be NULL or alias out;
  * in must not.  If norm2 != NULL (device, nrhs doubles) it receives
- * ||out_r||^2, summed in a fixed order.  1 <= nrhs <= 32.
+ * ||out_r||^2, summed in a fixed order (in the working precision over each
+ * warp's 32 sites, then in FP64).  1 <= nrhs <= 32.
  */
 int wd_dslash_mrhs(void *out, const void *in, const void *gauge, int parity, int dagger,
                    double a, const void *x, double bx, int nrhs, double *norm2,

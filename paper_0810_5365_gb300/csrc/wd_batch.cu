@@ -352,12 +352,12 @@ __global__ void __launch_bounds__(MRHS_BS) batch_update_r(const __grid_constant_
                                                           RedScratch rs, double* rr) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
   (void)rr;
-  __shared__ double red[MRHS_BS / 32];
+  __shared__ R red[MRHS_BS / 32];
   WD_TILE_LOOP
   for (int r = 0; r < pr.nrhs; r++) {
     const int gi = pr.rhs0 + r;
     if (active[gi] == 0) continue;
-    double t = 0.0;
+    R t = (R)0;
     if (valid) {
       const R alpha = (R)(gk[gi] / qq[gi]);
       char* fr = pr.f[0] + r * pr.s[0];
@@ -371,11 +371,11 @@ __global__ void __launch_bounds__(MRHS_BS) batch_update_r(const __grid_constant_
         a[k].i = fma(-alpha, b[k].i, a[k].i);
       }
       store_spinor<P, R>(fr, cb, VP, a);
-      t = site_norm2(a);
+      t = site_norm2<R>(a);
     }
-    double v[1] = {t};
-    block_sum<1, MRHS_BS>(v, red);
-    if (threadIdx.x == 0) rs.partials[(size_t)r * bt.ntiles + tile] = v[0];
+    R v[1] = {t};
+    block_sum<1, MRHS_BS, R>(v, red);
+    if (threadIdx.x == 0) rs.partials[(size_t)r * bt.ntiles + tile] = (double)v[0];
   }
   }
 }
@@ -637,7 +637,7 @@ __device__ __forceinline__ void pi_dslash_phase(const MrhsBatch& bt, int maxr, c
   for (int it = blockIdx.x * NW + threadIdx.y; it < items; it += stride) {
     const PiItem w = pi_item(bt, it, maxr, active);
     const MrhsProblem& pr = bt.p[w.j];
-    double nrm = 0.0;
+    real_of<P> nrm = 0;
     if (w.act && w.cb < pr.g.Vh) nrm = mrhs_site<P, RC, DAG, NORM, COH>(pr, w.cb, w.r);
     if constexpr (NORM) {
 #pragma unroll
@@ -661,7 +661,7 @@ __device__ __forceinline__ void pi_update_r(const BlasBatch& bt, int maxr, const
     const PiItem w = pi_item(bt, it, maxr, active);
     const BlasProblem& pr = bt.p[w.j];
     const int gi = pr.rhs0 + w.r;
-    double t = 0.0;
+    R t = (R)0;
     if (w.act && w.cb < pr.g.Vh) {
       const int VP = pr.g.Vh_pad, cb = w.cb;
       const R alpha = (R)(gk[gi] / qq[gi]);
@@ -676,7 +676,7 @@ __device__ __forceinline__ void pi_update_r(const BlasBatch& bt, int maxr, const
         a[k].i = fma(-alpha, b[k].i, a[k].i);
       }
       store_spinor<P, R>(fr, cb, VP, a);
-      t = site_norm2(a);
+      t = site_norm2<R>(a);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);

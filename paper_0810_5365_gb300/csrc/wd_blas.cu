@@ -68,6 +68,64 @@ cudaError_t device_flag(int** flag, cudaStream_t st) {
   return cudaMemsetAsync(s.dev_flag, 0, sizeof(int), st);
 }
 
+// The cross-block step of block_partials, in the same fixed order as the
+// last block of grid_reduce: CH chains per thread over the partials, combined
+// in order, then a block sum.
+template <int N>
+__global__ void __launch_bounds__(256) sum_blocks_kernel(const double* __restrict__ partials,
+                                                         int nblocks, SumOut out) {
+  constexpr int BS = 256;
+  constexpr int CH = N == 1 ? 8 : 4;
+  __shared__ double smem[N * (BS / 32)];
+  pdl_begin();
+  double part[CH][N];
+#pragma unroll
+  for (int c = 0; c < CH; c++)
+#pragma unroll
+    for (int j = 0; j < N; j++) part[c][j] = 0.0;
+  int b = threadIdx.x;
+  for (; b + (CH - 1) * BS < nblocks; b += CH * BS) {
+#pragma unroll
+    for (int c = 0; c < CH; c++)
+#pragma unroll
+      for (int j = 0; j < N; j++) part[c][j] += __ldcg(partials + (size_t)(b + c * BS) * N + j);
+  }
+  for (; b < nblocks; b += BS) {
+#pragma unroll
+    for (int j = 0; j < N; j++) part[0][j] += __ldcg(partials + (size_t)b * N + j);
+  }
+  double acc[N];
+#pragma unroll
+  for (int j = 0; j < N; j++) {
+    double t = part[0][j];
+#pragma unroll
+    for (int c = 1; c < CH; c++) t += part[c][j];
+    acc[j] = t;
+  }
+  block_sum<N, BS>(acc, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j++)
+      if (out.p[j]) *out.p[j] = acc[j];
+  }
+}
+
+cudaError_t sum_block_partials(int n, const double* partials, int nblocks, SumOut out,
+                               cudaStream_t st) {
+  switch (n) {
+    case 1: return launch_pdl(sum_blocks_kernel<1>, dim3(1), dim3(256), st, partials, nblocks, out);
+    case 2: return launch_pdl(sum_blocks_kernel<2>, dim3(1), dim3(256), st, partials, nblocks, out);
+    case 3: return launch_pdl(sum_blocks_kernel<3>, dim3(1), dim3(256), st, partials, nblocks, out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t sum_block_partials(int n, const double* partials, int nblocks, double* out,
+                               cudaStream_t st) {
+  SumOut o = {{out, n > 1 ? out + 1 : nullptr, n > 2 ? out + 2 : nullptr}};
+  return sum_block_partials(n, partials, nblocks, o, st);
+}
+
 RedScratch scratch() {
   RedScratch r;
   r.partials = state().partials;

@@ -8,6 +8,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <type_traits>
+
 #include "../../include/wd.h"
 
 namespace wd {
@@ -145,26 +147,32 @@ __device__ __forceinline__ cx<R> conj_cross(cx<R> a, cx<R> b, cx<R> c, cx<R> d) 
 
 // ---------------------------------------------------------------------------
 // per-site reductions: the 24 terms of one site are summed in the working
-// precision R; the sum over sites (the global sum) is FP64.  GB300 issues FP64
-// at 1/64 of its FP32 rate, so converting every element to double would cost
-// more than the memory traffic of the kernels that fuse these reductions.
+// precision R.  The kernels that fuse a reduction keep summing in R over the
+// sites of a warp or block, and the per-block (or per-warp) partials are
+// summed in FP64.  GB300 issues FP64 at 1/64 of its FP32 rate: a sum over
+// sites in FP64 (a shuffle tree of DADDs per warp) costs more than the
+// memory traffic of the kernels that fuse these reductions.
 // ---------------------------------------------------------------------------
 
-template <typename R>
-__device__ __forceinline__ double site_norm2(const cx<R> (&v)[12]) {
+// the arithmetic type of a storage precision (FP32 for FP16 storage)
+template <int P>
+using real_of = typename std::conditional<P == WD_F64, double, float>::type;
+
+template <typename T = double, typename R>
+__device__ __forceinline__ T site_norm2(const cx<R> (&v)[12]) {
   R t = (R)0;
 #pragma unroll
   for (int k = 0; k < 12; k++) {
     t = fma(v[k].r, v[k].r, t);
     t = fma(v[k].i, v[k].i, t);
   }
-  return (double)t;
+  return (T)t;
 }
 
 // re + i im += sum_k conj(a_k) b_k
-template <typename R>
-__device__ __forceinline__ void site_cdot(const cx<R> (&a)[12], const cx<R> (&b)[12], double& re,
-                                          double& im) {
+template <typename R, typename T>
+__device__ __forceinline__ void site_cdot(const cx<R> (&a)[12], const cx<R> (&b)[12], T& re,
+                                          T& im) {
   R r = (R)0, i = (R)0;
 #pragma unroll
   for (int k = 0; k < 12; k++) {
@@ -173,8 +181,8 @@ __device__ __forceinline__ void site_cdot(const cx<R> (&a)[12], const cx<R> (&b)
     i = fma(a[k].r, b[k].i, i);
     i = fma(-a[k].i, b[k].r, i);
   }
-  re += (double)r;
-  im += (double)i;
+  re += (T)r;
+  im += (T)i;
 }
 
 // ---------------------------------------------------------------------------
@@ -425,14 +433,15 @@ struct RedScratch {
 };
 
 // Sum over the BS threads of a block (1-, 2- or 3-dimensional; warps are
-// taken in linear thread order).  The total is in every thread of warp 0.
-template <int N, int BS>
-__device__ __forceinline__ void block_sum(double (&v)[N], double* smem /* N * BS/32 */) {
+// taken in linear thread order), in the type T.  The total is in every
+// thread of warp 0.
+template <int N, int BS, typename T = double>
+__device__ __forceinline__ void block_sum(T (&v)[N], T* smem /* N * BS/32 */) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int j = 0; j < N; j++) {
-    double t = v[j];
+    T t = v[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     v[j] = t;
@@ -446,7 +455,7 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* smem /* N * BS
   if (warp == 0) {
 #pragma unroll
     for (int j = 0; j < N; j++) {
-      double t = lane < BS / 32 ? smem[j * (BS / 32) + lane] : 0.0;
+      T t = lane < BS / 32 ? smem[j * (BS / 32) + lane] : (T)0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       v[j] = t;
@@ -454,16 +463,33 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* smem /* N * BS
   }
 }
 
-// Returns true in every thread of the last block; there `tot` holds the grid
-// total in thread 0 (and all threads of warp 0).
-template <int N, int BS>
-__device__ __forceinline__ bool grid_reduce(double (&v)[N], RedScratch rs, double (&tot)[N]) {
-  __shared__ double smem[N * (BS / 32)];
-  __shared__ bool last;
-  block_sum<N, BS>(v, smem);
+// The block's share of a grid sum, without the cross-block step: the block
+// sums v in T and thread 0 stores its N totals as FP64 partials.  A separate
+// launch that follows the kernel in its stream (sum_block_partials) adds the
+// partials in block order.  Unlike grid_reduce, no block waits for an atomic
+// round trip before it exits.
+template <int N, int BS, typename T>
+__device__ __forceinline__ void block_partials(T (&v)[N], double* partials) {
+  __shared__ T smem[N * (BS / 32)];
+  block_sum<N, BS, T>(v, smem);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < N; j++) rs.partials[(size_t)blockIdx.x * N + j] = v[j];
+    for (int j = 0; j < N; j++) partials[(size_t)blockIdx.x * N + j] = (double)v[j];
+  }
+}
+
+// Returns true in every thread of the last block; there `tot` holds the grid
+// total in thread 0 (and all threads of warp 0).  The block sums in T (the
+// kernel's working precision), the block partials in FP64.
+template <int N, int BS, typename T = double>
+__device__ __forceinline__ bool grid_reduce(T (&v)[N], RedScratch rs, double (&tot)[N]) {
+  __shared__ T tsmem[N * (BS / 32)];
+  __shared__ double smem[N * (BS / 32)];
+  __shared__ bool last;
+  block_sum<N, BS, T>(v, tsmem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j++) rs.partials[(size_t)blockIdx.x * N + j] = (double)v[j];
     // one acquire-release arrival: it orders the partials written above
     // before it for the last block, and that block's reads after it
     unsigned t;

@@ -561,9 +561,9 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
   pdl_begin();
   const Geom& g = a.g;
   const int cb = blockIdx.x * BS + threadIdx.x;
-  double red[NRED];
+  R red[NRED];
 #pragma unroll
-  for (int j = 0; j < NRED; j++) red[j] = 0.0;
+  for (int j = 0; j < NRED; j++) red[j] = (R)0;
   if (cb < g.Vh) {
     const int p = a.parity;
     int x0, x1, x2, x3;
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
     }
     if constexpr (RED != RED_NONE) {
       // (for FP16, acc now holds what was stored, after rounding to half)
-      if constexpr (RED == RED_NORM || RED == RED_NORM_DOTX) red[0] = site_norm2(acc);
+      if constexpr (RED == RED_NORM || RED == RED_NORM_DOTX) red[0] = site_norm2<R>(acc);
       if constexpr (RED == RED_NORM_DOTX) {
         cx<R> v[12];
         load_spinor_rw<P, R>(v, a.x, cb, VP);
@@ -664,13 +664,8 @@ __global__ void __launch_bounds__(BS, (DslashMinBlocksBS<P, RED != RED_NONE, BS>
       }
     }
   }
-  if constexpr (RED != RED_NONE) {
-    double tot[NRED];
-    if (grid_reduce<NRED, BS>(red, a.rs, tot) && threadIdx.x == 0) {
-#pragma unroll
-      for (int j = 0; j < NRED; j++) a.norm_out[j] = tot[j];
-    }
-  }
+  // (the launch that follows sums the block partials into norm_out)
+  if constexpr (RED != RED_NONE) block_partials<NRED, BS>(red, a.rs.partials);
 }
 
 // Launch a hopping kernel (see launch_pdl)
@@ -697,8 +692,8 @@ cudaError_t launch_dslash_plain_bs(const DslashArgs& a, int bs, cudaStream_t st)
 }
 
 template <int P, int RC, bool DG, bool TG>
-cudaError_t launch_dslash_red_tg(const DslashArgs& a, dim3 grid, dim3 block, int bs,
-                                 cudaStream_t st) {
+cudaError_t launch_dslash_red_one(const DslashArgs& a, dim3 grid, dim3 block, int bs,
+                                  cudaStream_t st) {
   const int mode = a.norm_out ? a.red_mode : RED_NONE;
   switch (mode) {
     case RED_NONE:
@@ -721,6 +716,16 @@ cudaError_t launch_dslash_red_tg(const DslashArgs& a, dim3 grid, dim3 block, int
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
+}
+
+// a reducing launch is followed by the sum of its block partials
+template <int P, int RC, bool DG, bool TG>
+cudaError_t launch_dslash_red_tg(const DslashArgs& a, dim3 grid, dim3 block, int bs,
+                                 cudaStream_t st) {
+  cudaError_t e = launch_dslash_red_one<P, RC, DG, TG>(a, grid, block, bs, st);
+  if (e != cudaSuccess || !a.norm_out || a.red_mode == RED_NONE) return e;
+  const int nred = a.red_mode == RED_NORM ? 1 : a.red_mode == RED_NORM_DOTX ? 3 : 2;
+  return sum_block_partials(nred, a.rs.partials, (int)grid.x, a.norm_out, st);
 }
 
 template <int P, int RC, bool DG>

@@ -142,6 +142,17 @@ State& state();
 // grow the reduction scratch to hold `doubles` partial sums (not during capture)
 cudaError_t ensure_scratch(size_t doubles);
 RedScratch scratch();
+// out[j] = sum over b < nblocks of partials[b * n + j] (j < n, n = 1, 2 or 3),
+// in block order: the cross-block step of the kernels that leave per-block
+// partials (block_partials); one CTA, launched with launch_pdl.  SumOut: a
+// destination per j (null: not written).
+struct SumOut {
+  double* p[3];
+};
+cudaError_t sum_block_partials(int n, const double* partials, int nblocks, SumOut out,
+                               cudaStream_t st);
+cudaError_t sum_block_partials(int n, const double* partials, int nblocks, double* out,
+                               cudaStream_t st);
 int num_sms();
 
 // grid of the grid-stride BLAS/reduction kernels for n sites

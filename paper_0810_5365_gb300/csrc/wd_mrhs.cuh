@@ -77,7 +77,7 @@ struct MrhsMinBlocks {
 // cy y, returning ||out||^2 at this site when NORM (else 0).  COH: the input
 // field is read with coherent loads (it was written earlier in the launch).
 template <int P, int RC, bool DAG, bool NORM, bool COH = false>
-__device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r) {
+__device__ __forceinline__ real_of<P> mrhs_site(const MrhsProblem& pr, int cb, int r) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
   constexpr int SF = DAG ? -1 : 1;
   constexpr int SB_ = -SF;
@@ -155,8 +155,8 @@ __device__ __forceinline__ double mrhs_site(const MrhsProblem& pr, int cb, int r
     else
       store_spinor<P, R>(out, cb, VP, acc);
   }
-  double nrm = 0.0;
-  if constexpr (NORM) nrm = site_norm2(acc);  // (FP16: acc holds what was stored)
+  R nrm = (R)0;
+  if constexpr (NORM) nrm = site_norm2<R>(acc);  // (FP16: acc holds what was stored)
   return nrm;
 }
 
@@ -175,15 +175,16 @@ __global__ void __launch_bounds__(MRHS_SUB* LANES, (MrhsMinBlocks<P, NORM, LANES
   const MrhsProblem& pr = bt.p[j];
   const int cb = (tile - pr.tile0) * MRHS_BS + q * MRHS_SUB + tx;
   const bool act = r < pr.nrhs && (active == nullptr || active[pr.rhs0 + r] != 0);
-  double nrm = 0.0;
+  real_of<P> nrm = 0;
   if (act && cb < pr.g.Vh) nrm = mrhs_site<P, RC, DAG, NORM>(pr, cb, r);
   if constexpr (NORM) {
-    // one warp = one right-hand side of these 32 sites; the per-(rhs,
-    // sub-tile) partials are summed in a fixed order by sum_partials_kernel
-    // ([local rhs][sub-tile] layout, so that those reads coalesce)
+    // one warp = one right-hand side of these 32 sites, summed in the
+    // working precision; the per-(rhs, sub-tile) partials are FP64, summed
+    // in a fixed order by sum_partials_kernel ([local rhs][sub-tile] layout,
+    // so that those reads coalesce)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    if (tx == 0 && act) rs.partials[(size_t)r * (bt.ntiles * SUBS) + sub] = nrm;
+    if (tx == 0 && act) rs.partials[(size_t)r * (bt.ntiles * SUBS) + sub] = (double)nrm;
   }
 }
 
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(MRHS_SUB* LANES, (Mrhs2MinBlocks<LANES>::value
   const int cb = (tile - pr.tile0) * MRHS_BS + q * MRHS_SUB + tx;
   const bool act0 = r0 < pr.nrhs && (active == nullptr || active[pr.rhs0 + r0] != 0);
   const bool act1 = r1 < pr.nrhs && (active == nullptr || active[pr.rhs0 + r1] != 0);
-  double nrm0 = 0.0, nrm1 = 0.0;
+  float nrm0 = 0.f, nrm1 = 0.f;
   if ((act0 || act1) && cb < pr.g.Vh) {
     const Geom& g = pr.g;
     const int p = pr.parity, qq = 1 - p, VP = g.Vh_pad;
@@ -323,11 +324,11 @@ __global__ void __launch_bounds__(MRHS_SUB* LANES, (Mrhs2MinBlocks<LANES>::value
     hop_pair_f32<RC, 3, SB_, false>(a0, a1, in0, in1, ga, b3, 6 + qq, b3, bflip, VP);
     if (act0) {
       mrhs_epilogue_f32(a0, pr, r0, cb, VP);
-      if constexpr (NORM) nrm0 = site_norm2(a0);
+      if constexpr (NORM) nrm0 = site_norm2<float>(a0);
     }
     if (act1) {
       mrhs_epilogue_f32(a1, pr, r1, cb, VP);
-      if constexpr (NORM) nrm1 = site_norm2(a1);
+      if constexpr (NORM) nrm1 = site_norm2<float>(a1);
     }
   }
   if constexpr (NORM) {
@@ -336,8 +337,8 @@ __global__ void __launch_bounds__(MRHS_SUB* LANES, (Mrhs2MinBlocks<LANES>::value
       nrm0 += __shfl_xor_sync(0xffffffffu, nrm0, o);
       nrm1 += __shfl_xor_sync(0xffffffffu, nrm1, o);
     }
-    if (tx == 0 && act0) rs.partials[(size_t)r0 * (bt.ntiles * SUBS) + sub] = nrm0;
-    if (tx == 0 && act1) rs.partials[(size_t)r1 * (bt.ntiles * SUBS) + sub] = nrm1;
+    if (tx == 0 && act0) rs.partials[(size_t)r0 * (bt.ntiles * SUBS) + sub] = (double)nrm0;
+    if (tx == 0 && act1) rs.partials[(size_t)r1 * (bt.ntiles * SUBS) + sub] = (double)nrm1;
   }
 }
 

@@ -636,9 +636,9 @@ struct PtrList {
 __global__ void __launch_bounds__(256) multi_cdot_kernel(const PtrList vs, int k, const char* w,
                                                          Geom g, size_t half, RedScratch rs,
                                                          double* res) {
-  double acc[2 * GCR_MAXK];
+  float acc[2 * GCR_MAXK];
 #pragma unroll
-  for (int j = 0; j < 2 * GCR_MAXK; j++) acc[j] = 0.0;
+  for (int j = 0; j < 2 * GCR_MAXK; j++) acc[j] = 0.f;
   const long long n = 2LL * g.Vh;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
@@ -698,14 +698,14 @@ __global__ void __launch_bounds__(256) multi_axpy_kernel(const PtrList Ws, const
 // out[0] = ||w||^2, out[1..2] = <w, r>
 __global__ void __launch_bounds__(256) norm_cdot_kernel(const char* w, const char* r, Geom g,
                                                         size_t half, RedScratch rs, double* out) {
-  double acc[3] = {0.0, 0.0, 0.0};
+  float acc[3] = {0.f, 0.f, 0.f};
   const long long n = 2LL * g.Vh;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
     cx<float> a[12], b[12];
     load_spinor_rw<WD_F32, float>(a, w + h * half, cb, g.Vh_pad);
     load_spinor_rw<WD_F32, float>(b, r + h * half, cb, g.Vh_pad);
-    acc[0] += site_norm2(a);
+    acc[0] += site_norm2<float>(a);
     site_cdot(a, b, acc[1], acc[2]);
   }
   double tot[3];
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(256) gcr_update_kernel(char* x, char* r, const
                                                          const char* w, const double* nc, Geom g,
                                                          size_t half, RedScratch rs, double* out) {
   const float ar = (float)(nc[1] / nc[0]), ai = (float)(nc[2] / nc[0]);
-  double acc[1] = {0.0};
+  float acc[1] = {0.f};
   const long long n = 2LL * g.Vh;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(256) gcr_update_kernel(char* x, char* r, const
     }
     store_spinor<WD_F32, float>(x + h * half, cb, g.Vh_pad, xv);
     store_spinor<WD_F32, float>(r + h * half, cb, g.Vh_pad, rv);
-    acc[0] += site_norm2(rv);
+    acc[0] += site_norm2<float>(rv);
   }
   double tot[1];
   if (grid_reduce<1, 256>(acc, rs, tot) && threadIdx.x == 0) out[0] = tot[0];
@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(256) fcg_update_xr(char* x, char* r, const cha
                                                      const char* q, FcgScalars* sc, int kp,
                                                      Geom g, size_t half, int nh, RedScratch rs) {
   const float a = (float)(sc->rho[kp] / (sc->qq[0] + sc->qq[1]));
-  double acc[1] = {0.0};
+  float acc[1] = {0.f};
   const long long n = (long long)nh * g.Vh;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(256) fcg_update_xr(char* x, char* r, const cha
     }
     store_spinor<WD_F32, float>(x + h * half, cb, g.Vh_pad, xv);
     store_spinor<WD_F32, float>(r + h * half, cb, g.Vh_pad, rv);
-    acc[0] += site_norm2(rv);
+    acc[0] += site_norm2<float>(rv);
   }
   double tot[1];
   if (grid_reduce<1, 256>(acc, rs, tot) && threadIdx.x == 0) sc->rr = tot[0];
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(256) fcg_update_xr(char* x, char* r, const cha
 __global__ void __launch_bounds__(256) fcg_dots(const char* s, const char* s_old, const char* z,
                                                 FcgScalars* sc, int slot, Geom g, size_t half,
                                                 int nh, RedScratch rs) {
-  double acc[3] = {0.0, 0.0, 0.0};
+  float acc[3] = {0.f, 0.f, 0.f};
   const long long n = (long long)nh * g.Vh;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
     const int h = (int)(i / g.Vh), cb = (int)(i - (long long)h * g.Vh);
@@ -828,7 +828,7 @@ __global__ void __launch_bounds__(256) fcg_dots(const char* s, const char* s_old
     site_cdot(sv, zv, acc[0], acc[1]);
     if (s_old) {
       load_spinor_rw<WD_F32, float>(sv, s_old + h * half, cb, g.Vh_pad);
-      double im = 0.0;
+      float im = 0.f;
       site_cdot(sv, zv, acc[2], im);
     }
   }

@@ -9,10 +9,10 @@
 //    framework caching allocator that has already reserved the GPU;
 //  * latency-critical loops that must never trigger the device-wide
 //    synchronisation that growing a cudaMalloc'd buffer (cudaFree) implies.
-// For them this entry point allocates nothing: the per-CTA partial sums and
-// the arrival counter of the deterministic reduction live in
-// `g_noalloc_scratch` below, which every GPU that loads the library holds
-// until the process exits.
+// For them this entry point allocates nothing: the per-CTA partial sums of
+// the deterministic reduction (summed by the launch that follows the hopping
+// kernel) live in `g_noalloc_scratch` below, which every GPU that loads the
+// library holds until the process exits.
 #include <cstdint>
 
 #include "wd_internal.h"
@@ -20,11 +20,11 @@
 namespace {
 
 // One partial per 128-site CTA: 16384 partials cover V/2 <= 2,097,152 sites
-// (e.g. 32^3x128).  The extra 256-byte slot at the end holds the counter.
+// (e.g. 32^3x128).
 constexpr int kMaxPartials = 16384;
 constexpr int kMaxDevices = 64;
 
-static __device__ __align__(256) double g_noalloc_scratch[kMaxPartials + 32];
+static __device__ __align__(256) double g_noalloc_scratch[kMaxPartials];
 
 // Device address of g_noalloc_scratch per device, looked up once.  In host
 // code the symbol's name is only a host-side stand-in, never a device address.
@@ -109,15 +109,7 @@ extern "C" int wd_dslash_ex_noalloc(void* out, const void* in, const void* gauge
   }
   RedScratch rs;
   rs.partials = g_scratch_addr[dev];
-  rs.counter = reinterpret_cast<unsigned*>(g_scratch_addr[dev] + kMaxPartials);
-  if (norm2) {
-    // the counter must start at zero; the array keeps whatever the last call left
-    e = cudaMemsetAsync(rs.counter, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) {
-      state().last_cuda_error = (int)e;
-      return WD_ERR_CUDA;
-    }
-  }
+  rs.counter = nullptr;  // (the hopping kernels' reductions use no counter)
   DslashArgs d;
   d.out = out;
   d.in = in;

@@ -52,8 +52,9 @@ template <int P, int BS>
 __global__ void __launch_bounds__(BS) cg_update_r(char* r, const char* __restrict__ q,
                                                   CgScalars* sc, int kp, Geom g, RedScratch rs) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
+  pdl_begin();
   const R alpha = (R)(sc->gamma[kp] / sc->qq);
-  double acc[1] = {0.0};
+  R acc[1] = {(R)0};
   for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
     cx<R> a[12], b[12];
     load_spinor_rw<P, R>(a, r, cb, g.Vh_pad);
@@ -64,10 +65,9 @@ __global__ void __launch_bounds__(BS) cg_update_r(char* r, const char* __restric
       a[k].i = fma(-alpha, b[k].i, a[k].i);
     }
     store_spinor<P, R>(r, cb, g.Vh_pad, a);
-    acc[0] += site_norm2(a);
+    acc[0] += site_norm2<R>(a);
   }
-  double tot[1];
-  if (grid_reduce<1, BS>(acc, rs, tot) && threadIdx.x == 0) sc->rr = tot[0];
+  block_partials<1, BS>(acc, rs.partials);  // summed into sc->rr by the next launch
 }
 
 // x += alpha p ; p = s + beta p ; beta = gamma[1-kp] / gamma[kp]
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(BS) cg_update_xp(char* x, char* p, const char*
                                                    const CgScalars* sc, int kp, Geom g) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
   using RX = typename std::conditional<PX == WD_F64, double, float>::type;
+  pdl_begin();
   const double g0 = sc->gamma[kp];
   const RX alpha = (RX)(g0 / sc->qq);
   const R beta = (R)(sc->gamma[1 - kp] / g0);
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(BS) bicg_update_p(char* p, const char* __restr
                                                     const char* __restrict__ v,
                                                     const CgScalars* sc, int kp, Geom g) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
+  pdl_begin();
   const int kq = 1 - kp;
   double ar, ai, wr, wi, t1r, t1i, t2r, t2i, br, bi;
   zdiv(sc->rho[kq][0], sc->rho[kq][1], sc->rv[kq][0], sc->rv[kq][1], ar, ai);   // alpha_old
@@ -162,6 +164,7 @@ __global__ void __launch_bounds__(BS) bicg_update_s(char* s, const char* __restr
                                                     const char* __restrict__ v,
                                                     const CgScalars* sc, int kp, Geom g) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
+  pdl_begin();
   double ar, ai;
   zdiv(sc->rho[kp][0], sc->rho[kp][1], sc->rv[kp][0], sc->rv[kp][1], ar, ai);
   const R Ar = (R)ar, Ai = (R)ai;
@@ -187,12 +190,13 @@ __global__ void __launch_bounds__(BS) bicg_update_xr(char* x, char* r, const cha
                                                      int kp, Geom g, RedScratch rs) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
   using RX = typename std::conditional<PX == WD_F64, double, float>::type;
+  pdl_begin();
   double ar, ai, wr, wi;
   zdiv(sc->rho[kp][0], sc->rho[kp][1], sc->rv[kp][0], sc->rv[kp][1], ar, ai);
   zdiv(sc->tts[kp][1], sc->tts[kp][2], sc->tts[kp][0], 0.0, wr, wi);
   const RX Ar = (RX)ar, Ai = (RX)ai, Wxr = (RX)wr, Wxi = (RX)wi;
   const R Wr = (R)wr, Wi = (R)wi;
-  double acc[3] = {0.0, 0.0, 0.0};
+  R acc[3] = {(R)0, (R)0, (R)0};
   for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
     cx<R> pv[12], sv[12], tv[12], zv[12];
     cx<RX> xv[12];
@@ -213,14 +217,10 @@ __global__ void __launch_bounds__(BS) bicg_update_xr(char* x, char* r, const cha
     if constexpr (P == WD_F16) load_spinor_rw<P, R>(sv, r, cb, g.Vh_pad);  // what was stored
     load_spinor_rw<P, R>(zv, r0, cb, g.Vh_pad);
     site_cdot(zv, sv, acc[0], acc[1]);
-    acc[2] += site_norm2(sv);
+    acc[2] += site_norm2<R>(sv);
   }
-  double tot[3];
-  if (grid_reduce<3, BS>(acc, rs, tot) && threadIdx.x == 0) {
-    sc->rho[1 - kp][0] = tot[0];
-    sc->rho[1 - kp][1] = tot[1];
-    sc->rr = tot[2];
-  }
+  // summed into rho[1 - kp] and rr by the next launch
+  block_partials<3, BS>(acc, rs.partials);
 }
 
 // restart: rho[0] = ||r||^2 (r0 = r), and the "previous" slot set so that the
@@ -350,8 +350,9 @@ static int ws_ensure(const int dims[4], int sprec, int srecon, int orecon) {
   WD_CK(cudaMemset(w.sc, 0, sizeof(CgScalars)));
   WD_CK(cudaMallocHost(&w.sc_host, sizeof(CgScalars)));
   WD_CK(cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
-  // the largest reduction grid used below is a dslash over Vh sites
-  WD_CK(ensure_scratch((size_t)((g.Vh + 127) / 128) * 2 + 1024));
+  // the largest reduction grid used below is a dslash over Vh sites, with up
+  // to three sums (BiCGstab's ||t||^2, <t, s>)
+  WD_CK(ensure_scratch((size_t)((g.Vh + 127) / 128) * 3 + 1024));
   return WD_OK;
 }
 
@@ -422,13 +423,14 @@ cudaError_t iteration_t(Ctx& c, int kp, cudaStream_t st) {
   cudaError_t e = mhat_sloppy(c, w.q, w.p, 0, &w.sc->qq, st);
   if (e != cudaSuccess) return e;
   int grid = blas_grid(g.Vh, 256);
-  cg_update_r<P, 256><<<grid, 256, 0, st>>>((char*)w.r, (const char*)w.q, w.sc, kp, g, scratch());
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(cg_update_r<P, 256>, dim3(grid), dim3(256), st, (char*)w.r,
+                      (const char*)w.q, w.sc, kp, g, scratch())))
+    return e;
+  if ((e = sum_block_partials(1, scratch().partials, grid, &w.sc->rr, st))) return e;
   e = mhat_sloppy(c, w.s, w.r, 1, &w.sc->gamma[1 - kp], st);
   if (e != cudaSuccess) return e;
-  cg_update_xp<P, PX, 256><<<grid, 256, 0, st>>>((char*)w.xs, (char*)w.p, (const char*)w.s, w.sc,
-                                                  kp, g);
-  return cudaGetLastError();
+  return launch_pdl(cg_update_xp<P, PX, 256>, dim3(grid), dim3(256), st, (char*)w.xs, (char*)w.p,
+                    (const char*)w.s, (const CgScalars*)w.sc, kp, g);
 }
 
 // one BiCGstab iteration on A = Mhat (sloppy)
@@ -439,9 +441,9 @@ cudaError_t iteration_bicg_t(Ctx& c, int kp, cudaStream_t st) {
   const double k2 = c.kappa * c.kappa;
   const int grid = blas_grid(g.Vh, 256);
   cudaError_t e;
-  bicg_update_p<P, 256><<<grid, 256, 0, st>>>((char*)w.p, (const char*)w.r, (const char*)w.q,
-                                               w.sc, kp, g);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(bicg_update_p<P, 256>, dim3(grid), dim3(256), st, (char*)w.p,
+                      (const char*)w.r, (const char*)w.q, (const CgScalars*)w.sc, kp, g)))
+    return e;
   // v = A p with <r0, v>
   if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.ts, w.p, WD_ODD, 0, 1.0, nullptr, 0, nullptr, 0,
                nullptr, st)))
@@ -449,9 +451,9 @@ cudaError_t iteration_bicg_t(Ctx& c, int kp, cudaStream_t st) {
   if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.q, w.ts, WD_EVEN, 0, -k2, w.p, 1.0, nullptr, 0,
                &w.sc->rv[kp][0], st, RED_DOTZ, w.r0)))
     return e;
-  bicg_update_s<P, 256><<<grid, 256, 0, st>>>((char*)w.s, (const char*)w.r, (const char*)w.q,
-                                               w.sc, kp, g);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(bicg_update_s<P, 256>, dim3(grid), dim3(256), st, (char*)w.s,
+                      (const char*)w.r, (const char*)w.q, (const CgScalars*)w.sc, kp, g)))
+    return e;
   // t = A s with ||t||^2, <t, s>
   if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.ts, w.s, WD_ODD, 0, 1.0, nullptr, 0, nullptr, 0,
                nullptr, st)))
@@ -459,10 +461,12 @@ cudaError_t iteration_bicg_t(Ctx& c, int kp, cudaStream_t st) {
   if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.t, w.ts, WD_EVEN, 0, -k2, w.s, 1.0, nullptr, 0,
                &w.sc->tts[kp][0], st, RED_NORM_DOTX)))
     return e;
-  bicg_update_xr<P, PX, 256><<<grid, 256, 0, st>>>((char*)w.xs, (char*)w.r, (const char*)w.p,
-                                                   (const char*)w.s, (const char*)w.t,
-                                                   (const char*)w.r0, w.sc, kp, g, scratch());
-  return cudaGetLastError();
+  if ((e = launch_pdl(bicg_update_xr<P, PX, 256>, dim3(grid), dim3(256), st, (char*)w.xs,
+                      (char*)w.r, (const char*)w.p, (const char*)w.s, (const char*)w.t,
+                      (const char*)w.r0, w.sc, kp, g, scratch())))
+    return e;
+  SumOut o = {{&w.sc->rho[1 - kp][0], &w.sc->rho[1 - kp][1], &w.sc->rr}};
+  return sum_block_partials(3, scratch().partials, grid, o, st);
 }
 
 cudaError_t iteration(Ctx& c, int kp, cudaStream_t st) {
