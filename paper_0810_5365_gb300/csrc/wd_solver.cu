@@ -47,6 +47,74 @@ __host__ __device__ __forceinline__ void zdiv(double ar, double ai, double br, d
   ci = (ai * br - ar * bi) / d;
 }
 
+// One site of a packed field as it sits in memory (the format load_spinor_rw
+// reads), so that a kernel can issue the loads of its next site before it
+// computes the current one.
+template <int P>
+struct RawSite;
+template <>
+struct RawSite<WD_F16> {
+  int4 v[3];
+  float s;
+};
+template <>
+struct RawSite<WD_F32> {
+  float4 v[6];
+};
+template <>
+struct RawSite<WD_F64> {
+  double2 v[12];
+};
+
+template <int P>
+__device__ __forceinline__ void load_raw(RawSite<P>& o, const void* base, int cb, int Vh_pad) {
+  if constexpr (P == WD_F16) {
+    const int4* p = (const int4*)base;
+#pragma unroll
+    for (int k = 0; k < 3; k++) o.v[k] = p[sbi(cb, k, 3)];
+    o.s = ((const float*)((const char*)base + (size_t)Vh_pad * 48))[cb];
+  } else if constexpr (P == WD_F32) {
+    const float4* p = (const float4*)base;
+#pragma unroll
+    for (int k = 0; k < 6; k++) o.v[k] = p[sbi(cb, k, 6)];
+  } else {
+    const double2* p = (const double2*)base;
+#pragma unroll
+    for (int k = 0; k < 12; k++) o.v[k] = p[sbi(cb, k, 12)];
+  }
+}
+
+// the values of a raw site, with the arithmetic of load_spinor_rw
+template <int P, typename R>
+__device__ __forceinline__ void unpack_raw(cx<R> (&s)[12], const RawSite<P>& o) {
+  if constexpr (P == WD_F16) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const __half2* h = reinterpret_cast<const __half2*>(&o.v[k]);
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const float2 f = __half22float2(h[j]);
+        s[4 * k + j] = mk<R>((R)(f.x * o.s), (R)(f.y * o.s));
+      }
+    }
+  } else if constexpr (P == WD_F32) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      s[2 * k] = mk<R>((R)o.v[k].x, (R)o.v[k].y);
+      s[2 * k + 1] = mk<R>((R)o.v[k].z, (R)o.v[k].w);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; k++) s[k] = mk<R>((R)o.v[k].x, (R)o.v[k].y);
+  }
+}
+
+// The two CG vector updates stream a few fields once, about 10-20 us per
+// call on 24^3x48.  They run on a grid of resident CTAs only (update_grid)
+// and each thread loads its next site before it computes the current one,
+// so that the load latency is paid about once per thread instead of once
+// per CTA generation.
+
 // r -= alpha q ; rr = ||r||^2 ; alpha = gamma[kp] / qq
 template <int P, int BS>
 __global__ void __launch_bounds__(BS) cg_update_r(char* r, const char* __restrict__ q,
@@ -55,37 +123,70 @@ __global__ void __launch_bounds__(BS) cg_update_r(char* r, const char* __restric
   pdl_begin();
   const R alpha = (R)(sc->gamma[kp] / sc->qq);
   R acc[1] = {(R)0};
-  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+  const int stride = gridDim.x * BS, VP = g.Vh_pad;
+  int cb = blockIdx.x * BS + threadIdx.x;
+  RawSite<P> ra, rb;
+  if (cb < g.Vh) {
+    load_raw<P>(ra, r, cb, VP);
+    load_raw<P>(rb, q, cb, VP);
+  }
+  for (; cb < g.Vh; cb += stride) {
+    const int nx = cb + stride;
+    RawSite<P> na, nb;
+    if (nx < g.Vh) {
+      load_raw<P>(na, r, nx, VP);
+      load_raw<P>(nb, q, nx, VP);
+    }
     cx<R> a[12], b[12];
-    load_spinor_rw<P, R>(a, r, cb, g.Vh_pad);
-    load_spinor_rw<P, R>(b, q, cb, g.Vh_pad);
+    unpack_raw<P, R>(a, ra);
+    unpack_raw<P, R>(b, rb);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
       a[k].r = fma(-alpha, b[k].r, a[k].r);
       a[k].i = fma(-alpha, b[k].i, a[k].i);
     }
-    store_spinor<P, R>(r, cb, g.Vh_pad, a);
+    store_spinor<P, R>(r, cb, VP, a);
     acc[0] += site_norm2<R>(a);
+    ra = na;
+    rb = nb;
   }
   block_partials<1, BS>(acc, rs.partials);  // summed into sc->rr by the next launch
 }
 
 // x += alpha p ; p = s + beta p ; beta = gamma[1-kp] / gamma[kp]
 template <int P, int PX, int BS>
-__global__ void __launch_bounds__(BS) cg_update_xp(char* x, char* p, const char* __restrict__ s,
-                                                   const CgScalars* sc, int kp, Geom g) {
+__global__ void __launch_bounds__(BS, (P == WD_F16 ? 2 : 1))
+    cg_update_xp(char* x, char* p, const char* __restrict__ s, const CgScalars* sc, int kp,
+                 Geom g) {
   using R = typename std::conditional<P == WD_F64, double, float>::type;
   using RX = typename std::conditional<PX == WD_F64, double, float>::type;
   pdl_begin();
   const double g0 = sc->gamma[kp];
   const RX alpha = (RX)(g0 / sc->qq);
   const R beta = (R)(sc->gamma[1 - kp] / g0);
-  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+  const int stride = gridDim.x * BS, VP = g.Vh_pad;
+  int cb = blockIdx.x * BS + threadIdx.x;
+  RawSite<P> rp, rsv;
+  RawSite<PX> rx;
+  if (cb < g.Vh) {
+    load_raw<P>(rp, p, cb, VP);
+    load_raw<P>(rsv, s, cb, VP);
+    load_raw<PX>(rx, x, cb, VP);
+  }
+  for (; cb < g.Vh; cb += stride) {
+    const int nx = cb + stride;
+    RawSite<P> np, ns;
+    RawSite<PX> nxr;
+    if (nx < g.Vh) {
+      load_raw<P>(np, p, nx, VP);
+      load_raw<P>(ns, s, nx, VP);
+      load_raw<PX>(nxr, x, nx, VP);
+    }
     cx<R> pv[12], sv[12];
     cx<RX> xv[12];
-    load_spinor_rw<P, R>(pv, p, cb, g.Vh_pad);
-    load_spinor_rw<P, R>(sv, s, cb, g.Vh_pad);
-    load_spinor_rw<PX, RX>(xv, x, cb, g.Vh_pad);
+    unpack_raw<P, R>(pv, rp);
+    unpack_raw<P, R>(sv, rsv);
+    unpack_raw<PX, RX>(xv, rx);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
       xv[k].r = fma(alpha, (RX)pv[k].r, xv[k].r);
@@ -93,9 +194,31 @@ __global__ void __launch_bounds__(BS) cg_update_xp(char* x, char* p, const char*
       pv[k].r = fma(beta, pv[k].r, sv[k].r);
       pv[k].i = fma(beta, pv[k].i, sv[k].i);
     }
-    store_spinor<PX, RX>(x, cb, g.Vh_pad, xv);
-    store_spinor<P, R>(p, cb, g.Vh_pad, pv);
+    store_spinor<PX, RX>(x, cb, VP, xv);
+    store_spinor<P, R>(p, cb, VP, pv);
+    rp = np;
+    rsv = ns;
+    rx = nxr;
   }
+}
+
+// The grid of an update kernel: as many CTAs of 256 threads as are resident
+// at once (the occupancy query), at most one per 256 sites.
+template <typename K>
+static int resident_grid(K kernel, int vh) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const long long need = (vh + 255) / 256;
+  const long long cap = (long long)per_sm * num_sms();
+  return (int)(need < cap ? need : cap);
+}
+
+template <int P, int PX>
+static void update_grids_t(int vh, int& gr, int& gxp) {
+  gr = resident_grid(cg_update_r<P, 256>, vh);
+  gxp = resident_grid(cg_update_xp<P, PX, 256>, vh);
 }
 
 // x64 += xs ; xs = 0
@@ -268,6 +391,7 @@ struct Workspace {
   double* gf_spinor = nullptr;     // rotated right-hand side (canonical)
   CgScalars* sc = nullptr;
   CgScalars* sc_host = nullptr;    // pinned
+  int grid_r = 1, grid_xp = 1;     // grids of cg_update_r / cg_update_xp
   cudaStream_t cap = nullptr;      // private capture stream
   // the instantiated iteration graph of the last solve, reused by the next
   // solve on this workspace with the same key (its kernels hold workspace
@@ -353,6 +477,11 @@ static int ws_ensure(const int dims[4], int sprec, int srecon, int orecon) {
   // the largest reduction grid used below is a dslash over Vh sites, with up
   // to three sums (BiCGstab's ||t||^2, <t, s>)
   WD_CK(ensure_scratch((size_t)((g.Vh + 127) / 128) * 3 + 1024));
+  switch (sprec) {
+    case WD_F64: update_grids_t<WD_F64, WD_F64>(g.Vh, w.grid_r, w.grid_xp); break;
+    case WD_F32: update_grids_t<WD_F32, WD_F32>(g.Vh, w.grid_r, w.grid_xp); break;
+    default: update_grids_t<WD_F16, WD_F32>(g.Vh, w.grid_r, w.grid_xp); break;
+  }
   return WD_OK;
 }
 
@@ -422,15 +551,14 @@ cudaError_t iteration_t(Ctx& c, int kp, cudaStream_t st) {
   const Geom& g = w.g;
   cudaError_t e = mhat_sloppy(c, w.q, w.p, 0, &w.sc->qq, st);
   if (e != cudaSuccess) return e;
-  int grid = blas_grid(g.Vh, 256);
-  if ((e = launch_pdl(cg_update_r<P, 256>, dim3(grid), dim3(256), st, (char*)w.r,
+  if ((e = launch_pdl(cg_update_r<P, 256>, dim3(w.grid_r), dim3(256), st, (char*)w.r,
                       (const char*)w.q, w.sc, kp, g, scratch())))
     return e;
-  if ((e = sum_block_partials(1, scratch().partials, grid, &w.sc->rr, st))) return e;
+  if ((e = sum_block_partials(1, scratch().partials, w.grid_r, &w.sc->rr, st))) return e;
   e = mhat_sloppy(c, w.s, w.r, 1, &w.sc->gamma[1 - kp], st);
   if (e != cudaSuccess) return e;
-  return launch_pdl(cg_update_xp<P, PX, 256>, dim3(grid), dim3(256), st, (char*)w.xs, (char*)w.p,
-                    (const char*)w.s, (const CgScalars*)w.sc, kp, g);
+  return launch_pdl(cg_update_xp<P, PX, 256>, dim3(w.grid_xp), dim3(256), st, (char*)w.xs,
+                    (char*)w.p, (const char*)w.s, (const CgScalars*)w.sc, kp, g);
 }
 
 // one BiCGstab iteration on A = Mhat (sloppy)
