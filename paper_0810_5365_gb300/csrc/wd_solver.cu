@@ -109,8 +109,8 @@ __device__ __forceinline__ void unpack_raw(cx<R> (&s)[12], const RawSite<P>& o) 
   }
 }
 
-// The two CG vector updates stream a few fields once, about 10-20 us per
-// call on 24^3x48.  They run on a grid of resident CTAs only (update_grid)
+// The CG vector updates (and BiCGstab's p and s updates below) stream a few
+// fields once, about 10-20 us per call on 24^3x48.  They run on a grid of resident CTAs only (update_grid)
 // and each thread loads its next site before it computes the current one,
 // so that the load latency is paid about once per thread instead of once
 // per CTA generation.
@@ -215,11 +215,6 @@ static int resident_grid(K kernel, int vh) {
   return (int)(need < cap ? need : cap);
 }
 
-template <int P, int PX>
-static void update_grids_t(int vh, int& gr, int& gxp) {
-  gr = resident_grid(cg_update_r<P, 256>, vh);
-  gxp = resident_grid(cg_update_xp<P, PX, 256>, vh);
-}
 
 // x64 += xs ; xs = 0
 template <int PX, int BS>
@@ -264,11 +259,27 @@ __global__ void __launch_bounds__(BS) bicg_update_p(char* p, const char* __restr
   br = t1r * t2r - t1i * t2i;
   bi = t1r * t2i + t1i * t2r;
   const R Br = (R)br, Bi = (R)bi, Wr = (R)wr, Wi = (R)wi;
-  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+  // resident grid, next site's loads first (as in cg_update_xp)
+  const int stride = gridDim.x * BS, VP = g.Vh_pad;
+  int cb = blockIdx.x * BS + threadIdx.x;
+  RawSite<P> rp, rr, rv;
+  if (cb < g.Vh) {
+    load_raw<P>(rp, p, cb, VP);
+    load_raw<P>(rr, r, cb, VP);
+    load_raw<P>(rv, v, cb, VP);
+  }
+  for (; cb < g.Vh; cb += stride) {
+    const int nx = cb + stride;
+    RawSite<P> np, nr, nv;
+    if (nx < g.Vh) {
+      load_raw<P>(np, p, nx, VP);
+      load_raw<P>(nr, r, nx, VP);
+      load_raw<P>(nv, v, nx, VP);
+    }
     cx<R> pv[12], rv_[12], vv[12];
-    load_spinor_rw<P, R>(pv, p, cb, g.Vh_pad);
-    load_spinor_rw<P, R>(rv_, r, cb, g.Vh_pad);
-    load_spinor_rw<P, R>(vv, v, cb, g.Vh_pad);
+    unpack_raw<P, R>(pv, rp);
+    unpack_raw<P, R>(rv_, rr);
+    unpack_raw<P, R>(vv, rv);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
       // u = p - omega v
@@ -277,7 +288,10 @@ __global__ void __launch_bounds__(BS) bicg_update_p(char* p, const char* __restr
       pv[k].r = rv_[k].r + (Br * ur - Bi * ui);
       pv[k].i = rv_[k].i + (Br * ui + Bi * ur);
     }
-    store_spinor<P, R>(p, cb, g.Vh_pad, pv);
+    store_spinor<P, R>(p, cb, VP, pv);
+    rp = np;
+    rr = nr;
+    rv = nv;
   }
 }
 
@@ -291,16 +305,32 @@ __global__ void __launch_bounds__(BS) bicg_update_s(char* s, const char* __restr
   double ar, ai;
   zdiv(sc->rho[kp][0], sc->rho[kp][1], sc->rv[kp][0], sc->rv[kp][1], ar, ai);
   const R Ar = (R)ar, Ai = (R)ai;
-  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+  // resident grid, next site's loads first (as in cg_update_r)
+  const int stride = gridDim.x * BS, VP = g.Vh_pad;
+  int cb = blockIdx.x * BS + threadIdx.x;
+  RawSite<P> rr, rv;
+  if (cb < g.Vh) {
+    load_raw<P>(rr, r, cb, VP);
+    load_raw<P>(rv, v, cb, VP);
+  }
+  for (; cb < g.Vh; cb += stride) {
+    const int nx = cb + stride;
+    RawSite<P> nr, nv;
+    if (nx < g.Vh) {
+      load_raw<P>(nr, r, nx, VP);
+      load_raw<P>(nv, v, nx, VP);
+    }
     cx<R> rv_[12], vv[12];
-    load_spinor_rw<P, R>(rv_, r, cb, g.Vh_pad);
-    load_spinor_rw<P, R>(vv, v, cb, g.Vh_pad);
+    unpack_raw<P, R>(rv_, rr);
+    unpack_raw<P, R>(vv, rv);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
       rv_[k].r -= Ar * vv[k].r - Ai * vv[k].i;
       rv_[k].i -= Ar * vv[k].i + Ai * vv[k].r;
     }
-    store_spinor<P, R>(s, cb, g.Vh_pad, rv_);
+    store_spinor<P, R>(s, cb, VP, rv_);
+    rr = nr;
+    rv = nv;
   }
 }
 
@@ -364,6 +394,14 @@ __global__ void bicg_restart_scalars(CgScalars* sc) {
 // workspace
 // ---------------------------------------------------------------------------
 
+template <int P, int PX>
+static void update_grids_t(int vh, int (&grid)[4]) {
+  grid[0] = resident_grid(cg_update_r<P, 256>, vh);
+  grid[1] = resident_grid(cg_update_xp<P, PX, 256>, vh);
+  grid[2] = resident_grid(bicg_update_p<P, 256>, vh);
+  grid[3] = resident_grid(bicg_update_s<P, 256>, vh);
+}
+
 struct Workspace {
   int dims[4] = {0, 0, 0, 0};
   int sprec = -1, srecon = 0, orecon = 0;
@@ -391,7 +429,8 @@ struct Workspace {
   double* gf_spinor = nullptr;     // rotated right-hand side (canonical)
   CgScalars* sc = nullptr;
   CgScalars* sc_host = nullptr;    // pinned
-  int grid_r = 1, grid_xp = 1;     // grids of cg_update_r / cg_update_xp
+  // grids of cg_update_r, cg_update_xp, bicg_update_p, bicg_update_s
+  int upd_grid[4] = {1, 1, 1, 1};
   cudaStream_t cap = nullptr;      // private capture stream
   // the instantiated iteration graph of the last solve, reused by the next
   // solve on this workspace with the same key (its kernels hold workspace
@@ -478,9 +517,9 @@ static int ws_ensure(const int dims[4], int sprec, int srecon, int orecon) {
   // to three sums (BiCGstab's ||t||^2, <t, s>)
   WD_CK(ensure_scratch((size_t)((g.Vh + 127) / 128) * 3 + 1024));
   switch (sprec) {
-    case WD_F64: update_grids_t<WD_F64, WD_F64>(g.Vh, w.grid_r, w.grid_xp); break;
-    case WD_F32: update_grids_t<WD_F32, WD_F32>(g.Vh, w.grid_r, w.grid_xp); break;
-    default: update_grids_t<WD_F16, WD_F32>(g.Vh, w.grid_r, w.grid_xp); break;
+    case WD_F64: update_grids_t<WD_F64, WD_F64>(g.Vh, w.upd_grid); break;
+    case WD_F32: update_grids_t<WD_F32, WD_F32>(g.Vh, w.upd_grid); break;
+    default: update_grids_t<WD_F16, WD_F32>(g.Vh, w.upd_grid); break;
   }
   return WD_OK;
 }
@@ -551,13 +590,13 @@ cudaError_t iteration_t(Ctx& c, int kp, cudaStream_t st) {
   const Geom& g = w.g;
   cudaError_t e = mhat_sloppy(c, w.q, w.p, 0, &w.sc->qq, st);
   if (e != cudaSuccess) return e;
-  if ((e = launch_pdl(cg_update_r<P, 256>, dim3(w.grid_r), dim3(256), st, (char*)w.r,
+  if ((e = launch_pdl(cg_update_r<P, 256>, dim3(w.upd_grid[0]), dim3(256), st, (char*)w.r,
                       (const char*)w.q, w.sc, kp, g, scratch())))
     return e;
-  if ((e = sum_block_partials(1, scratch().partials, w.grid_r, &w.sc->rr, st))) return e;
+  if ((e = sum_block_partials(1, scratch().partials, w.upd_grid[0], &w.sc->rr, st))) return e;
   e = mhat_sloppy(c, w.s, w.r, 1, &w.sc->gamma[1 - kp], st);
   if (e != cudaSuccess) return e;
-  return launch_pdl(cg_update_xp<P, PX, 256>, dim3(w.grid_xp), dim3(256), st, (char*)w.xs,
+  return launch_pdl(cg_update_xp<P, PX, 256>, dim3(w.upd_grid[1]), dim3(256), st, (char*)w.xs,
                     (char*)w.p, (const char*)w.s, (const CgScalars*)w.sc, kp, g);
 }
 
@@ -569,7 +608,7 @@ cudaError_t iteration_bicg_t(Ctx& c, int kp, cudaStream_t st) {
   const double k2 = c.kappa * c.kappa;
   const int grid = blas_grid(g.Vh, 256);
   cudaError_t e;
-  if ((e = launch_pdl(bicg_update_p<P, 256>, dim3(grid), dim3(256), st, (char*)w.p,
+  if ((e = launch_pdl(bicg_update_p<P, 256>, dim3(w.upd_grid[2]), dim3(256), st, (char*)w.p,
                       (const char*)w.r, (const char*)w.q, (const CgScalars*)w.sc, kp, g)))
     return e;
   // v = A p with <r0, v>
@@ -579,7 +618,7 @@ cudaError_t iteration_bicg_t(Ctx& c, int kp, cudaStream_t st) {
   if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.q, w.ts, WD_EVEN, 0, -k2, w.p, 1.0, nullptr, 0,
                &w.sc->rv[kp][0], st, RED_DOTZ, w.r0)))
     return e;
-  if ((e = launch_pdl(bicg_update_s<P, 256>, dim3(grid), dim3(256), st, (char*)w.s,
+  if ((e = launch_pdl(bicg_update_s<P, 256>, dim3(w.upd_grid[3]), dim3(256), st, (char*)w.s,
                       (const char*)w.r, (const char*)w.q, (const CgScalars*)w.sc, kp, g)))
     return e;
   // t = A s with ||t||^2, <t, s>
