@@ -350,27 +350,83 @@ __global__ void __launch_bounds__(BS) bicg_update_xr(char* x, char* r, const cha
   const RX Ar = (RX)ar, Ai = (RX)ai, Wxr = (RX)wr, Wxi = (RX)wi;
   const R Wr = (R)wr, Wi = (R)wi;
   R acc[3] = {(R)0, (R)0, (R)0};
-  for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
-    cx<R> pv[12], sv[12], tv[12], zv[12];
-    cx<RX> xv[12];
-    load_spinor_rw<P, R>(pv, p, cb, g.Vh_pad);
-    load_spinor_rw<P, R>(sv, s, cb, g.Vh_pad);
-    load_spinor_rw<P, R>(tv, t, cb, g.Vh_pad);
-    load_spinor_rw<PX, RX>(xv, x, cb, g.Vh_pad);
+  if constexpr (P == WD_F64) {
+    // (FP64: five prefetched sites do not fit the register file; plain loop)
+    for (int cb = blockIdx.x * BS + threadIdx.x; cb < g.Vh; cb += gridDim.x * BS) {
+      cx<R> pv[12], sv[12], tv[12], zv[12];
+      cx<RX> xv[12];
+      load_spinor_rw<P, R>(pv, p, cb, g.Vh_pad);
+      load_spinor_rw<P, R>(sv, s, cb, g.Vh_pad);
+      load_spinor_rw<P, R>(tv, t, cb, g.Vh_pad);
+      load_spinor_rw<PX, RX>(xv, x, cb, g.Vh_pad);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      const RX pr = (RX)pv[k].r, pi = (RX)pv[k].i, sr = (RX)sv[k].r, si = (RX)sv[k].i;
-      xv[k].r += Ar * pr - Ai * pi + Wxr * sr - Wxi * si;
-      xv[k].i += Ar * pi + Ai * pr + Wxr * si + Wxi * sr;
-      sv[k].r -= Wr * tv[k].r - Wi * tv[k].i;
-      sv[k].i -= Wr * tv[k].i + Wi * tv[k].r;
+      for (int k = 0; k < 12; k++) {
+        const RX pr = (RX)pv[k].r, pi = (RX)pv[k].i, sr = (RX)sv[k].r, si = (RX)sv[k].i;
+        xv[k].r += Ar * pr - Ai * pi + Wxr * sr - Wxi * si;
+        xv[k].i += Ar * pi + Ai * pr + Wxr * si + Wxi * sr;
+        sv[k].r -= Wr * tv[k].r - Wi * tv[k].i;
+        sv[k].i -= Wr * tv[k].i + Wi * tv[k].r;
+      }
+      store_spinor<PX, RX>(x, cb, g.Vh_pad, xv);
+      store_spinor<P, R>(r, cb, g.Vh_pad, sv);
+      load_spinor_rw<P, R>(zv, r0, cb, g.Vh_pad);
+      site_cdot(zv, sv, acc[0], acc[1]);
+      acc[2] += site_norm2<R>(sv);
     }
-    store_spinor<PX, RX>(x, cb, g.Vh_pad, xv);
-    store_spinor<P, R>(r, cb, g.Vh_pad, sv);
-    if constexpr (P == WD_F16) load_spinor_rw<P, R>(sv, r, cb, g.Vh_pad);  // what was stored
-    load_spinor_rw<P, R>(zv, r0, cb, g.Vh_pad);
-    site_cdot(zv, sv, acc[0], acc[1]);
-    acc[2] += site_norm2<R>(sv);
+  } else {
+    // resident grid, next site's loads first (as in cg_update_xp)
+    const int stride = gridDim.x * BS, VP = g.Vh_pad;
+    int cb = blockIdx.x * BS + threadIdx.x;
+    RawSite<P> rp, rsv, rt, rz;
+    RawSite<PX> rx;
+    if (cb < g.Vh) {
+      load_raw<P>(rp, p, cb, VP);
+      load_raw<P>(rsv, s, cb, VP);
+      load_raw<P>(rt, t, cb, VP);
+      load_raw<PX>(rx, x, cb, VP);
+      load_raw<P>(rz, r0, cb, VP);
+    }
+    for (; cb < g.Vh; cb += stride) {
+      const int nx = cb + stride;
+      RawSite<P> np, ns, nt, nz;
+      RawSite<PX> nxr;
+      if (nx < g.Vh) {
+        load_raw<P>(np, p, nx, VP);
+        load_raw<P>(ns, s, nx, VP);
+        load_raw<P>(nt, t, nx, VP);
+        load_raw<PX>(nxr, x, nx, VP);
+        load_raw<P>(nz, r0, nx, VP);
+      }
+      cx<R> pv[12], sv[12], tv[12], zv[12];
+      cx<RX> xv[12];
+      unpack_raw<P, R>(pv, rp);
+      unpack_raw<P, R>(sv, rsv);
+      unpack_raw<P, R>(tv, rt);
+      unpack_raw<PX, RX>(xv, rx);
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        const RX pr = (RX)pv[k].r, pi = (RX)pv[k].i, sr = (RX)sv[k].r, si = (RX)sv[k].i;
+        xv[k].r += Ar * pr - Ai * pi + Wxr * sr - Wxi * si;
+        xv[k].i += Ar * pi + Ai * pr + Wxr * si + Wxi * sr;
+        sv[k].r -= Wr * tv[k].r - Wi * tv[k].i;
+        sv[k].i -= Wr * tv[k].i + Wi * tv[k].r;
+      }
+      store_spinor<PX, RX>(x, cb, VP, xv);
+      // (FP16: sv becomes the site as stored, the values load_spinor_rw would
+      // read back)
+      if constexpr (P == WD_F16)
+        store_spinor_f16<R, true>(r, cb, VP, sv);
+      else
+        store_spinor<P, R>(r, cb, VP, sv);
+      unpack_raw<P, R>(zv, rz);
+      site_cdot(zv, sv, acc[0], acc[1]);
+      acc[2] += site_norm2<R>(sv);
+      rp = np;
+      rsv = ns;
+      rt = nt;
+      rx = nxr;
+      rz = nz;
+    }
   }
   // summed into rho[1 - kp] and rr by the next launch
   block_partials<3, BS>(acc, rs.partials);
@@ -395,11 +451,12 @@ __global__ void bicg_restart_scalars(CgScalars* sc) {
 // ---------------------------------------------------------------------------
 
 template <int P, int PX>
-static void update_grids_t(int vh, int (&grid)[4]) {
+static void update_grids_t(int vh, int (&grid)[5]) {
   grid[0] = resident_grid(cg_update_r<P, 256>, vh);
   grid[1] = resident_grid(cg_update_xp<P, PX, 256>, vh);
   grid[2] = resident_grid(bicg_update_p<P, 256>, vh);
   grid[3] = resident_grid(bicg_update_s<P, 256>, vh);
+  grid[4] = resident_grid(bicg_update_xr<P, PX, 256>, vh);
 }
 
 struct Workspace {
@@ -429,8 +486,9 @@ struct Workspace {
   double* gf_spinor = nullptr;     // rotated right-hand side (canonical)
   CgScalars* sc = nullptr;
   CgScalars* sc_host = nullptr;    // pinned
-  // grids of cg_update_r, cg_update_xp, bicg_update_p, bicg_update_s
-  int upd_grid[4] = {1, 1, 1, 1};
+  // grids of cg_update_r, cg_update_xp, bicg_update_p, bicg_update_s,
+  // bicg_update_xr
+  int upd_grid[5] = {1, 1, 1, 1, 1};
   cudaStream_t cap = nullptr;      // private capture stream
   // the instantiated iteration graph of the last solve, reused by the next
   // solve on this workspace with the same key (its kernels hold workspace
@@ -606,7 +664,6 @@ cudaError_t iteration_bicg_t(Ctx& c, int kp, cudaStream_t st) {
   Workspace& w = *c.w;
   const Geom& g = w.g;
   const double k2 = c.kappa * c.kappa;
-  const int grid = blas_grid(g.Vh, 256);
   cudaError_t e;
   if ((e = launch_pdl(bicg_update_p<P, 256>, dim3(w.upd_grid[2]), dim3(256), st, (char*)w.p,
                       (const char*)w.r, (const char*)w.q, (const CgScalars*)w.sc, kp, g)))
@@ -628,12 +685,12 @@ cudaError_t iteration_bicg_t(Ctx& c, int kp, cudaStream_t st) {
   if ((e = dsl(c, c.sprec, c.srecon, w.gs, w.t, w.ts, WD_EVEN, 0, -k2, w.s, 1.0, nullptr, 0,
                &w.sc->tts[kp][0], st, RED_NORM_DOTX)))
     return e;
-  if ((e = launch_pdl(bicg_update_xr<P, PX, 256>, dim3(grid), dim3(256), st, (char*)w.xs,
-                      (char*)w.r, (const char*)w.p, (const char*)w.s, (const char*)w.t,
-                      (const char*)w.r0, w.sc, kp, g, scratch())))
+  if ((e = launch_pdl(bicg_update_xr<P, PX, 256>, dim3(w.upd_grid[4]), dim3(256), st,
+                      (char*)w.xs, (char*)w.r, (const char*)w.p, (const char*)w.s,
+                      (const char*)w.t, (const char*)w.r0, w.sc, kp, g, scratch())))
     return e;
   SumOut o = {{&w.sc->rho[1 - kp][0], &w.sc->rho[1 - kp][1], &w.sc->rr}};
-  return sum_block_partials(3, scratch().partials, grid, o, st);
+  return sum_block_partials(3, scratch().partials, w.upd_grid[4], o, st);
 }
 
 cudaError_t iteration(Ctx& c, int kp, cudaStream_t st) {
