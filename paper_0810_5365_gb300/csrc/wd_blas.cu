@@ -4,7 +4,9 @@
 // GPU in double precision by parallel reduction, and BLAS-like updates
 // (section "Wilson inverter: Main features").  Reductions here are two-level
 // and deterministic: fixed grid, fixed tree inside a block, and a fixed-order
-// sum of the per-block partials by the last block to finish.
+// sum of the per-block partials, either by the last block to finish
+// (grid_reduce: wd_norm2, wd_cdot) or by a one-CTA launch that follows the
+// kernel in its stream (sum_block_partials: the fused norms of the solvers).
 #include "wd_internal.h"
 
 namespace wd {

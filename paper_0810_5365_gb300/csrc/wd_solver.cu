@@ -18,7 +18,11 @@
 //    the true residual is recomputed with the FP64 operator;
 //  * all CG scalars stay on the device; each block of `check_interval`
 //    iterations is one captured CUDA graph; the host reads four doubles per
-//    block to decide on convergence.
+//    block to decide on convergence;
+//  * the norms and dot products are fused into the kernels that produce the
+//    vectors (per-CTA partials, summed in a fixed order by a one-CTA launch
+//    behind them), and consecutive launches overlap (programmatic dependent
+//    launch).
 #include <chrono>
 #include <cmath>
 #include <cstring>
