@@ -285,8 +285,10 @@ int wd_dslash_set_block(int sites);
 
 /* Launch overlap of consecutive single-field hopping kernels (the paper has
  * no such component).  enable = 1 (the default): every hopping launch of
- * wd_dslash, wd_dslash_dag, wd_dslash_ex, wd_mhat and the solvers is a
- * programmatic dependent launch.  The kernel first lets the next kernel of
+ * wd_dslash, wd_dslash_dag, wd_dslash_ex, wd_mhat and the solvers, the
+ * one-CTA launch that sums a fused norm's per-CTA partials, and the CG and
+ * BiCGstab vector updates of wd_solve_ex are programmatic dependent
+ * launches.  The kernel first lets the next kernel of
  * the stream be scheduled once all of its own CTAs have started, then waits
  * until the previous kernel of the stream has completed and its writes are
  * visible, before it reads or writes any memory.  So consecutive launches
